@@ -1,0 +1,336 @@
+/*
+ * ch_oracle.c -- plain, slow, single-threaded FP64 reference of the Cahn-Hilliard
+ * ensemble time-stepper.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or load this
+ * file; only the test-suite, the smoke check and the CPU-baseline leg of the benchmark
+ * do.  It shares no code, header, table or constant generator with the CUDA library.
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (see oracle/build.py), so every
+ * product below is rounded on its own (no fused multiply-add).
+ *
+ * What it computes (paper: O Naraigh & Gloster, "A large-scale statistical study of the
+ * coarsening rate in models of Ostwald-Ripening"):
+ *   - the Cahn-Hilliard equation with constant mobility, Sec. 1 Eq. (3):
+ *         dC/dt = lap(C^3 - C - gamma lap C),  periodic square domain [0,L)^2;
+ *   - the free energy and its time derivative, Sec. 1 Eq. (4), with the bulk term
+ *     1/4 (C^2-1)^2 (the prefactor that makes Eq. (4)'s dF/dt the derivative of F for
+ *     the flux of Eq. (3));
+ *   - the coarsening rate beta = -(t/F) dF/dt, Sec. 1 Eq. (6), and its time average
+ *     over a window [t1, T], Sec. 3.3 Eq. (42) (the paper's beta_0 estimate,
+ *     applied to the CH ensembles in Sec. 4.2, Table 4).
+ * The discretisation (Sec. 4.1 says only "semi-implicit ADI finite differences,
+ * periodic") is read as the delta-form approximate factorisation
+ *     (I + s D_x^4)(I + s D_y^4)(C^{n+1} - C^n) = dt * lap_h( C^3 - C - gamma lap_h C )^n,
+ *     s = gamma*dt,  D^4 = (D^2)^2,  lap_h the 5-point Laplacian,
+ * i.e. the nonlinear and cross terms explicit and gamma*lap^2 implicit per direction.
+ * Each implicit factor is a cyclic, constant, symmetric pentadiagonal system per grid
+ * line; this file solves it by Gaussian elimination of the bordered band (no pivoting:
+ * the matrix is symmetric positive definite).  Every step is written in the order the
+ * scheme states it; no blocking, fusion or reordering.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_ENOMEM (-2)
+
+/* ------------------------------------------------------------------------------ */
+/* SplitMix64 (G. Steele, D. Lea, C. Flood, "Fast splittable pseudorandom number     */
+/* generators", OOPSLA 2014).  The generator keeps a 64-bit state, adds the odd       */
+/* constant 0x9e3779b97f4a7c15 before each draw and returns a bijective mix of the   */
+/* new state, so the k-th draw (k = 0, 1, ...) of a stream started from `seed` is    */
+/* mix(seed + (k+1) * 0x9e3779b97f4a7c15): a counter-based generator.                 */
+/* ------------------------------------------------------------------------------ */
+static uint64_t or_sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+uint64_t or_splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t state = seed;
+  state += (k + 1ULL) * 0x9e3779b97f4a7c15ULL;
+  return or_sm64_mix(state);
+}
+
+/* Uniform u in [0,1): the top 53 bits of the draw times 2^-53 (exact in FP64). */
+double or_uniform(uint64_t seed, uint64_t k) {
+  return (double)(or_splitmix64(seed, k) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/*
+ * Initial field: C = C0 + 0.1 * (2u - 1), u i.i.d. uniform, one draw per grid point,
+ * draw index k = counter_base + j*nx + i (row-major, x fastest).  This is the
+ * "mean + uniform noise" construction of Sec. 4.1 with the noise amplitude +-0.1 about
+ * a chosen mean C0 (the paper's two mixtures are C0 = 0.45 and C0 = 0.5 read off its
+ * formulas; here C0 is an input).
+ */
+void or_initial_field(int nx, int ny, double C0, uint64_t seed, uint64_t counter_base,
+                      double* C) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      uint64_t k = counter_base + (uint64_t)j * (uint64_t)nx + (uint64_t)i;
+      double u = or_uniform(seed, k);
+      double noise = 0.1 * (2.0 * u - 1.0);
+      C[(size_t)j * nx + i] = C0 + noise;
+    }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* 5-point periodic Laplacian:                                                        */
+/*   lap_h v = (v[i+1] + v[i-1] - 2 v[i]) / hx^2 + (v[j+1] + v[j-1] - 2 v[j]) / hy^2  */
+/* ------------------------------------------------------------------------------ */
+static double or_lap_at(const double* v, int nx, int ny, double hx, double hy, int i, int j) {
+  int ip = (i + 1) % nx, im = (i + nx - 1) % nx;
+  int jp = (j + 1) % ny, jm = (j + ny - 1) % ny;
+  double c = v[(size_t)j * nx + i];
+  double dxx = (v[(size_t)j * nx + ip] + v[(size_t)j * nx + im] - 2.0 * c) / (hx * hx);
+  double dyy = (v[(size_t)jp * nx + i] + v[(size_t)jm * nx + i] - 2.0 * c) / (hy * hy);
+  return dxx + dyy;
+}
+
+void or_laplacian(int nx, int ny, double hx, double hy, const double* v, double* out) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) out[(size_t)j * nx + i] = or_lap_at(v, nx, ny, hx, hy, i, j);
+}
+
+/*
+ * Chemical potential and explicit right-hand side of the delta form:
+ *   f  = C^3 - C                   (derivative of the bulk energy 1/4 (C^2-1)^2)
+ *   mu = f - gamma lap_h C         (the bracket of Eq. (3))
+ *   R  = dt lap_h mu               (explicit update; the implicit part is solved below)
+ */
+void or_rhs(int nx, int ny, double hx, double hy, double gamma, double dt, const double* C,
+            double* mu, double* R) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t p = (size_t)j * nx + i;
+      double c = C[p];
+      double f = c * c * c - c;
+      mu[p] = f - gamma * or_lap_at(C, nx, ny, hx, hy, i, j);
+    }
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) R[(size_t)j * nx + i] = dt * or_lap_at(mu, nx, ny, hx, hy, i, j);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Cyclic pentadiagonal solve  A x = r,  A = I + s (D^2)^2  on a periodic line of n   */
+/* points (D^2 the unit-spacing second difference, s already divided by h^4):        */
+/* A[i][i] = 1 + 6s, A[i][i+-1] = -4s, A[i][i+-2] = s, indices mod n.  Needs n >= 5 so */
+/* the +-1 and +-2 offsets never alias.                                               */
+/*                                                                                    */
+/* Method: split the unknowns into the first m = n-2 ("band") and the last two        */
+/* ("border").  In block form [[B, E], [F, G]] with B the non-cyclic pentadiagonal    */
+/* band, E, F the corner couplings and G the 2x2 corner block.  Gaussian elimination  */
+/* of B without pivoting is applied to [E | r_B]; the 2x2 Schur complement            */
+/* G - F B^-1 E gives the border unknowns, back-substitution the rest.  This is plain */
+/* Gaussian elimination of A in natural order with the fill confined to the last two */
+/* rows and columns.                                                                  */
+/* ------------------------------------------------------------------------------ */
+static double or_penta_coef(int n, double s, int i, int j) {
+  int d = ((j - i) % n + n) % n;
+  if (d == 0) return 1.0 + 6.0 * s;
+  if (d == 1 || d == n - 1) return -4.0 * s;
+  if (d == 2 || d == n - 2) return s;
+  return 0.0;
+}
+
+int or_cyclic_penta_solve(int n, double s, const double* r, double* x) {
+  if (n < 5) return OR_EINVAL;
+  int m = n - 2;
+  /* band[i][2 + (j - i)] holds B[i][j] for |j - i| <= 2 */
+  double* band = (double*)calloc((size_t)m * 5, sizeof(double));
+  double* rhs = (double*)calloc((size_t)m * 3, sizeof(double)); /* columns: E0, E1, r_B */
+  if (!band || !rhs) {
+    free(band);
+    free(rhs);
+    return OR_ENOMEM;
+  }
+  for (int i = 0; i < m; ++i) {
+    for (int d = -2; d <= 2; ++d) {
+      int j = i + d;
+      if (j >= 0 && j < m) band[(size_t)i * 5 + 2 + d] = or_penta_coef(n, s, i, j);
+    }
+    rhs[(size_t)i * 3 + 0] = or_penta_coef(n, s, i, m);
+    rhs[(size_t)i * 3 + 1] = or_penta_coef(n, s, i, m + 1);
+    rhs[(size_t)i * 3 + 2] = r[i];
+  }
+  /* forward elimination (no pivoting) */
+  for (int k = 0; k < m; ++k) {
+    double piv = band[(size_t)k * 5 + 2];
+    for (int i = k + 1; i <= k + 2 && i < m; ++i) {
+      double l = band[(size_t)i * 5 + 2 + (k - i)] / piv;
+      for (int j = k; j <= k + 2 && j < m; ++j)
+        band[(size_t)i * 5 + 2 + (j - i)] -= l * band[(size_t)k * 5 + 2 + (j - k)];
+      for (int c = 0; c < 3; ++c) rhs[(size_t)i * 3 + c] -= l * rhs[(size_t)k * 3 + c];
+    }
+  }
+  /* back substitution: Y = B^-1 [E0 E1 r_B] */
+  for (int i = m - 1; i >= 0; --i) {
+    for (int c = 0; c < 3; ++c) {
+      double acc = rhs[(size_t)i * 3 + c];
+      for (int j = i + 1; j <= i + 2 && j < m; ++j) acc -= band[(size_t)i * 5 + 2 + (j - i)] * rhs[(size_t)j * 3 + c];
+      rhs[(size_t)i * 3 + c] = acc / band[(size_t)i * 5 + 2];
+    }
+  }
+  /* Schur complement S = G - F Y[:,0:2], t = r_C - F Y[:,2] */
+  double S[2][2], t[2];
+  for (int a = 0; a < 2; ++a) {
+    for (int b = 0; b < 2; ++b) {
+      double acc = or_penta_coef(n, s, m + a, m + b);
+      for (int j = 0; j < m; ++j) acc -= or_penta_coef(n, s, m + a, j) * rhs[(size_t)j * 3 + b];
+      S[a][b] = acc;
+    }
+    double acc = r[m + a];
+    for (int j = 0; j < m; ++j) acc -= or_penta_coef(n, s, m + a, j) * rhs[(size_t)j * 3 + 2];
+    t[a] = acc;
+  }
+  double det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
+  double xm0 = (t[0] * S[1][1] - S[0][1] * t[1]) / det;
+  double xm1 = (S[0][0] * t[1] - S[1][0] * t[0]) / det;
+  x[m] = xm0;
+  x[m + 1] = xm1;
+  for (int i = 0; i < m; ++i)
+    x[i] = rhs[(size_t)i * 3 + 2] - rhs[(size_t)i * 3 + 0] * xm0 - rhs[(size_t)i * 3 + 1] * xm1;
+  free(band);
+  free(rhs);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Observables (Eq. (4) discretised; read at C^n and the mu^n of the same step):      */
+/*   F_h    = hx hy sum [ 1/4 (C^2-1)^2 + 1/2 gamma ((D+x C)^2 + (D+y C)^2) ]         */
+/*   dFdt_h = -hx hy sum [ (D+x mu)^2 + (D+y mu)^2 ]                                  */
+/* with forward differences D+x v = (v[i+1]-v[i])/hx (periodic).  Summation in        */
+/* row-major order.                                                                   */
+/* ------------------------------------------------------------------------------ */
+void or_observables(int nx, int ny, double hx, double hy, double gamma, const double* C,
+                    const double* mu, double* F, double* dFdt) {
+  double sF = 0.0, sD = 0.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      int ip = (i + 1) % nx, jp = (j + 1) % ny;
+      size_t p = (size_t)j * nx + i;
+      double c = C[p];
+      double cx = (C[(size_t)j * nx + ip] - c) / hx;
+      double cy = (C[(size_t)jp * nx + i] - c) / hy;
+      double w = c * c - 1.0;
+      sF += 0.25 * w * w + 0.5 * gamma * (cx * cx + cy * cy);
+      double mx = (mu[(size_t)j * nx + ip] - mu[p]) / hx;
+      double my = (mu[(size_t)jp * nx + i] - mu[p]) / hy;
+      sD += mx * mx + my * my;
+    }
+  *F = hx * hy * sF;
+  *dFdt = -(hx * hy * sD);
+}
+
+/* Coarsening rate, Eq. (6): beta = -(t/F) dF/dt, t = n dt measured from t = 0. */
+double or_beta(double t, double F, double dFdt) { return -(t / F) * dFdt; }
+
+/* ------------------------------------------------------------------------------ */
+/* One time step of the delta-form factorised scheme on one member (in place):       */
+/*   1. mu, R from C^n (or_rhs);                                                      */
+/*   2. W  = A_x^-1 R  on every row   (A_x = I + s_x D_x^4,  s_x = gamma dt / hx^4); */
+/*   3. dC = A_y^-1 W  on every column (s_y = gamma dt / hy^4);                       */
+/*   4. C^{n+1} = C^n + dC.                                                           */
+/* If obs != NULL, obs[0..1] receive F_h and dFdt_h of C^n (before the update).       */
+/* ------------------------------------------------------------------------------ */
+int or_step(int nx, int ny, double L, double gamma, double dt, double* C, double* obs) {
+  if (nx < 5 || ny < 5) return OR_EINVAL;
+  double hx = L / nx, hy = L / ny;
+  double sx = gamma * dt / (hx * hx * hx * hx);
+  double sy = gamma * dt / (hy * hy * hy * hy);
+  size_t np = (size_t)nx * ny;
+  int nmax = nx > ny ? nx : ny;
+  double* mu = (double*)malloc(np * sizeof(double));
+  double* R = (double*)malloc(np * sizeof(double));
+  double* lin = (double*)malloc((size_t)nmax * sizeof(double));
+  double* lout = (double*)malloc((size_t)nmax * sizeof(double));
+  int rc = OR_OK;
+  if (!mu || !R || !lin || !lout) {
+    rc = OR_ENOMEM;
+    goto done;
+  }
+  or_rhs(nx, ny, hx, hy, gamma, dt, C, mu, R);
+  if (obs) or_observables(nx, ny, hx, hy, gamma, C, mu, &obs[0], &obs[1]);
+  /* rows: R -> W (stored back into R) */
+  for (int j = 0; j < ny; ++j) {
+    for (int i = 0; i < nx; ++i) lin[i] = R[(size_t)j * nx + i];
+    rc = or_cyclic_penta_solve(nx, sx, lin, lout);
+    if (rc) goto done;
+    for (int i = 0; i < nx; ++i) R[(size_t)j * nx + i] = lout[i];
+  }
+  /* columns: W -> dC, then C += dC */
+  for (int i = 0; i < nx; ++i) {
+    for (int j = 0; j < ny; ++j) lin[j] = R[(size_t)j * nx + i];
+    rc = or_cyclic_penta_solve(ny, sy, lin, lout);
+    if (rc) goto done;
+    for (int j = 0; j < ny; ++j) C[(size_t)j * nx + i] = C[(size_t)j * nx + i] + lout[j];
+  }
+done:
+  free(mu);
+  free(R);
+  free(lin);
+  free(lout);
+  return rc;
+}
+
+/* Observables of the current field without stepping (F_h, dFdt_h at C). */
+int or_field_observables(int nx, int ny, double L, double gamma, const double* C, double* F,
+                         double* dFdt) {
+  if (nx < 5 || ny < 5) return OR_EINVAL;
+  double hx = L / nx, hy = L / ny;
+  size_t np = (size_t)nx * ny;
+  double* mu = (double*)malloc(np * sizeof(double));
+  double* R = (double*)malloc(np * sizeof(double));
+  if (!mu || !R) {
+    free(mu);
+    free(R);
+    return OR_ENOMEM;
+  }
+  or_rhs(nx, ny, hx, hy, gamma, 1.0, C, mu, R);
+  or_observables(nx, ny, hx, hy, gamma, C, mu, F, dFdt);
+  free(mu);
+  free(R);
+  return OR_OK;
+}
+
+/*
+ * A run of one member from step index n0 for nsteps steps.  On every step index n with
+ * n % every == 0 a sample (t_n, F_h, dFdt_h, beta) is taken from C^n before that step's
+ * update and appended to `series` (4 doubles per sample, capacity max_samples).  Samples
+ * with t_n >= t1 are added to the running time average of beta (rectangle rule over the
+ * samples, the discrete form of Eq. (42)): *beta_sum += beta, *beta_count += 1.
+ */
+int or_run(int nx, int ny, double L, double gamma, double dt, double* C, int64_t n0,
+           int64_t nsteps, int every, double t1, double* series, int64_t max_samples,
+           int64_t* nsamples, double* beta_sum, int64_t* beta_count) {
+  if (every < 1) return OR_EINVAL;
+  int64_t ns = 0;
+  for (int64_t n = n0; n < n0 + nsteps; ++n) {
+    int take = (n % every) == 0;
+    double obs[2];
+    int rc = or_step(nx, ny, L, gamma, dt, C, take ? obs : NULL);
+    if (rc) return rc;
+    if (take) {
+      double t = (double)n * dt;
+      double beta = or_beta(t, obs[0], obs[1]);
+      if (series && ns < max_samples) {
+        series[ns * 4 + 0] = t;
+        series[ns * 4 + 1] = obs[0];
+        series[ns * 4 + 2] = obs[1];
+        series[ns * 4 + 3] = beta;
+      }
+      ++ns;
+      if (t >= t1) {
+        *beta_sum += beta;
+        *beta_count += 1;
+      }
+    }
+  }
+  if (nsamples) *nsamples = ns;
+  return OR_OK;
+}

@@ -1,0 +1,308 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Each pin takes an `Oracle` instance and raises AssertionError on a mismatch.  None of them
+retypes the oracle's own formula: they use published generator outputs, closed forms
+(Fourier symbols, exact sums of cos^k), dense brute force with a library solver,
+conservation, energy decay and the continuum interface energy.  The pin tests run them
+on the oracle; the mutation test runs them on deliberately broken builds and requires
+every break to be caught.
+"""
+import math
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TWO_PI = 2.0 * math.pi
+
+
+def _golden_splitmix():
+    vals = []
+    with open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                vals.append(int(line, 16))
+    return vals
+
+
+def _symbol(k_index, n, h):
+    """Eigenvalue of minus the periodic second difference for mode k: (4/h^2) sin^2(theta/2)."""
+    theta = TWO_PI * k_index / n
+    return 4.0 / (h * h) * math.sin(theta / 2.0) ** 2
+
+
+# ------------------------------------------------------------------------------------------
+# Random numbers and the initial field
+# ------------------------------------------------------------------------------------------
+def pin_splitmix_golden(orc):
+    for k, v in enumerate(_golden_splitmix()):
+        got = orc.splitmix64(0, k)
+        assert got == v, "splitmix64(0,%d) = %#x, published %#x" % (k, got, v)
+
+
+def pin_uniform_exact(orc):
+    for k, v in enumerate(_golden_splitmix()):
+        want = float(v >> 11) / 9007199254740992.0
+        assert orc.uniform(0, k) == want
+
+
+def pin_initial_field(orc):
+    gold = _golden_splitmix()
+    nx, ny, C0 = 7, 5, 0.3
+    C = orc.initial_field(nx, ny, C0, 0, 0)
+    for k in range(3):
+        u = float(gold[k] >> 11) / 9007199254740992.0
+        assert C[0, k] == C0 + 0.1 * (2.0 * u - 1.0), "IC point %d" % k
+    # draw k = base + j*nx + i: row-major, x fastest, counter shifted by the base
+    C2 = orc.initial_field(nx, ny, C0, 0, 3)
+    assert np.array_equal(C2.ravel()[:-3], C.ravel()[3:])
+    assert np.all(np.abs(C - C0) <= 0.1)
+    big = orc.initial_field(128, 128, -0.2, 12345, 0)
+    assert abs(big.mean() + 0.2) < 4 * 0.1 / math.sqrt(3 * 128 * 128)
+    assert abs(big.std() - 0.1 / math.sqrt(3)) < 2e-3
+
+
+# ------------------------------------------------------------------------------------------
+# Stencils: exact Fourier symbols, the nonlinear term in closed form
+# ------------------------------------------------------------------------------------------
+def pin_laplacian_symbol(orc):
+    nx, ny, L = 12, 10, TWO_PI
+    hx, hy = L / nx, L / ny
+    x = np.arange(nx) * hx
+    y = np.arange(ny) * hy
+    X, Y = np.meshgrid(x, y)
+    for kx, ky in [(1, 0), (0, 1), (2, 3), (5, 4), (6, 5)]:
+        v = np.cos(kx * X + ky * Y + 0.37)
+        lam = _symbol(kx, nx, hx) + _symbol(ky, ny, hy)
+        got = orc.laplacian(v, hx, hy)
+        assert np.max(np.abs(got + lam * v)) <= 1e-12 * max(1.0, lam), (kx, ky)
+
+
+def pin_rhs_constant(orc):
+    C = np.full((9, 11), 0.37)
+    mu, R = orc.rhs(C, 0.5, 0.4, 0.01, 1e-3)
+    assert np.all(R == 0.0)
+    assert np.allclose(mu, 0.37 ** 3 - 0.37, rtol=0, atol=1e-15)
+
+
+def _rhs_single_axis_case(orc, axis):
+    # C = a cos(k x) along one axis: C^3 - C = (3a^3/4 - a) cos(k x) + (a^3/4) cos(3 k x),
+    # every cos(m k x) is an eigenfunction of lap_h with eigenvalue -symbol(m k).
+    n_along, n_across, L, gamma, dt, a, k = 16, 6, TWO_PI, 0.013, 2e-3, 0.7, 1
+    h = L / n_along
+    s = np.arange(n_along) * h
+    c1 = np.cos(k * s)
+    c3 = np.cos(3 * k * s)
+    line = a * c1
+    if axis == 0:  # variation along x
+        C = np.tile(line, (n_across, 1))
+        hx, hy = h, L / n_across
+    else:
+        C = np.tile(line[:, None], (1, n_across))
+        hx, hy = L / n_across, h
+    l1, l3 = _symbol(k, n_along, h), _symbol(3 * k, n_along, h)
+    mu_line = (0.75 * a ** 3 - a + gamma * a * l1) * c1 + 0.25 * a ** 3 * c3
+    R_line = -dt * ((0.75 * a ** 3 - a + gamma * a * l1) * l1 * c1 + 0.25 * a ** 3 * l3 * c3)
+    mu, R = orc.rhs(C, hx, hy, gamma, dt)
+    mu_want = np.tile(mu_line, (n_across, 1)) if axis == 0 else np.tile(mu_line[:, None], (1, n_across))
+    R_want = np.tile(R_line, (n_across, 1)) if axis == 0 else np.tile(R_line[:, None], (1, n_across))
+    assert np.max(np.abs(mu - mu_want)) < 1e-12
+    assert np.max(np.abs(R - R_want)) < 1e-12 * max(1.0, np.max(np.abs(R_want)))
+
+
+def pin_rhs_nonlinear_x(orc):
+    _rhs_single_axis_case(orc, 0)
+
+
+def pin_rhs_nonlinear_y(orc):
+    _rhs_single_axis_case(orc, 1)
+
+
+# ------------------------------------------------------------------------------------------
+# Cyclic pentadiagonal solve
+# ------------------------------------------------------------------------------------------
+def _dense_cyclic(n, s):
+    P = np.roll(np.eye(n), 1, axis=1)
+    P2 = P @ P
+    return (1 + 6 * s) * np.eye(n) - 4 * s * (P + P.T) + s * (P2 + P2.T)
+
+
+def pin_penta_dense_lu(orc):
+    rng = np.random.default_rng(7)
+    for n in range(5, 17):
+        for s in [1e-3, 0.107, 1.0, 13.8, 880.0, 1e4]:
+            A = _dense_cyclic(n, s)
+            r = rng.standard_normal(n)
+            ref = np.linalg.solve(A, r)
+            got = orc.penta_solve(s, r)
+            tol = 64 * np.finfo(float).eps * (1 + 16 * s) * max(1.0, np.max(np.abs(ref)))
+            assert np.max(np.abs(got - ref)) <= tol, (n, s, np.max(np.abs(got - ref)), tol)
+
+
+def pin_penta_eigenvectors(orc):
+    for n in [5, 7, 16, 64]:
+        for s in [0.3, 3.7, 500.0]:
+            i = np.arange(n)
+            for k in range(n):
+                theta = TWO_PI * k / n
+                r = np.cos(theta * i + 0.3)
+                want = r / (1.0 + s * (2.0 - 2.0 * math.cos(theta)) ** 2)
+                got = orc.penta_solve(s, r)
+                assert np.max(np.abs(got - want)) < 1e-13 * (1 + 16 * s), (n, s, k)
+
+
+def pin_penta_constant(orc):
+    for n in [5, 6, 33]:
+        for s in [0.01, 10.0, 1e4]:
+            got = orc.penta_solve(s, np.full(n, -1.25))
+            assert np.max(np.abs(got + 1.25)) < 1e-14 * (1 + 16 * s)
+
+
+# ------------------------------------------------------------------------------------------
+# Full step: linear amplification of a single Fourier mode, conservation, energy
+# ------------------------------------------------------------------------------------------
+def pin_mode_amplification(orc):
+    nx, ny, L, gamma, dt, C0, eps, nsteps = 16, 12, TWO_PI, 0.01, 1e-3, 0.3, 1e-6, 20
+    hx, hy = L / nx, L / ny
+    X, Y = np.meshgrid(np.arange(nx) * hx, np.arange(ny) * hy)
+    sigma = gamma * dt
+    d = 3 * C0 * C0 - 1
+    for kx, ky in [(1, 0), (0, 2), (2, 1), (3, 3), (7, 5)]:
+        phi = np.cos(kx * X + ky * Y)
+        C = C0 + eps * phi
+        for _ in range(nsteps):
+            orc.step(C, L, gamma, dt)
+        amp = np.sum((C - C0) * phi) / np.sum(phi * phi)
+        ax, ay = _symbol(kx, nx, hx), _symbol(ky, ny, hy)
+        A = ax + ay
+        G = 1 - dt * (A * d + gamma * A * A) / ((1 + sigma * ax * ax) * (1 + sigma * ay * ay))
+        want = eps * G ** nsteps
+        assert abs(amp - want) <= 1e-7 * abs(want), (kx, ky, amp, want)
+
+
+def pin_mass_conservation(orc):
+    C = orc.initial_field(40, 24, 0.2, 99, 0)
+    m0 = C.sum()
+    for _ in range(100):
+        orc.step(C, TWO_PI, 0.01, 1e-3)
+    bound = 50 * C.size * np.finfo(float).eps * np.max(np.abs(C)) * math.sqrt(100)
+    assert abs(C.sum() - m0) <= bound, (C.sum() - m0, bound)
+
+
+def pin_energy_monotone(orc):
+    C = orc.initial_field(32, 32, 0.0, 5, 0)
+    Fs = []
+    for _ in range(300):
+        F, _ = orc.step(C, TWO_PI, 0.01, 1e-5, with_obs=True)
+        Fs.append(F)
+    Fs = np.array(Fs)
+    assert np.all(np.diff(Fs) <= 1e-13 * Fs[:-1]), np.max(np.diff(Fs))
+    assert Fs[-1] < Fs[0]
+
+
+def pin_dFdt_is_time_derivative(orc):
+    # Semi-discrete identity: the rate of change of F_h along the scheme equals dFdt_h as
+    # dt -> 0, to first order in dt.
+    n, L, gamma = 32, TWO_PI, 0.05
+    h = L / n
+    X, Y = np.meshgrid(np.arange(n) * h, np.arange(n) * h)
+    base = 0.4 * np.cos(X) + 0.3 * np.sin(2 * Y) + 0.2 * np.cos(X + Y) + 0.1
+    errs = []
+    for dt in [2e-6, 1e-6]:
+        C = base.copy()
+        F0, D0 = orc.step(C, L, gamma, dt, with_obs=True)
+        F1, _ = orc.field_observables(C, L, gamma)
+        errs.append(abs((F1 - F0) / dt - D0) / abs(D0))
+    assert errs[1] < 1e-4, errs
+    assert 0.35 < errs[1] / errs[0] < 0.65, errs  # first order in dt
+
+
+def pin_constant_field_observables(orc):
+    C0, L, gamma = 0.3, 1.7, 0.02
+    C = np.full((9, 12), C0)
+    F, D = orc.field_observables(C, L, gamma)
+    assert abs(F - 0.25 * (C0 * C0 - 1) ** 2 * L * L) <= 1e-14 * F
+    assert D == 0.0
+    assert orc.beta(3.0, F, D) == 0.0
+
+
+def pin_single_mode_energy(orc):
+    # C = C0 + a cos(theta i) along x: exact sums sum cos = 0, cos^2 = n/2, cos^3 = 0,
+    # cos^4 = 3n/8 (4k not a multiple of n), sum (c_{i+1}-c_i)^2 = n (1 - cos theta).
+    nx, ny, L, gamma, C0, a, k = 16, 7, 3.0, 0.02, 0.25, 0.6, 1
+    hx, hy = L / nx, L / ny
+    theta = TWO_PI * k / nx
+    line = C0 + a * np.cos(theta * np.arange(nx))
+    C = np.tile(line, (ny, 1))
+    p, q, r = C0 * C0 - 1, 2 * C0 * a, a * a
+    bulk = nx * p * p + (q * q + 2 * p * r) * nx / 2 + r * r * 3 * nx / 8
+    grad = (a * a / (hx * hx)) * nx * (1 - math.cos(theta))
+    want = hx * hy * ny * (0.25 * bulk + 0.5 * gamma * grad)
+    F, _ = orc.field_observables(C, L, gamma)
+    assert abs(F - want) <= 1e-13 * abs(want), (F, want)
+
+
+def pin_interface_energy(orc):
+    # Two flat interfaces relaxed to equilibrium: F -> 2 L (2 sqrt(2)/3) sqrt(gamma), the
+    # interface energy of the 1/4 (C^2-1)^2 + gamma/2 |grad C|^2 functional; O(h^2) error.
+    nx, ny, L, gamma, dt = 256, 6, TWO_PI, 0.01, 1e-3
+    x = np.arange(nx) * (L / nx)
+    w = math.sqrt(2 * gamma)
+    line = np.tanh((np.abs(x - L / 2) - L / 4) / (1.5 * w))
+    C = np.ascontiguousarray(np.tile(line, (ny, 1)))
+    for _ in range(600):
+        orc.step(C, L, gamma, dt)
+    F, D = orc.field_observables(C, L, gamma)
+    want = 2 * L * (2 * math.sqrt(2) / 3) * math.sqrt(gamma)
+    assert abs(F - want) <= 5e-3 * want, (F, want)
+    assert -5e-3 < D <= 0.0, D  # relaxing towards equilibrium
+
+
+def pin_run_sampling(orc):
+    L, gamma, dt, every = TWO_PI, 0.01, 1e-3, 5
+    C = orc.initial_field(16, 12, 0.1, 3, 0)
+    t1 = 20 * dt
+    res = orc.run(C, L, gamma, dt, 37, every=every, t1=t1)
+    # samples at n = 0, 5, ..., 35 from C^n before the update
+    assert res.series.shape[0] == 8
+    ref = C.copy()
+    betas_in_window = []
+    for n in range(37):
+        if n % every == 0:
+            F, D = orc.field_observables(ref, L, gamma)
+            row = res.series[n // every]
+            assert row[0] == n * dt
+            assert abs(row[1] - F) <= 1e-13 * abs(F) and abs(row[2] - D) <= 1e-12 * abs(D) + 1e-14
+            t = n * dt
+            b = -t * D / F
+            assert abs(row[3] - b) <= 1e-12 * abs(b) + 1e-15
+            if t >= t1:
+                betas_in_window.append(row[3])
+        orc.step(ref, L, gamma, dt)
+    assert res.series[0, 3] == 0.0
+    assert np.array_equal(ref, res.C)
+    assert res.beta_count == len(betas_in_window) == 4
+    assert abs(res.beta_sum - sum(betas_in_window)) <= 1e-14 * abs(res.beta_sum)
+
+
+ALL_PINS = [
+    pin_splitmix_golden,
+    pin_uniform_exact,
+    pin_initial_field,
+    pin_laplacian_symbol,
+    pin_rhs_constant,
+    pin_rhs_nonlinear_x,
+    pin_rhs_nonlinear_y,
+    pin_penta_dense_lu,
+    pin_penta_eigenvectors,
+    pin_penta_constant,
+    pin_mode_amplification,
+    pin_mass_conservation,
+    pin_energy_monotone,
+    pin_dFdt_is_time_derivative,
+    pin_constant_field_observables,
+    pin_single_mode_energy,
+    pin_interface_energy,
+    pin_run_sampling,
+]

@@ -1,0 +1,72 @@
+"""Plausible mistakes planted in a CPU copy of the oracle must each fail at least one pin.
+
+This shows the pins constrain every part of the oracle: a dropped term, a wrong sign,
+index or prefactor, a transposed operand.  Mutants are compiled into a temporary
+directory; the oracle source itself is never modified.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle_pins as P
+from oracle import build as obuild
+from oracle.oracle import Oracle
+
+MUTANTS = {
+    "nonlinear_sign": ("double f = c * c * c - c;", "double f = c - c * c * c;"),
+    "gamma_sign": ("mu[p] = f - gamma * or_lap_at", "mu[p] = f + gamma * or_lap_at"),
+    "lap_y_uses_hx": ("- 2.0 * c) / (hy * hy);", "- 2.0 * c) / (hx * hx);"),
+    "lap_drop_center": ("+ v[(size_t)jm * nx + i] - 2.0 * c)", "+ v[(size_t)jm * nx + i] - 1.0 * c)"),
+    "rhs_no_dt": ("R[(size_t)j * nx + i] = dt * or_lap_at", "R[(size_t)j * nx + i] = or_lap_at"),
+    "sx_wrong_power": ("double sx = gamma * dt / (hx * hx * hx * hx);", "double sx = gamma * dt / (hx * hx * hx);"),
+    "sy_uses_hx": ("double sy = gamma * dt / (hy * hy * hy * hy);", "double sy = gamma * dt / (hx * hx * hx * hx);"),
+    "penta_offdiag": ("return -4.0 * s;", "return -3.0 * s;"),
+    "penta_diag": ("return 1.0 + 6.0 * s;", "return 1.0 + 4.0 * s;"),
+    "schur_sign": ("acc -= or_penta_coef(n, s, m + a, j) * rhs[(size_t)j * 3 + b];",
+                   "acc += or_penta_coef(n, s, m + a, j) * rhs[(size_t)j * 3 + b];"),
+    "backsub_drop_border": ("- rhs[(size_t)i * 3 + 1] * xm1;", ";"),
+    "elim_pivot_row": ("double l = band[(size_t)i * 5 + 2 + (k - i)] / piv;",
+                       "double l = band[(size_t)i * 5 + 2 + (k - i)] / (piv + 1e-3);"),
+    "update_sign": ("C[(size_t)j * nx + i] + lout[j]", "C[(size_t)j * nx + i] - lout[j]"),
+    "rows_cols_swapped_s": ("rc = or_cyclic_penta_solve(nx, sx, lin, lout);", "rc = or_cyclic_penta_solve(nx, sy, lin, lout);"),
+    "bulk_half": ("sF += 0.25 * w * w", "sF += 0.5 * w * w"),
+    "grad_no_half": ("+ 0.5 * gamma * (cx * cx + cy * cy)", "+ gamma * (cx * cx + cy * cy)"),
+    "grad_drop_y": ("(cx * cx + cy * cy)", "(cx * cx)"),
+    "dFdt_sign": ("*dFdt = -(hx * hy * sD);", "*dFdt = (hx * hy * sD);"),
+    "dFdt_uses_C": ("double mx = (mu[(size_t)j * nx + ip] - mu[p]) / hx;",
+                    "double mx = (C[(size_t)j * nx + ip] - C[p]) / hx;"),
+    "beta_sign": ("return -(t / F) * dFdt;", "return (t / F) * dFdt;"),
+    "time_offset": ("double t = (double)n * dt;", "double t = (double)(n + 1) * dt;"),
+    "window_strict": ("if (t >= t1) {", "if (t > t1) {"),
+    "noise_amplitude": ("0.1 * (2.0 * u - 1.0)", "0.1 * (u - 0.5)"),
+    "counter_transposed": ("(uint64_t)j * (uint64_t)nx + (uint64_t)i", "(uint64_t)i * (uint64_t)ny + (uint64_t)j"),
+    "mix_constant": ("0xbf58476d1ce4e5b9ULL", "0xbf58476d1ce4e5b8ULL"),
+    "uniform_bits": ("or_splitmix64(seed, k) >> 11", "or_splitmix64(seed, k) >> 12"),
+    "sample_after_update": ("int take = (n % every) == 0;", "int take = ((n + 1) % every) == 0;"),
+}
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(obuild.SRC) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, source, tmp_path):
+    old, new = MUTANTS[name]
+    assert source.count(old) == 1, "mutation anchor must occur exactly once: %r" % old
+    src = tmp_path / "mut.c"
+    src.write_text(source.replace(old, new))
+    lib = tmp_path / ("libmut_%s.so" % name)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared", "-o", str(lib),
+                    str(src), "-lm"], check=True)
+    orc = Oracle(str(lib))
+    failed = []
+    for pin in P.ALL_PINS:
+        try:
+            pin(orc)
+        except (AssertionError, ValueError, FloatingPointError, ZeroDivisionError):
+            failed.append(pin.__name__)
+    assert failed, "mutant %s passed every pin" % name
