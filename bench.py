@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Cahn-Hilliard ensemble engine (one JSON line on rank 0).
+
+Workload (default): an ensemble of 256 independent periodic runs on 256x256 grids,
+gamma = 0.005, dt = 1e-3, 20 000 steps (t = 20), members 0-127 at C0 = 0 and 128-255 at
+C0 = 0.4, uniform noise +-0.1, F / dF/dt / beta sampled every 100 steps and beta averaged
+over t >= 4, FP64.  One benchmark "step" is one sampling interval: 100 time steps of
+every member (stencil + row sweep, column sweep + update) including the sample.  The
+default --steps 200 therefore times the whole 20 000-step horizon.
+
+Reported:
+  value          grid-point-steps/s of the FP64 path, device-timed (CUDA events on the
+                 engine's stream), inputs resident in HBM; max over ranks for N > 1.
+  e2e            the same metric through the C ABI with host buffers: the initial fields
+                 are uploaded from page-locked host memory and every step ends with a
+                 device-to-host read of F, dF/dt, beta (ch_observables).
+  fp32           the FP32 form on the same workload (throughput, <beta> against FP64).
+  roofline       the dominant kernel against its bound (FP64 pipe for the FP64 path).
+  cpu_baseline   the FP64 CPU oracle timed on this host's cores (bounded sample).
+  --impl reference  times the oracle alone (the reference arm), same metric and config.
+"""
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CH grid-point-steps/s per GB300 (FP32 vs FP64 path); served p50/p99 latency"
+UNIT = "grid-point-steps/s"
+STEPS_PER_BENCH_STEP = 100
+FP64_PIPE_PEAK = 1.25e12  # FLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+# Algorithmic work per grid point of one time step of this scheme (the design doc derives them):
+FLOPS_ROWS = 23.0         # mu (9) + R' (6) + forward/backward row recurrences (8)
+FLOPS_COLS = 10.0         # forward/backward column recurrences (8) + update (2)
+BYTES_ROWS = 2            # words per point: read C, write W
+BYTES_COLS = 3            # words per point: read W, read C, write C
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle legs (spawn pool, created before any CUDA call)
+# ------------------------------------------------------------------------------------------
+def _oracle_worker(args):
+    nx, ny, L, gamma, dt, C0, seed, base, nsteps, field = args
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle.oracle import get
+    orc = get()
+    C = orc.initial_field(nx, ny, C0, seed, base) if field is None else np.array(field)
+    t = time.perf_counter()
+    for _ in range(nsteps):
+        orc.step(C, L, gamma, dt)
+    return time.perf_counter() - t, C
+
+
+def make_pool(cores):
+    from oracle import build as obuild
+    obuild.build()
+    return mp.get_context("spawn").Pool(cores)
+
+
+def oracle_sample(pool, p, cores, nsteps, fields=None):
+    """Run `cores` members of the workload for nsteps each, one per process."""
+    from paper_1911_03386_gb300 import workloads as wl
+    jobs = []
+    for k in range(cores):
+        mk = (k * len(p["C0"])) // cores
+        jobs.append((p["nx"], p["ny"], p["L"], p["gamma"], p["dt"], p["C0"][mk], wl.BASE_SEED,
+                     mk * p["nx"] * p["ny"], nsteps, None if fields is None else fields[k]))
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    pts = cores * p["nx"] * p["ny"] * nsteps
+    return pts, wall, [r[1] for r in res]
+
+
+def cpu_baseline(pool, p, cores, target_s=12.0):
+    pts1, wall1, _ = oracle_sample(pool, p, cores, 2)          # calibration
+    per_step = wall1 / 2
+    nsteps = max(2, int(target_s / max(per_step, 1e-6)))
+    pts, wall, _ = oracle_sample(pool, p, cores, nsteps)
+    return {"value": pts / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d members x %d steps of %dx%d (one member per process, FP64, single-threaded C "
+                      "oracle), %.1f s wall" % (cores, nsteps, p["nx"], p["ny"], wall)}
+
+
+# ------------------------------------------------------------------------------------------
+# Helpers
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index) if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/ch_clocks_%d_%d.csv" % (os.getpid(), index)
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() in ("active", "0x1", "1")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1911_03386_gb300", "csrc"))):
+        if f.endswith((".cu", ".h", ".cuh")):
+            with open(os.path.join(ROOT, "paper_1911_03386_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = data.get("%s|%s" % (kernel, workload))
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def workload_config(p, prec_name):
+    return {"workload": p["name"], "members": len(p["C0"]), "nx": p["nx"], "ny": p["ny"], "L": "2*pi",
+            "gamma": p["gamma"], "dt": p["dt"], "time_steps": p["steps"], "C0": "half 0.0, half 0.4",
+            "time_steps_per_bench_step": STEPS_PER_BENCH_STEP, "sample_every": p["every"], "beta_window_t1": p["t1"],
+            "precision": prec_name,
+            "l2": "inputs larger than L2: field %d MiB + row-solve scratch %d MiB (FP64) > 126 MiB L2" % (
+                len(p["C0"]) * p["nx"] * p["ny"] * 8 >> 20, len(p["C0"]) * p["nx"] * p["ny"] * 8 >> 20)}
+
+
+# ------------------------------------------------------------------------------------------
+# GPU legs
+# ------------------------------------------------------------------------------------------
+def run_gpu_leg(ch, torch, p, prec, K, W, rank, world, dist, profile_kernels=True):
+    """Device-timed run of K bench steps after W warm-up steps; returns a dict."""
+    from paper_1911_03386_gb300 import workloads as wl
+    npts = len(p["C0"]) * p["nx"] * p["ny"]
+    e = ch.Ensemble.create(p["nx"], p["ny"], p["L"], p["gamma"], p["dt"], p["C0"], wl.BASE_SEED + rank, prec)
+    stream = torch.cuda.Stream()
+    e.set_stream(stream.cuda_stream)
+    e.set_sampling(p["every"], p["t1"], capacity=0)
+    for _ in range(W):
+        e.step(STEPS_PER_BENCH_STEP)
+    e.synchronize()
+    e.reset()  # the timed region covers steps 0 .. K*100 of the workload
+    e.set_sampling(p["every"], p["t1"], capacity=0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(K):
+            e.step(STEPS_PER_BENCH_STEP)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    avg, cnt = e.beta_avg()
+    out = {"ms": ms, "pts": npts * K * STEPS_PER_BENCH_STEP, "clocks": clk.summary(), "beta_avg": avg,
+           "launches": K * STEPS_PER_BENCH_STEP * 2}
+    if profile_kernels:
+        # Per-kernel durations: events around each phase launch on the engine's stream,
+        # over 2 sampling intervals of the same state after the timed region.
+        reps = 2 * STEPS_PER_BENCH_STEP
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
+        for r in range(reps):
+            evs[3 * r].record(stream)
+            e.launch_phase(0)
+            evs[3 * r + 1].record(stream)
+            e.launch_phase(1)
+            evs[3 * r + 2].record(stream)
+        torch.cuda.synchronize()
+        out["ms_rows"] = sum(evs[3 * r].elapsed_time(evs[3 * r + 1]) for r in range(reps)) / reps
+        out["ms_cols"] = sum(evs[3 * r + 1].elapsed_time(evs[3 * r + 2]) for r in range(reps)) / reps
+    e.close()
+    return out
+
+
+def run_e2e_leg(ch, torch, p, prec, K, rank, dist):
+    """End to end through the C ABI with host buffers (see module docstring)."""
+    import numpy as np
+    from paper_1911_03386_gb300 import workloads as wl
+    m = len(p["C0"])
+    npts = m * p["nx"] * p["ny"]
+    e = ch.Ensemble.create(p["nx"], p["ny"], p["L"], p["gamma"], p["dt"], p["C0"], wl.BASE_SEED + rank, prec)
+    e.set_sampling(p["every"], p["t1"], capacity=0)
+    # the job's input: every member's initial field, in page-locked host memory
+    host_in = torch.empty(npts, dtype=torch.float64).pin_memory()
+    e.get_fields_ptr(host_in.data_ptr())
+    e.reset()
+    e.set_sampling(p["every"], p["t1"], capacity=0)
+    F = np.empty(m)
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e.set_fields_ptr(host_in.data_ptr())
+    for _ in range(K):
+        e.step(STEPS_PER_BENCH_STEP)
+        F, D, B = e.observables()
+    avg, cnt = e.beta_avg()
+    t1 = time.perf_counter()
+    if dist:
+        torch.distributed.barrier()
+    e.close()
+    return {"s": t1 - t0, "pts": npts * K * STEPS_PER_BENCH_STEP, "h2d": npts * 8 / K, "d2h": 3 * m * 8}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200, help="bench steps (100 time steps each)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    K, W = args.steps, args.warmup
+    if W < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    from paper_1911_03386_gb300 import workloads as wl
+    p = wl.ENSEMBLE_256
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = os.cpu_count() or 1
+
+    if args.impl == "reference":
+        # The reference arm: the FP64 CPU oracle as it stands, on the host cores, rank 0 only.
+        if rank != 0:
+            return
+        pool = make_pool(cores)
+        fields = None
+        for _ in range(W):
+            _, _, fields = oracle_sample(pool, p, cores, 1, fields)
+        tot_pts, tot_s = 0, 0.0
+        ref_steps = 2
+        for _ in range(K):
+            pts, wall, fields = oracle_sample(pool, p, cores, ref_steps, fields)
+            tot_pts += pts
+            tot_s += wall
+        pool.close()
+        v = tot_pts / tot_s
+        line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K, "warmup": W,
+                "ms_per_step": 1e3 * tot_s / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": workload_config(p, "fp64"), "impl": "reference",
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": "per step: %d members x %d time steps of %dx%d, one member per process"
+                                           % (cores, ref_steps, p["nx"], p["ny"])},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    pool = make_pool(cores) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1911_03386_gb300 as ch
+
+    dist = world > 1
+    torch.cuda.set_device(local_rank)
+    if dist:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    r64 = run_gpu_leg(ch, torch, p, ch.CH_FP64, K, W, rank, world, dist)
+    r32 = None if args.no_fp32 else run_gpu_leg(ch, torch, p, ch.CH_FP32, K, W, rank, world, dist)
+    e2e = None if args.no_e2e else run_e2e_leg(ch, torch, p, ch.CH_FP64, K, rank, dist)
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def gather_avg(avg):
+        if not dist:
+            return avg
+        import numpy as np
+        t = torch.tensor(avg, dtype=torch.float64, device="cuda")
+        out = [torch.empty_like(t) for _ in range(world)]
+        torch.distributed.all_gather(out, t)
+        return np.concatenate([o.cpu().numpy() for o in out])
+
+    ms64 = max_over_ranks(r64["ms"])
+    total_pts = r64["pts"] * world
+    value = total_pts / (ms64 * 1e-3)
+    avg64 = gather_avg(r64["beta_avg"])
+    fp32 = None
+    if r32 is not None:
+        ms32 = max_over_ranks(r32["ms"])
+        avg32 = gather_avg(r32["beta_avg"])
+        fp32 = {"value": r32["pts"] * world / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32 / K,
+                "speedup_vs_fp64": ms64 / ms32}
+    e2e_line = None
+    if e2e is not None:
+        s = max_over_ranks(e2e["s"])
+        e2e_line = {"value": e2e["pts"] * world / s, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                    "d2h_bytes_per_step": e2e["d2h"]}
+
+    cpu = cpu_baseline(pool, p, cores) if pool is not None else None
+    if pool is not None:
+        pool.close()
+    if rank != 0:
+        return
+
+    import numpy as np
+
+    def beta_stats(avg):
+        out = {}
+        m = len(p["C0"])
+        for c0 in sorted(set(p["C0"])):
+            idx = [k for k in range(len(avg)) if p["C0"][k % m] == c0]
+            v = np.array([avg[k] for k in idx])
+            out["C0=%g" % c0] = {"mean": float(v.mean()), "se": float(v.std(ddof=1) / math.sqrt(len(v))), "n": len(v)}
+        return out
+
+    npts = len(p["C0"]) * p["nx"] * p["ny"]
+    rows_f = FLOPS_ROWS * npts / (r64["ms_rows"] * 1e-3)
+    cols_f = FLOPS_COLS * npts / (r64["ms_cols"] * 1e-3)
+    dom = "rows" if r64["ms_rows"] >= r64["ms_cols"] else "cols"
+    achieved = rows_f if dom == "rows" else cols_f
+    kname = "rows_kernel<double>" if dom == "rows" else "cols_kernel<double>"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": FP64_PIPE_PEAK / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PIPE_PEAK,
+                "traffic": ncu_traffic(kname, p["name"]),
+                "peak_source": "FP64 pipe, nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz); no measured FP64 peak",
+                "ms_per_launch": {"rows": r64["ms_rows"], "cols": r64["ms_cols"]},
+                "algorithmic_flops_per_point": {"rows": FLOPS_ROWS, "cols": FLOPS_COLS},
+                "hbm_frac_of_measured": (5 * 8 * npts / ((r64["ms_rows"] + r64["ms_cols"]) * 1e-3)) / 6694.5e9}
+    if fp32 is not None:
+        hbm = 6694.5e9
+        rows_b = BYTES_ROWS * 4 * npts / (r32["ms_rows"] * 1e-3)
+        cols_b = BYTES_COLS * 4 * npts / (r32["ms_cols"] * 1e-3)
+        d32 = "rows" if r32["ms_rows"] >= r32["ms_cols"] else "cols"
+        fp32["roofline"] = {"bound": "hbm", "kernel": "%s_kernel<float>" % d32,
+                            "achieved": (rows_b if d32 == "rows" else cols_b) / 1e9, "peak": 6694.5, "unit": "GB/s",
+                            "frac": (rows_b if d32 == "rows" else cols_b) / hbm, "peak_source": "measured hbm_gbs",
+                            "traffic": ncu_traffic("%s_kernel<float>" % d32, p["name"]),
+                            "ms_per_launch": {"rows": r32["ms_rows"], "cols": r32["ms_cols"]},
+                            "step_frac_of_16B_per_point": 16 * npts / ((r32["ms_rows"] + r32["ms_cols"]) * 1e-3) / hbm}
+        s64, s32 = beta_stats(avg64), beta_stats(avg32)
+        fp32["beta_avg_vs_fp64"] = {k: {"fp32": s32[k]["mean"], "fp64": s64[k]["mean"], "se_fp64": s64[k]["se"],
+                                        "within_one_se": abs(s32[k]["mean"] - s64[k]["mean"]) <= s64[k]["se"]}
+                                    for k in s64}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms64 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": workload_config(p, "fp64"),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_line,
+            "gpu_launches": r64["launches"], "clocks": r64["clocks"], "fp32": fp32,
+            "beta_avg": beta_stats(avg64), "kernel_source": kernel_source_hash()}
+    print(json.dumps(line), flush=True)
+    if dist:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * ch.h -- C ABI of the GB300 Cahn-Hilliard ensemble engine (libch.so).
+ *
+ * The engine time-steps ensembles of independent periodic 2-D Cahn-Hilliard runs
+ *     dC/dt = lap(C^3 - C - gamma lap C)                      (paper Sec. 1, Eq. (3))
+ * and accumulates, per run, the free energy F and dF/dt       (Sec. 1, Eq. (4)),
+ * the coarsening rate beta = -(t/F) dF/dt                     (Sec. 1, Eq. (6))
+ * and the time average of beta over a window [t1, T]          (Sec. 3.3, Eq. (42); the
+ * window [20, 100] of Sec. 4.2, Table 4).  The paper (Sec. 4.1) runs M = 1024 such
+ * simulations with "semi-implicit ADI finite differences, periodic in both directions";
+ * this library's scheme is the delta-form approximate factorisation
+ *     (I + s D_x^4)(I + s D_y^4)(C^{n+1} - C^n) = dt lap_h(C^3 - C - gamma lap_h C)^n,
+ *     s = gamma dt,  D^4 = (D^2)^2,  lap_h the 5-point Laplacian, h = L/n per axis,
+ * so one step is a 13-point explicit stencil followed by cyclic pentadiagonal solves
+ * along every row and then every column.
+ *
+ * Conventions
+ *  - All functions return CH_OK (0) on success or a negative CH_E* code; a message for
+ *    the last failure on the calling host thread is in ch_last_error().
+ *  - Fields are row-major ny x nx arrays, x fastest: C[j*nx + i] is at (i*L/nx, j*L/ny).
+ *  - Host pointers are caller-owned and only read/written during the call.  The library
+ *    allocates and owns all device memory of a handle (released by ch_destroy).
+ *  - A handle is not thread-safe: use one handle per host thread.  Work is enqueued on the
+ *    handle's CUDA stream (its own by default, or the caller's via ch_set_stream); calls
+ *    that return host data synchronise that stream only.
+ *  - Precision: CH_FP64 keeps fields and all arithmetic in FP64.  CH_FP32 keeps fields,
+ *    the stencil and the sweeps in FP32 (sweep coefficients computed in FP64, rounded
+ *    once), while the F / dF/dt reductions, beta and its time average stay in FP64.
+ */
+#ifndef CH_H_
+#define CH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CH_OK 0
+#define CH_PENDING 1         /* ch_poll: request not finished yet */
+#define CH_EINVAL (-1)       /* invalid argument (sizes, NULL pointers, non-finite values) */
+#define CH_ENOMEM (-2)       /* device or host allocation failed, or over the HBM budget */
+#define CH_ECUDA (-3)        /* a CUDA runtime call failed (message in ch_last_error) */
+#define CH_ENONFINITE (-4)   /* a run's F or dF/dt became NaN/Inf (the run has diverged) */
+#define CH_ETIMEOUT (-5)     /* a bounded wait ran out */
+#define CH_EBUSY (-6)        /* the serving queue is full */
+#define CH_ENOTFOUND (-7)    /* unknown request id */
+
+/* Precision forms. */
+#define CH_FP64 0
+#define CH_FP32 1
+
+typedef struct ch_ensemble* ch_handle;
+
+/*
+ * One member of an uneven batch: an independent run on its own nx x ny periodic grid
+ * over [0,L)^2 with interface parameter gamma and step dt.  The initial field is
+ *     C = C0 + 0.1 (2u - 1),  u = top 53 bits of SplitMix64 draw k times 2^-53,
+ *     k = counter_base + j*nx + i,   SplitMix64 stream seeded with `seed`
+ * (the uniform-noise initial condition of Sec. 4.1 about the mean C0; SplitMix64 as
+ * published by Steele, Lea & Flood, OOPSLA 2014).
+ */
+typedef struct {
+  int nx, ny;              /* grid points per axis, each >= 5 */
+  double L;                /* domain edge, > 0 */
+  double gamma;            /* > 0 */
+  double dt;               /* > 0 */
+  double C0;               /* mean of the initial field, finite */
+  uint64_t seed;
+  uint64_t counter_base;
+} ch_member_desc;
+
+/*
+ * Create an ensemble of m members sharing nx, ny, L, gamma, dt (Sec. 4.1, Table 3: one
+ * ensemble = M runs of one size).  Member k starts from C0[k] + noise, with draws
+ * counter_base = k*nx*ny of the stream `seed`.  C0 is host memory of length m (read
+ * during the call only).  precision is CH_FP64 or CH_FP32.  Sampling defaults to every
+ * step with the beta window starting at t1 = 0 (see ch_set_sampling).
+ * Errors: CH_EINVAL (nx or ny < 5, m < 1, L/gamma/dt not > 0, non-finite C0, bad
+ * precision, NULL out), CH_ENOMEM, CH_ECUDA.
+ */
+int ch_create_ensemble(int nx, int ny, double L, double gamma, double dt, int m,
+                       const double* C0, uint64_t seed, int precision, ch_handle* out);
+
+/*
+ * Create an uneven batch: m members of differing sizes and parameters (d: host array of
+ * length m), stepped together by the same kernels in one launch per phase.
+ * Errors as ch_create_ensemble, per member.
+ */
+int ch_create_batch(int m, const ch_member_desc* d, int precision, ch_handle* out);
+
+/* Release every device and host resource of h (NULL is ignored).  Synchronises first. */
+void ch_destroy(ch_handle h);
+
+/*
+ * Run all further work of h on the caller's CUDA stream (a cudaStream_t passed as void*;
+ * NULL restores the handle's own stream).  Captured step graphs are discarded.
+ */
+int ch_set_stream(ch_handle h, void* cuda_stream);
+
+/*
+ * Sampling of the observables (Sec. 1 Eqs. (4), (6)): on every step index n with
+ * n % every == 0, F_h, dF_h/dt and beta = -(t_n/F_h) dF_h/dt, t_n = n dt, are taken
+ * from C^n (before that step's update) and appended to the member's series ring of
+ * `capacity` samples (0: keep none).  Samples with t_n >= t1 enter the running time
+ * average of beta (rectangle rule, the discrete form of Sec. 3.3 Eq. (42)).
+ * Resets the series and the averages.  Errors: CH_EINVAL (every < 1, capacity < 0,
+ * t1 not finite).
+ */
+int ch_set_sampling(ch_handle h, int every, double t1, int64_t capacity);
+
+/*
+ * Advance every member by nsteps >= 0 steps (asynchronous on the handle's stream; the
+ * launches are replayed from captured CUDA graphs).  Errors: CH_EINVAL, CH_ECUDA.
+ */
+int ch_step(ch_handle h, int64_t nsteps);
+
+/* Wait for the handle's stream.  Errors: CH_ECUDA. */
+int ch_synchronize(ch_handle h);
+
+/*
+ * F_h, dF_h/dt and beta of the current fields, one value per member (host arrays of
+ * length m, any of them may be NULL).  Discretisation of Eq. (4) with forward
+ * differences:  F_h = hx hy sum[1/4 (C^2-1)^2 + gamma/2 ((D+x C)^2 + (D+y C)^2)],
+ * dF_h/dt = -hx hy sum[(D+x mu)^2 + (D+y mu)^2], mu = C^3 - C - gamma lap_h C;
+ * beta = -(t/F) dF/dt at t = n dt (Eq. (6)).  Synchronises the stream.
+ * Errors: CH_ENONFINITE if any member's field is not finite, CH_ECUDA.
+ */
+int ch_observables(ch_handle h, double* F, double* dFdt, double* beta);
+
+/*
+ * Per-member running time average of beta over the samples with t >= t1 (host arrays of
+ * length m; either may be NULL): avg[k] = sum / count (NaN when count is 0).
+ * Synchronises the stream.
+ */
+int ch_beta_avg(ch_handle h, double* avg, int64_t* count);
+
+/*
+ * Copy member k's series to out (host, 4 doubles per sample: t, F, dF/dt, beta), oldest
+ * first, at most cap samples; *n receives the number written.  Synchronises.
+ */
+int ch_series(ch_handle h, int member, double* out, int64_t cap, int64_t* n);
+
+/* Copy member k's current field to out (host, ny*nx doubles; FP32 fields are widened). */
+int ch_get_field(ch_handle h, int member, double* out);
+
+/*
+ * Overwrite member k's field with in (host, ny*nx doubles; rounded to FP32 in the FP32
+ * form).  Does not change the step index.  Synchronises.
+ */
+int ch_set_field(ch_handle h, int member, const double* in);
+
+/*
+ * Bulk transfer of every member's field: `in` / `out` hold the members in order, member
+ * k as ny_k*nx_k doubles (total = sum of nx*ny).  With page-locked host buffers the FP64
+ * copies are asynchronous DMA; FP32 fields are converted on the host.  Synchronises.
+ */
+int ch_set_fields(ch_handle h, const double* in);
+int ch_get_fields(ch_handle h, double* out);
+
+/*
+ * Launch one phase of a step for every member, on the handle's stream: phase 0 = the row
+ * kernel (13-point stencil, observables on sample steps, row sweep), phase 1 = the column
+ * kernel (column sweep, update, sample finalisation, step counter).  Phase 0 then phase 1
+ * is exactly one ch_step(h, 1); the split exists so callers can time each kernel with
+ * events on the stream.  Errors: CH_EINVAL (phase), CH_ECUDA.
+ */
+int ch_launch_phase(ch_handle h, int phase);
+
+/* Step index n of member k (t = n dt). */
+int ch_get_step(ch_handle h, int member, int64_t* n);
+
+/* Regenerate every initial field, set the step index to 0 and clear samples/averages. */
+int ch_reset(ch_handle h);
+
+/* Number of members; per-member grid size (either pointer may be NULL). */
+int ch_num_members(ch_handle h, int* m);
+int ch_member_shape(ch_handle h, int member, int* nx, int* ny);
+
+/*
+ * After a ch_step, copy member k's row-solve output W = (I + s D_x^4)^-1 R of the last
+ * step, R = dt lap_h mu (the intermediate of the factorised step), into out (host,
+ * ny*nx doubles).  For testing the row kernel on its own.
+ */
+int ch_debug_last_rows(ch_handle h, int member, double* out);
+
+/*
+ * Checkpoint / resume: write or read every field, step index, sample series and
+ * average accumulator of h to/from the file at path (the resumed run continues
+ * bit-identically).  ch_load needs a handle created with the same members and precision.
+ * Errors: CH_EINVAL (mismatch), CH_ECUDA, CH_ENOMEM.
+ */
+int ch_save(ch_handle h, const char* path);
+int ch_load(ch_handle h, const char* path);
+
+/*
+ * Host-side constants of one implicit factor, no GPU work: for the cyclic pentadiagonal
+ * operator I + s D^4 (stencil [s, -4s, 1+6s, -4s, s], s = gamma dt / h^4 > 0) returns
+ * c, p1, p2 with  I + s D^4 = c Q Q^T,  Q y = r  <=>  y_i = r_i + p1 y_{i-1} + p2 y_{i-2}
+ * (indices mod n), and the pre-roll length K after which a recurrence started from a zero
+ * state agrees with the periodic solution to the precision's round-off (CH_FP64 or
+ * CH_FP32).  These are the coefficients the sweeps use (Sec. 4.1: each ADI direction is
+ * a batch of pentadiagonal solves).  Any output pointer may be NULL.
+ * Errors: CH_EINVAL (s not finite or <= 0, bad precision, no convergence).
+ */
+int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, int* K);
+
+/* Message of the last failure on this host thread ("" if none). */
+const char* ch_last_error(void);
+
+/* Library build id, e.g. "ch 0.1 sm_103a". */
+const char* ch_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CH_H_ */

@@ -1,0 +1,335 @@
+"""Python binding of libch (include/ch.h): argument marshalling only.
+
+Every call forwards to the C ABI of the in-tree CUDA library
+paper_1911_03386_gb300/_build/libch.so; every step of the Cahn-Hilliard path runs in its
+sm_103a kernels.  There is no CPU fallback: if the library is missing or cannot be
+loaded, `lib()` raises.  The names follow the C ABI (ch_create_ensemble, ch_step, ...);
+`Ensemble` is a small convenience holder of a handle.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "CH_OK", "CH_PENDING", "CH_EINVAL", "CH_ENOMEM", "CH_ECUDA", "CH_ENONFINITE", "CH_ETIMEOUT",
+    "CH_EBUSY", "CH_ENOTFOUND", "CH_FP64", "CH_FP32", "ChError", "MemberDesc", "lib", "lib_path",
+    "ch_create_ensemble", "ch_create_batch", "ch_destroy", "ch_set_stream", "ch_set_sampling",
+    "ch_step", "ch_synchronize", "ch_observables", "ch_beta_avg", "ch_series", "ch_get_field",
+    "ch_set_field", "ch_set_fields", "ch_get_fields", "ch_launch_phase", "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
+    "ch_debug_last_rows", "ch_save", "ch_load", "ch_penta_factor", "ch_last_error", "ch_version",
+    "Ensemble",
+]
+
+CH_OK, CH_PENDING = 0, 1
+CH_EINVAL, CH_ENOMEM, CH_ECUDA, CH_ENONFINITE, CH_ETIMEOUT, CH_EBUSY, CH_ENOTFOUND = -1, -2, -3, -4, -5, -6, -7
+CH_FP64, CH_FP32 = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "_build", "libch.so")
+
+
+class ChError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libch error %d: %s" % (code, msg))
+        self.code = code
+
+
+class MemberDesc(ctypes.Structure):
+    """ch_member_desc: one run of an uneven batch."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("L", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("C0", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("counter_base", ctypes.c_uint64)]
+
+
+_c_int, _c_dbl, _c_i64, _c_u64, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "ch_create_ensemble": (_c_int, [_c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_int, _dp, _c_u64, _c_int,
+                                    ctypes.POINTER(_vp)]),
+    "ch_create_batch": (_c_int, [_c_int, ctypes.POINTER(MemberDesc), _c_int, ctypes.POINTER(_vp)]),
+    "ch_destroy": (None, [_vp]),
+    "ch_set_stream": (_c_int, [_vp, _vp]),
+    "ch_set_sampling": (_c_int, [_vp, _c_int, _c_dbl, _c_i64]),
+    "ch_step": (_c_int, [_vp, _c_i64]),
+    "ch_synchronize": (_c_int, [_vp]),
+    "ch_observables": (_c_int, [_vp, _dp, _dp, _dp]),
+    "ch_beta_avg": (_c_int, [_vp, _dp, _i64p]),
+    "ch_series": (_c_int, [_vp, _c_int, _dp, _c_i64, _i64p]),
+    "ch_get_field": (_c_int, [_vp, _c_int, _dp]),
+    "ch_set_field": (_c_int, [_vp, _c_int, _dp]),
+    "ch_get_step": (_c_int, [_vp, _c_int, _i64p]),
+    "ch_set_fields": (_c_int, [_vp, _vp]),
+    "ch_get_fields": (_c_int, [_vp, _vp]),
+    "ch_launch_phase": (_c_int, [_vp, _c_int]),
+    "ch_reset": (_c_int, [_vp]),
+    "ch_num_members": (_c_int, [_vp, _ip]),
+    "ch_member_shape": (_c_int, [_vp, _c_int, _ip, _ip]),
+    "ch_debug_last_rows": (_c_int, [_vp, _c_int, _dp]),
+    "ch_save": (_c_int, [_vp, ctypes.c_char_p]),
+    "ch_load": (_c_int, [_vp, ctypes.c_char_p]),
+    "ch_penta_factor": (_c_int, [_c_dbl, _c_int, _dp, _dp, _dp, _ip]),
+    "ch_last_error": (ctypes.c_char_p, []),
+    "ch_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libch (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(lib_path):
+            raise RuntimeError("libch.so is not built (%s); run __graft_entry__.build()" % lib_path)
+        L = ctypes.CDLL(lib_path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, ok=(CH_OK,)):
+    if rc not in ok:
+        raise ChError(rc, lib().ch_last_error().decode())
+    return rc
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def ch_last_error():
+    return lib().ch_last_error().decode()
+
+
+def ch_version():
+    return lib().ch_version().decode()
+
+
+def ch_penta_factor(s, precision=CH_FP64):
+    """(c, p1, p2, K) of I + s D^4 = c Q Q^T (host computation, no GPU)."""
+    c, p1, p2, K = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib().ch_penta_factor(s, precision, ctypes.byref(c), ctypes.byref(p1), ctypes.byref(p2), ctypes.byref(K)))
+    return c.value, p1.value, p2.value, K.value
+
+
+def ch_create_ensemble(nx, ny, L, gamma, dt, C0, seed, precision=CH_FP64):
+    C0 = _f64(C0).ravel()
+    h = _vp()
+    _check(lib().ch_create_ensemble(nx, ny, L, gamma, dt, C0.size, _ptr(C0), seed, precision, ctypes.byref(h)))
+    return h.value
+
+
+def ch_create_batch(descs, precision=CH_FP64):
+    arr = (MemberDesc * len(descs))()
+    for k, d in enumerate(descs):
+        arr[k] = d if isinstance(d, MemberDesc) else MemberDesc(**d)
+    h = _vp()
+    _check(lib().ch_create_batch(len(descs), arr, precision, ctypes.byref(h)))
+    return h.value
+
+
+def ch_destroy(h):
+    lib().ch_destroy(h)
+
+
+def ch_set_stream(h, stream_ptr):
+    _check(lib().ch_set_stream(h, stream_ptr or None))
+
+
+def ch_set_sampling(h, every, t1=0.0, capacity=0):
+    _check(lib().ch_set_sampling(h, every, t1, capacity))
+
+
+def ch_step(h, nsteps):
+    _check(lib().ch_step(h, nsteps))
+
+
+def ch_synchronize(h):
+    _check(lib().ch_synchronize(h))
+
+
+def ch_num_members(h):
+    m = ctypes.c_int()
+    _check(lib().ch_num_members(h, ctypes.byref(m)))
+    return m.value
+
+
+def ch_member_shape(h, member):
+    nx, ny = ctypes.c_int(), ctypes.c_int()
+    _check(lib().ch_member_shape(h, member, ctypes.byref(nx), ctypes.byref(ny)))
+    return nx.value, ny.value
+
+
+def ch_observables(h):
+    """(F, dFdt, beta) arrays of the current fields."""
+    m = ch_num_members(h)
+    F, D, B = np.empty(m), np.empty(m), np.empty(m)
+    _check(lib().ch_observables(h, _ptr(F), _ptr(D), _ptr(B)))
+    return F, D, B
+
+
+def ch_beta_avg(h):
+    m = ch_num_members(h)
+    avg = np.empty(m)
+    cnt = np.empty(m, dtype=np.int64)
+    _check(lib().ch_beta_avg(h, _ptr(avg), cnt.ctypes.data_as(_i64p)))
+    return avg, cnt
+
+
+def ch_series(h, member, cap):
+    out = np.zeros((max(cap, 1), 4))
+    n = ctypes.c_int64()
+    _check(lib().ch_series(h, member, _ptr(out), cap, ctypes.byref(n)))
+    return out[: n.value].copy()
+
+
+def ch_get_field(h, member):
+    nx, ny = ch_member_shape(h, member)
+    out = np.empty((ny, nx))
+    _check(lib().ch_get_field(h, member, _ptr(out)))
+    return out
+
+
+def ch_set_field(h, member, field):
+    nx, ny = ch_member_shape(h, member)
+    f = _f64(field, nx * ny)
+    _check(lib().ch_set_field(h, member, _ptr(f)))
+
+
+def ch_get_step(h, member=0):
+    n = ctypes.c_int64()
+    _check(lib().ch_get_step(h, member, ctypes.byref(n)))
+    return n.value
+
+
+def ch_set_fields(h, ptr):
+    """All members' fields from host memory at address ptr (FP64, member order)."""
+    _check(lib().ch_set_fields(h, ptr))
+
+
+def ch_get_fields(h, ptr):
+    _check(lib().ch_get_fields(h, ptr))
+
+
+def ch_launch_phase(h, phase):
+    _check(lib().ch_launch_phase(h, phase))
+
+
+def ch_reset(h):
+    _check(lib().ch_reset(h))
+
+
+def ch_debug_last_rows(h, member):
+    nx, ny = ch_member_shape(h, member)
+    out = np.empty((ny, nx))
+    _check(lib().ch_debug_last_rows(h, member, _ptr(out)))
+    return out
+
+
+def ch_save(h, path):
+    _check(lib().ch_save(h, os.fsencode(path)))
+
+
+def ch_load(h, path):
+    _check(lib().ch_load(h, os.fsencode(path)))
+
+
+class Ensemble:
+    """Owns one libch handle; methods forward to the ch_* functions above."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    @classmethod
+    def create(cls, nx, ny, L, gamma, dt, C0, seed, precision=CH_FP64):
+        return cls(ch_create_ensemble(nx, ny, L, gamma, dt, C0, seed, precision))
+
+    @classmethod
+    def batch(cls, descs, precision=CH_FP64):
+        return cls(ch_create_batch(descs, precision))
+
+    def close(self):
+        if self.h:
+            ch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def m(self):
+        return ch_num_members(self.h)
+
+    def step(self, n):
+        ch_step(self.h, n)
+
+    def synchronize(self):
+        ch_synchronize(self.h)
+
+    def set_sampling(self, every, t1=0.0, capacity=0):
+        ch_set_sampling(self.h, every, t1, capacity)
+
+    def observables(self):
+        return ch_observables(self.h)
+
+    def beta_avg(self):
+        return ch_beta_avg(self.h)
+
+    def series(self, member, cap):
+        return ch_series(self.h, member, cap)
+
+    def field(self, member):
+        return ch_get_field(self.h, member)
+
+    def set_field(self, member, field):
+        ch_set_field(self.h, member, field)
+
+    def set_fields_ptr(self, ptr):
+        ch_set_fields(self.h, ptr)
+
+    def get_fields_ptr(self, ptr):
+        ch_get_fields(self.h, ptr)
+
+    def launch_phase(self, phase):
+        ch_launch_phase(self.h, phase)
+
+    def step_index(self, member=0):
+        return ch_get_step(self.h, member)
+
+    def reset(self):
+        ch_reset(self.h)
+
+    def last_rows(self, member):
+        return ch_debug_last_rows(self.h, member)
+
+    def set_stream(self, stream_ptr):
+        ch_set_stream(self.h, stream_ptr)
+
+    def save(self, path):
+        ch_save(self.h, path)
+
+    def load(self, path):
+        ch_load(self.h, path)

@@ -1,0 +1,819 @@
+// ch_api.cu -- host side of libch: the C ABI declared in include/ch.h.
+//
+// A handle owns one set of device buffers (see ch_internal.h), a stream, the FP64
+// constants of every member and captured CUDA graphs of a fixed number of steps.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ch.h"
+#include "ch_internal.h"
+
+using chk::MemberParams;
+using chk::MemberState;
+using chk::Tile;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(CH_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CH_CUDA(call, what)                      \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory per CTA on sm_103a
+constexpr int kRowsThreads = 256;
+constexpr int kColsThreads = 256;
+constexpr int kGraphSteps = 16;
+
+// ---------------------------------------------------------------------------------------
+// Spectral factor of the cyclic pentadiagonal operator I + s D^4 (stencil
+// [s, -4s, 1+6s, -4s, s], symbol 1 + s (z - 2 + 1/z)^2):
+//   I + s D^4 = c Q Q^T,  q(z) = 1 - p1 z - p2 z^2 = (1 - a z)(1 - conj(a) z),  |a| < 1.
+// The zeros of the symbol solve z^2 - w z + 1 = 0 with w = 2 +- i/sqrt(s); a is the root
+// inside the unit circle (a = 2 / (w + sqrt(w^2 - 4)) on the larger-modulus branch), so
+// p1 = 2 Re a, p2 = -|a|^2, c = s / |a|^2.  The three coefficient equations
+//   c (1 + p1^2 + p2^2) = 1 + 6s,  c (p1 p2 - p1) = -4s,  -c p2 = s
+// are then polished by Newton's method in FP64.
+// ---------------------------------------------------------------------------------------
+bool spectral_factor(double s, double* c, double* p1, double* p2) {
+  const double a0 = 1.0 + 6.0 * s, a1 = -4.0 * s, a2 = s;
+  const std::complex<double> w(2.0, 1.0 / std::sqrt(s));
+  const std::complex<double> disc = std::sqrt(w * w - 4.0);
+  const std::complex<double> den = std::abs(w + disc) >= std::abs(w - disc) ? w + disc : w - disc;
+  const std::complex<double> a = 2.0 / den;
+  double q1 = 2.0 * a.real(), q2 = -std::norm(a), cc = s / std::norm(a);
+  for (int it = 0; it < 4; ++it) {
+    const double f0 = cc * (1.0 + q1 * q1 + q2 * q2) - a0;
+    const double f1 = cc * (q1 * q2 - q1) - a1;
+    const double f2 = -cc * q2 - a2;
+    // Jacobian rows d(f0, f1, f2)/d(c, p1, p2)
+    const double J[3][3] = {{1.0 + q1 * q1 + q2 * q2, 2.0 * cc * q1, 2.0 * cc * q2},
+                            {q1 * q2 - q1, cc * (q2 - 1.0), cc * q1},
+                            {-q2, 0.0, -cc}};
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (!(std::fabs(det) > 0.0)) break;
+    const double f[3] = {f0, f1, f2};
+    double dx[3];
+    for (int k = 0; k < 3; ++k) {  // Cramer's rule
+      double M[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i][j] = (j == k) ? f[i] : J[i][j];
+      dx[k] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+               M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) /
+              det;
+    }
+    cc -= dx[0];
+    q1 -= dx[1];
+    q2 -= dx[2];
+  }
+  if (!std::isfinite(cc) || !(cc > 0.0) || !std::isfinite(q1) || !std::isfinite(q2)) return false;
+  // roots of q outside the unit circle: |a|^2 = -p2 < 1
+  if (!(-q2 < 1.0) || !(-q2 > 0.0)) return false;
+  const double r0 = cc * (1.0 + q1 * q1 + q2 * q2) - a0;
+  const double r1 = cc * (q1 * q2 - q1) - a1;
+  const double r2 = -cc * q2 - a2;
+  if (!(std::fabs(r0) <= 1e-13 * a0 && std::fabs(r1) <= 1e-13 * a0 && std::fabs(r2) <= 1e-13 * a0)) return false;
+  *c = cc;
+  *p1 = q1;
+  *p2 = q2;
+  return true;
+}
+
+// Smallest K with max |(M^K)_ij| <= tol for the companion matrix M = [[p1, p2], [1, 0]]:
+// a recurrence pre-rolled over K points from a zero state then carries a state error
+// below tol relative to the line's largest value.
+int preroll_length(double p1, double p2, double tol) {
+  double m00 = 1, m01 = 0, m10 = 0, m11 = 1;
+  for (int k = 1; k <= 4000000; ++k) {
+    const double n00 = p1 * m00 + p2 * m10, n01 = p1 * m01 + p2 * m11;
+    m10 = m00;
+    m11 = m01;
+    m00 = n00;
+    m01 = n01;
+    const double mx = std::fmax(std::fmax(std::fabs(m00), std::fabs(m01)), std::fmax(std::fabs(m10), std::fabs(m11)));
+    if (mx <= tol) return k;
+  }
+  return -1;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+struct ch_ensemble {
+  int precision = CH_FP64;
+  int m = 0;
+  size_t elt = 8;
+  int device = 0;
+  std::vector<MemberParams> hp;
+  std::vector<MemberState> hs0;  // initial state (for reset)
+  std::vector<Tile> rt, ct;
+  chk::LaunchShape shape{};
+  int64_t total_points = 0, max_points = 0;
+  int64_t total_bands = 0;
+  int every = 1;
+  double t1 = 0.0;
+  int64_t series_cap = 0;
+  // device
+  void* C = nullptr;
+  void* W = nullptr;
+  MemberParams* dmp = nullptr;
+  MemberState* dms = nullptr;
+  Tile* drt = nullptr;
+  Tile* dct = nullptr;
+  double2* dpart = nullptr;
+  double* dseries = nullptr;
+  double* dobs = nullptr;
+  cudaStream_t own = nullptr;
+  cudaStream_t stream = nullptr;
+  bool external_stream = false;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+
+  chk::DevView view() const {
+    chk::DevView v;
+    v.C = C;
+    v.W = W;
+    v.mp = dmp;
+    v.ms = dms;
+    v.row_tiles = drt;
+    v.col_tiles = dct;
+    v.partials = dpart;
+    v.series = dseries;
+    v.obs_now = dobs;
+    v.m = m;
+    return v;
+  }
+};
+
+namespace {
+
+void drop_graph(ch_ensemble* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_steps = 0;
+}
+
+void free_device(ch_ensemble* h) {
+  drop_graph(h);
+  cudaFree(h->C);
+  cudaFree(h->W);
+  cudaFree(h->dmp);
+  cudaFree(h->dms);
+  cudaFree(h->drt);
+  cudaFree(h->dct);
+  cudaFree(h->dpart);
+  cudaFree(h->dseries);
+  cudaFree(h->dobs);
+  h->C = h->W = nullptr;
+  h->dmp = nullptr;
+  h->dms = nullptr;
+  h->drt = h->dct = nullptr;
+  h->dpart = nullptr;
+  h->dseries = h->dobs = nullptr;
+}
+
+int validate_desc(const ch_member_desc& d, int k) {
+  char buf[160];
+  if (d.nx < 5 || d.ny < 5) {
+    snprintf(buf, sizeof buf, "member %d: nx=%d ny=%d, both must be >= 5", k, d.nx, d.ny);
+    return fail(CH_EINVAL, buf);
+  }
+  if ((int64_t)d.nx * d.ny > (int64_t)1 << 30) {
+    snprintf(buf, sizeof buf, "member %d: nx*ny too large", k);
+    return fail(CH_EINVAL, buf);
+  }
+  if (!finite_pos(d.L) || !finite_pos(d.gamma) || !finite_pos(d.dt)) {
+    snprintf(buf, sizeof buf, "member %d: L, gamma and dt must be finite and > 0", k);
+    return fail(CH_EINVAL, buf);
+  }
+  if (!std::isfinite(d.C0)) {
+    snprintf(buf, sizeof buf, "member %d: C0 is not finite", k);
+    return fail(CH_EINVAL, buf);
+  }
+  return CH_OK;
+}
+
+// Constants of one member (all computed in FP64).
+int fill_params(const ch_member_desc& d, int precision, MemberParams* p) {
+  std::memset(p, 0, sizeof *p);
+  p->nx = d.nx;
+  p->ny = d.ny;
+  p->L = d.L;
+  p->hx = d.L / d.nx;
+  p->hy = d.L / d.ny;
+  p->gamma = d.gamma;
+  p->dt = d.dt;
+  p->C0 = d.C0;
+  p->seed = d.seed;
+  p->counter_base = d.counter_base;
+  const double hx2 = p->hx * p->hx, hy2 = p->hy * p->hy;
+  p->a = 1.0 - 2.0 * d.gamma / hx2 - 2.0 * d.gamma / hy2;
+  p->bx = d.gamma / hx2;
+  p->by = d.gamma / hy2;
+  p->rho = hx2 / hy2;
+  p->w0 = -2.0 * (1.0 + p->rho);
+  const double sigma = d.gamma * d.dt;
+  const double sx = sigma / (hx2 * hx2), sy = sigma / (hy2 * hy2);
+  if (!spectral_factor(sx, &p->cx, &p->p1x, &p->p2x) || !spectral_factor(sy, &p->cy, &p->p1y, &p->p2y))
+    return fail(CH_EINVAL, "factorisation of I + s D^4 did not converge (s out of range)");
+  const double tol = precision == CH_FP64 ? 1e-17 : 1e-8;
+  p->kx = preroll_length(p->p1x, p->p2x, tol);
+  p->ky = preroll_length(p->p1y, p->p2y, tol);
+  if (p->kx < 0 || p->ky < 0) return fail(CH_EINVAL, "decay of I + s D^4 too slow (s out of range)");
+  p->kappa = d.dt / (hx2 * p->cx * p->cy);
+  p->every = 1;
+  p->t1 = 0.0;
+  return CH_OK;
+}
+
+size_t rows_smem_bytes(int nr, int nx, size_t elt, int threads) {
+  size_t b = (size_t)(2 * nr + 6) * (nx + 1) * elt;
+  b = (b + 15) & ~(size_t)15;
+  return b + (size_t)2 * (threads / 32) * sizeof(double);
+}
+
+size_t cols_smem_bytes(int nc, int ny, size_t elt) { return (size_t)2 * ny * (nc + 1) * elt; }
+
+int build_tiles(ch_ensemble* h) {
+  const bool f64 = h->precision == CH_FP64;
+  h->rt.clear();
+  h->ct.clear();
+  h->shape.rows_threads = kRowsThreads;
+  h->shape.cols_threads = kColsThreads;
+  h->shape.rows_smem = 0;
+  h->shape.cols_smem = 0;
+  int64_t part = 0;
+  for (int k = 0; k < h->m; ++k) {
+    MemberParams& p = h->hp[k];
+    // rows: band height and threads per row
+    int br = std::min(p.ny, f64 ? 16 : 32);
+    while (br > 1 && rows_smem_bytes(br, p.nx, h->elt, kRowsThreads) > kSmemMax) br = (br + 1) / 2;
+    if (rows_smem_bytes(br, p.nx, h->elt, kRowsThreads) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
+    p.rows_p = f64 ? 1 : std::max(1, std::min(kRowsThreads / br, p.nx / 64));
+    // columns: panel width and threads per column
+    int bc = std::min(p.nx, f64 ? 16 : 32);
+    while (bc > 1 && cols_smem_bytes(bc, p.ny, h->elt) > kSmemMax) bc = (bc + 1) / 2;
+    if (cols_smem_bytes(bc, p.ny, h->elt) > kSmemMax) return fail(CH_EINVAL, "column too long for shared memory");
+    p.cols_p = f64 ? 1 : std::max(1, std::min(kColsThreads / bc, p.ny / 64));
+    int b = 0;
+    for (int j0 = 0; j0 < p.ny; j0 += br, ++b) h->rt.push_back(Tile{k, j0, std::min(br, p.ny - j0), b});
+    p.nbands = b;
+    p.partial_base = part;
+    part += b;
+    int q = 0;
+    for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) h->ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
+    h->shape.rows_smem = std::max(h->shape.rows_smem, rows_smem_bytes(br, p.nx, h->elt, kRowsThreads));
+    h->shape.cols_smem = std::max(h->shape.cols_smem, cols_smem_bytes(bc, p.ny, h->elt));
+  }
+  h->total_bands = part;
+  return CH_OK;
+}
+
+int upload_params(ch_ensemble* h) {
+  CH_CUDA(cudaMemcpyAsync(h->dmp, h->hp.data(), sizeof(MemberParams) * h->m, cudaMemcpyHostToDevice, h->stream),
+          "upload member parameters");
+  return CH_OK;
+}
+
+int reset_state(ch_ensemble* h) {
+  CH_CUDA(chk::launch_init_fields(h->view(), h->precision, h->max_points, h->stream), "initial fields");
+  CH_CUDA(cudaMemcpyAsync(h->dms, h->hs0.data(), sizeof(MemberState) * h->m, cudaMemcpyHostToDevice, h->stream),
+          "reset member state");
+  if (h->dseries && h->series_cap > 0)
+    CH_CUDA(cudaMemsetAsync(h->dseries, 0, sizeof(double) * 4 * h->series_cap * h->m, h->stream), "clear series");
+  return CH_OK;
+}
+
+int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out) {
+  if (!out) return fail(CH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || !d) return fail(CH_EINVAL, "need m >= 1 members");
+  if (precision != CH_FP64 && precision != CH_FP32) return fail(CH_EINVAL, "precision must be CH_FP64 or CH_FP32");
+  for (int k = 0; k < m; ++k) {
+    int rc = validate_desc(d[k], k);
+    if (rc) return rc;
+  }
+  ch_ensemble* h = new ch_ensemble();
+  h->precision = precision;
+  h->m = m;
+  h->elt = precision == CH_FP64 ? sizeof(double) : sizeof(float);
+  cudaGetDevice(&h->device);
+  h->hp.resize(m);
+  int64_t off = 0;
+  for (int k = 0; k < m; ++k) {
+    int rc = fill_params(d[k], precision, &h->hp[k]);
+    if (rc) {
+      delete h;
+      return rc;
+    }
+    h->hp[k].offset = off;
+    const int64_t np = (int64_t)d[k].nx * d[k].ny;
+    // keep every member's field 16-byte aligned
+    off += (np + 3) & ~(int64_t)3;
+    h->max_points = std::max(h->max_points, np);
+  }
+  h->total_points = off;
+  int rc = build_tiles(h);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  h->hs0.assign(m, MemberState{});
+  for (auto& s : h->hs0) s.remaining = chk::kUnbounded;
+
+  cudaError_t e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  h->stream = h->own;
+  auto alloc = [&](void** p, size_t bytes) -> cudaError_t { return cudaMalloc(p, bytes == 0 ? 16 : bytes); };
+  if ((e = alloc(&h->C, h->elt * off)) != cudaSuccess || (e = alloc(&h->W, h->elt * off)) != cudaSuccess ||
+      (e = alloc((void**)&h->dmp, sizeof(MemberParams) * m)) != cudaSuccess ||
+      (e = alloc((void**)&h->dms, sizeof(MemberState) * m)) != cudaSuccess ||
+      (e = alloc((void**)&h->drt, sizeof(Tile) * h->rt.size())) != cudaSuccess ||
+      (e = alloc((void**)&h->dct, sizeof(Tile) * h->ct.size())) != cudaSuccess ||
+      (e = alloc((void**)&h->dpart, sizeof(double2) * h->total_bands)) != cudaSuccess ||
+      (e = alloc((void**)&h->dobs, sizeof(double) * 3 * m)) != cudaSuccess) {
+    free_device(h);
+    cudaStreamDestroy(h->own);
+    delete h;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? CH_ENOMEM : CH_ECUDA,
+                std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  if ((e = chk::set_kernel_smem_limits(precision, h->shape.rows_smem, h->shape.cols_smem)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->W, 0, h->elt * off, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->drt, h->rt.data(), sizeof(Tile) * h->rt.size(), cudaMemcpyHostToDevice, h->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(h->dct, h->ct.data(), sizeof(Tile) * h->ct.size(), cudaMemcpyHostToDevice, h->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(h->dpart, 0, sizeof(double2) * h->total_bands, h->stream)) != cudaSuccess) {
+    int r = cuda_fail(e, "handle set-up");
+    ch_destroy(h);
+    return r;
+  }
+  if ((rc = upload_params(h)) || (rc = reset_state(h))) {
+    ch_destroy(h);
+    return rc;
+  }
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+    int r = cuda_fail(e, "handle set-up");
+    ch_destroy(h);
+    return r;
+  }
+  *out = h;
+  return CH_OK;
+}
+
+int check_handle(ch_handle h) { return h ? CH_OK : fail(CH_EINVAL, "handle is NULL"); }
+
+int check_member(ch_handle h, int member) {
+  if (!h) return fail(CH_EINVAL, "handle is NULL");
+  if (member < 0 || member >= h->m) return fail(CH_EINVAL, "member index out of range");
+  return CH_OK;
+}
+
+int launch_steps_direct(ch_ensemble* h, int64_t n) {
+  const chk::DevView v = h->view();
+  for (int64_t i = 0; i < n; ++i) {
+    cudaError_t e = chk::launch_step(v, h->precision, (int)h->rt.size(), (int)h->ct.size(), h->shape, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+  }
+  return CH_OK;
+}
+
+int ensure_graph(ch_ensemble* h) {
+  if (h->graph) return CH_OK;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "begin graph capture");
+  const chk::DevView v = h->view();
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i)
+    le = chk::launch_step(v, h->precision, (int)h->rt.size(), (int)h->ct.size(), h->shape, h->stream);
+  e = cudaStreamEndCapture(h->stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(le, "step launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "end graph capture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return cuda_fail(e, "graph instantiate");
+  }
+  h->graph_steps = kGraphSteps;
+  return CH_OK;
+}
+
+int copy_out(ch_ensemble* h, void* dst, const void* src, size_t bytes, const char* what) {
+  CH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream), what);
+  CH_CUDA(cudaStreamSynchronize(h->stream), what);
+  return CH_OK;
+}
+
+int read_states(ch_ensemble* h, std::vector<MemberState>& s) {
+  s.resize(h->m);
+  return copy_out(h, s.data(), h->dms, sizeof(MemberState) * h->m, "read member state");
+}
+
+}  // namespace
+
+extern "C" {
+
+int ch_create_ensemble(int nx, int ny, double L, double gamma, double dt, int m, const double* C0, uint64_t seed,
+                       int precision, ch_handle* out) {
+  if (m < 1 || !C0) return fail(CH_EINVAL, "need m >= 1 and a C0 array");
+  std::vector<ch_member_desc> d(m);
+  for (int k = 0; k < m; ++k) {
+    d[k].nx = nx;
+    d[k].ny = ny;
+    d[k].L = L;
+    d[k].gamma = gamma;
+    d[k].dt = dt;
+    d[k].C0 = C0[k];
+    d[k].seed = seed;
+    d[k].counter_base = (uint64_t)k * (uint64_t)nx * (uint64_t)ny;
+  }
+  return create_common(m, d.data(), precision, out);
+}
+
+int ch_create_batch(int m, const ch_member_desc* d, int precision, ch_handle* out) {
+  return create_common(m, d, precision, out);
+}
+
+void ch_destroy(ch_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_device(h);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+int ch_set_stream(ch_handle h, void* cuda_stream) {
+  if (int rc = check_handle(h)) return rc;
+  CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise before stream switch");
+  drop_graph(h);
+  h->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->own;
+  h->external_stream = cuda_stream != nullptr;
+  return CH_OK;
+}
+
+int ch_set_sampling(ch_handle h, int every, double t1, int64_t capacity) {
+  if (int rc = check_handle(h)) return rc;
+  if (every < 1 || capacity < 0 || !std::isfinite(t1)) return fail(CH_EINVAL, "every >= 1, capacity >= 0, finite t1");
+  if (capacity > 0 && (double)capacity * h->m * 4 * sizeof(double) > 64.0 * (1ull << 30))
+    return fail(CH_EINVAL, "series capacity too large");
+  CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  if (capacity != h->series_cap) {
+    cudaFree(h->dseries);
+    h->dseries = nullptr;
+    h->series_cap = 0;
+    if (capacity > 0) {
+      cudaError_t e = cudaMalloc(&h->dseries, sizeof(double) * 4 * capacity * h->m);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CH_ENOMEM, "series allocation");
+      }
+    }
+    h->series_cap = capacity;
+  }
+  h->every = every;
+  h->t1 = t1;
+  for (auto& p : h->hp) {
+    p.every = every;
+    p.t1 = t1;
+    p.series_cap = capacity;
+  }
+  if (int rc = upload_params(h)) return rc;
+  // clear samples and averages, keep fields and step indices
+  std::vector<MemberState> s;
+  if (int rc = read_states(h, s)) return rc;
+  for (auto& x : s) {
+    x.nsamples = 0;
+    x.beta_count = 0;
+    x.beta_sum = 0.0;
+  }
+  CH_CUDA(cudaMemcpyAsync(h->dms, s.data(), sizeof(MemberState) * h->m, cudaMemcpyHostToDevice, h->stream),
+          "write member state");
+  if (h->dseries) CH_CUDA(cudaMemsetAsync(h->dseries, 0, sizeof(double) * 4 * capacity * h->m, h->stream), "clear series");
+  drop_graph(h);  // graphs hold the old DevView (series pointer)
+  CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  return CH_OK;
+}
+
+int ch_step(ch_handle h, int64_t nsteps) {
+  if (int rc = check_handle(h)) return rc;
+  if (nsteps < 0) return fail(CH_EINVAL, "nsteps must be >= 0");
+  // The legacy default stream cannot be captured: launch directly there.
+  const bool can_graph = h->stream != nullptr && h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
+  int64_t left = nsteps;
+  if (can_graph && left >= kGraphSteps) {
+    if (int rc = ensure_graph(h)) return rc;
+    while (left >= h->graph_steps) {
+      CH_CUDA(cudaGraphLaunch(h->graph, h->stream), "graph launch");
+      left -= h->graph_steps;
+    }
+  }
+  return launch_steps_direct(h, left);
+}
+
+int ch_synchronize(ch_handle h) {
+  if (int rc = check_handle(h)) return rc;
+  CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  return CH_OK;
+}
+
+int ch_observables(ch_handle h, double* F, double* dFdt, double* beta) {
+  if (int rc = check_handle(h)) return rc;
+  CH_CUDA(chk::launch_observe(h->view(), h->precision, (int)h->rt.size(), h->shape, h->stream), "observe launch");
+  std::vector<double> o(3 * (size_t)h->m);
+  if (int rc = copy_out(h, o.data(), h->dobs, sizeof(double) * o.size(), "read observables")) return rc;
+  bool bad = false;
+  for (int k = 0; k < h->m; ++k) {
+    if (F) F[k] = o[3 * k];
+    if (dFdt) dFdt[k] = o[3 * k + 1];
+    if (beta) beta[k] = o[3 * k + 2];
+    if (!std::isfinite(o[3 * k]) || !std::isfinite(o[3 * k + 1])) bad = true;
+  }
+  if (bad) return fail(CH_ENONFINITE, "a member's F or dF/dt is not finite (the run diverged)");
+  return CH_OK;
+}
+
+int ch_beta_avg(ch_handle h, double* avg, int64_t* count) {
+  if (int rc = check_handle(h)) return rc;
+  std::vector<MemberState> s;
+  if (int rc = read_states(h, s)) return rc;
+  for (int k = 0; k < h->m; ++k) {
+    if (avg) avg[k] = s[k].beta_count ? s[k].beta_sum / (double)s[k].beta_count : NAN;
+    if (count) count[k] = s[k].beta_count;
+  }
+  return CH_OK;
+}
+
+int ch_series(ch_handle h, int member, double* out, int64_t cap, int64_t* n) {
+  if (int rc = check_member(h, member)) return rc;
+  if (cap < 0 || (cap > 0 && !out)) return fail(CH_EINVAL, "bad output buffer");
+  std::vector<MemberState> s;
+  if (int rc = read_states(h, s)) return rc;
+  const int64_t have = std::min<int64_t>(s[member].nsamples, h->series_cap);
+  const int64_t take = std::min<int64_t>(have, cap);
+  if (take > 0) {
+    std::vector<double> ring(4 * (size_t)h->series_cap);
+    if (int rc = copy_out(h, ring.data(), h->dseries + (size_t)member * 4 * h->series_cap,
+                          sizeof(double) * ring.size(), "read series"))
+      return rc;
+    const int64_t first = s[member].nsamples - have;  // oldest kept sample number
+    for (int64_t i = 0; i < take; ++i) {
+      const int64_t slot = (first + i) % h->series_cap;
+      std::memcpy(out + 4 * i, ring.data() + 4 * slot, 4 * sizeof(double));
+    }
+  }
+  if (n) *n = take;
+  return CH_OK;
+}
+
+int ch_get_field(ch_handle h, int member, double* out) {
+  if (int rc = check_member(h, member)) return rc;
+  if (!out) return fail(CH_EINVAL, "out is NULL");
+  const MemberParams& p = h->hp[member];
+  const int64_t np = (int64_t)p.nx * p.ny;
+  if (h->precision == CH_FP64)
+    return copy_out(h, out, static_cast<double*>(h->C) + p.offset, sizeof(double) * np, "read field");
+  std::vector<float> tmp(np);
+  if (int rc = copy_out(h, tmp.data(), static_cast<float*>(h->C) + p.offset, sizeof(float) * np, "read field")) return rc;
+  for (int64_t i = 0; i < np; ++i) out[i] = tmp[i];
+  return CH_OK;
+}
+
+int ch_set_field(ch_handle h, int member, const double* in) {
+  if (int rc = check_member(h, member)) return rc;
+  if (!in) return fail(CH_EINVAL, "in is NULL");
+  const MemberParams& p = h->hp[member];
+  const int64_t np = (int64_t)p.nx * p.ny;
+  for (int64_t i = 0; i < np; ++i)
+    if (!std::isfinite(in[i])) return fail(CH_EINVAL, "field value is not finite");
+  if (h->precision == CH_FP64) {
+    CH_CUDA(cudaMemcpyAsync(static_cast<double*>(h->C) + p.offset, in, sizeof(double) * np, cudaMemcpyHostToDevice,
+                            h->stream),
+            "write field");
+  } else {
+    std::vector<float> tmp(np);
+    for (int64_t i = 0; i < np; ++i) tmp[i] = (float)in[i];
+    CH_CUDA(cudaMemcpyAsync(static_cast<float*>(h->C) + p.offset, tmp.data(), sizeof(float) * np, cudaMemcpyHostToDevice,
+                            h->stream),
+            "write field");
+    CH_CUDA(cudaStreamSynchronize(h->stream), "write field");
+  }
+  CH_CUDA(cudaStreamSynchronize(h->stream), "write field");
+  return CH_OK;
+}
+
+int ch_set_fields(ch_handle h, const double* in) {
+  if (int rc = check_handle(h)) return rc;
+  if (!in) return fail(CH_EINVAL, "in is NULL");
+  int64_t src = 0;
+  std::vector<float> tmp;
+  for (int k = 0; k < h->m; ++k) {
+    const MemberParams& p = h->hp[k];
+    const int64_t np = (int64_t)p.nx * p.ny;
+    if (h->precision == CH_FP64) {
+      CH_CUDA(cudaMemcpyAsync(static_cast<double*>(h->C) + p.offset, in + src, sizeof(double) * np,
+                              cudaMemcpyHostToDevice, h->stream),
+              "write fields");
+    } else {
+      tmp.resize(np);
+      for (int64_t i = 0; i < np; ++i) tmp[i] = (float)in[src + i];
+      CH_CUDA(cudaMemcpyAsync(static_cast<float*>(h->C) + p.offset, tmp.data(), sizeof(float) * np,
+                              cudaMemcpyHostToDevice, h->stream),
+              "write fields");
+      CH_CUDA(cudaStreamSynchronize(h->stream), "write fields");
+    }
+    src += np;
+  }
+  CH_CUDA(cudaStreamSynchronize(h->stream), "write fields");
+  return CH_OK;
+}
+
+int ch_get_fields(ch_handle h, double* out) {
+  if (int rc = check_handle(h)) return rc;
+  if (!out) return fail(CH_EINVAL, "out is NULL");
+  int64_t dst = 0;
+  std::vector<float> tmp;
+  for (int k = 0; k < h->m; ++k) {
+    const MemberParams& p = h->hp[k];
+    const int64_t np = (int64_t)p.nx * p.ny;
+    if (h->precision == CH_FP64) {
+      CH_CUDA(cudaMemcpyAsync(out + dst, static_cast<double*>(h->C) + p.offset, sizeof(double) * np,
+                              cudaMemcpyDeviceToHost, h->stream),
+              "read fields");
+    } else {
+      tmp.resize(np);
+      if (int rc = copy_out(h, tmp.data(), static_cast<float*>(h->C) + p.offset, sizeof(float) * np, "read fields"))
+        return rc;
+      for (int64_t i = 0; i < np; ++i) out[dst + i] = tmp[i];
+    }
+    dst += np;
+  }
+  CH_CUDA(cudaStreamSynchronize(h->stream), "read fields");
+  return CH_OK;
+}
+
+int ch_launch_phase(ch_handle h, int phase) {
+  if (int rc = check_handle(h)) return rc;
+  if (phase != 0 && phase != 1) return fail(CH_EINVAL, "phase must be 0 (rows) or 1 (columns)");
+  const int n = phase == 0 ? (int)h->rt.size() : (int)h->ct.size();
+  CH_CUDA(chk::launch_phase(h->view(), h->precision, phase, n, h->shape, h->stream), "phase launch");
+  return CH_OK;
+}
+
+int ch_get_step(ch_handle h, int member, int64_t* n) {
+  if (int rc = check_member(h, member)) return rc;
+  if (!n) return fail(CH_EINVAL, "n is NULL");
+  MemberState s;
+  if (int rc = copy_out(h, &s, h->dms + member, sizeof s, "read step")) return rc;
+  *n = s.step;
+  return CH_OK;
+}
+
+int ch_reset(ch_handle h) {
+  if (int rc = check_handle(h)) return rc;
+  if (int rc = reset_state(h)) return rc;
+  CH_CUDA(cudaStreamSynchronize(h->stream), "reset");
+  return CH_OK;
+}
+
+int ch_num_members(ch_handle h, int* m) {
+  if (int rc = check_handle(h)) return rc;
+  if (m) *m = h->m;
+  return CH_OK;
+}
+
+int ch_member_shape(ch_handle h, int member, int* nx, int* ny) {
+  if (int rc = check_member(h, member)) return rc;
+  if (nx) *nx = h->hp[member].nx;
+  if (ny) *ny = h->hp[member].ny;
+  return CH_OK;
+}
+
+int ch_debug_last_rows(ch_handle h, int member, double* out) {
+  if (int rc = check_member(h, member)) return rc;
+  if (!out) return fail(CH_EINVAL, "out is NULL");
+  const MemberParams& p = h->hp[member];
+  const int64_t np = (int64_t)p.nx * p.ny;
+  const double scale = p.dt / (p.hx * p.hx * p.cx);
+  if (h->precision == CH_FP64) {
+    if (int rc = copy_out(h, out, static_cast<double*>(h->W) + p.offset, sizeof(double) * np, "read W")) return rc;
+    for (int64_t i = 0; i < np; ++i) out[i] *= scale;
+    return CH_OK;
+  }
+  std::vector<float> tmp(np);
+  if (int rc = copy_out(h, tmp.data(), static_cast<float*>(h->W) + p.offset, sizeof(float) * np, "read W")) return rc;
+  for (int64_t i = 0; i < np; ++i) out[i] = (double)tmp[i] * scale;
+  return CH_OK;
+}
+
+// Checkpoint file: "CHCKPT01", int32 precision, int32 m, m x (int32 nx, int32 ny),
+// int64 series_cap, fields (elt * total_points bytes), MemberState[m], series ring.
+int ch_save(ch_handle h, const char* path) {
+  if (int rc = check_handle(h)) return rc;
+  if (!path) return fail(CH_EINVAL, "path is NULL");
+  std::vector<unsigned char> fields(h->elt * h->total_points);
+  if (int rc = copy_out(h, fields.data(), h->C, fields.size(), "read fields")) return rc;
+  std::vector<MemberState> s;
+  if (int rc = read_states(h, s)) return rc;
+  std::vector<double> series(4 * (size_t)h->series_cap * h->m);
+  if (!series.empty())
+    if (int rc = copy_out(h, series.data(), h->dseries, sizeof(double) * series.size(), "read series")) return rc;
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(CH_EINVAL, std::string("cannot open ") + path);
+  bool ok = fwrite("CHCKPT01", 1, 8, f) == 8;
+  int32_t hdr[2] = {h->precision, h->m};
+  ok = ok && fwrite(hdr, sizeof hdr, 1, f) == 1;
+  for (int k = 0; k < h->m && ok; ++k) {
+    int32_t sh[2] = {h->hp[k].nx, h->hp[k].ny};
+    ok = fwrite(sh, sizeof sh, 1, f) == 1;
+  }
+  int64_t cap = h->series_cap;
+  ok = ok && fwrite(&cap, sizeof cap, 1, f) == 1;
+  ok = ok && fwrite(fields.data(), 1, fields.size(), f) == fields.size();
+  ok = ok && fwrite(s.data(), sizeof(MemberState), s.size(), f) == s.size();
+  if (!series.empty()) ok = ok && fwrite(series.data(), sizeof(double), series.size(), f) == series.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? CH_OK : fail(CH_EINVAL, std::string("write failed: ") + path);
+}
+
+int ch_load(ch_handle h, const char* path) {
+  if (int rc = check_handle(h)) return rc;
+  if (!path) return fail(CH_EINVAL, "path is NULL");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(CH_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t hdr[2];
+  bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "CHCKPT01", 8) == 0;
+  ok = ok && fread(hdr, sizeof hdr, 1, f) == 1 && hdr[0] == h->precision && hdr[1] == h->m;
+  for (int k = 0; k < h->m && ok; ++k) {
+    int32_t sh[2];
+    ok = fread(sh, sizeof sh, 1, f) == 1 && sh[0] == h->hp[k].nx && sh[1] == h->hp[k].ny;
+  }
+  int64_t cap = -1;
+  ok = ok && fread(&cap, sizeof cap, 1, f) == 1 && cap == h->series_cap;
+  std::vector<unsigned char> fields(h->elt * h->total_points);
+  std::vector<MemberState> s(h->m);
+  std::vector<double> series(4 * (size_t)h->series_cap * h->m);
+  ok = ok && fread(fields.data(), 1, fields.size(), f) == fields.size();
+  ok = ok && fread(s.data(), sizeof(MemberState), s.size(), f) == s.size();
+  if (!series.empty()) ok = ok && fread(series.data(), sizeof(double), series.size(), f) == series.size();
+  fclose(f);
+  if (!ok) return fail(CH_EINVAL, "checkpoint does not match this handle (members, precision or sampling)");
+  CH_CUDA(cudaMemcpyAsync(h->C, fields.data(), fields.size(), cudaMemcpyHostToDevice, h->stream), "write fields");
+  CH_CUDA(cudaMemcpyAsync(h->dms, s.data(), sizeof(MemberState) * s.size(), cudaMemcpyHostToDevice, h->stream),
+          "write state");
+  if (!series.empty())
+    CH_CUDA(cudaMemcpyAsync(h->dseries, series.data(), sizeof(double) * series.size(), cudaMemcpyHostToDevice, h->stream),
+            "write series");
+  CH_CUDA(cudaStreamSynchronize(h->stream), "load");
+  return CH_OK;
+}
+
+int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, int* K) {
+  if (!finite_pos(s)) return fail(CH_EINVAL, "s must be finite and > 0");
+  if (precision != CH_FP64 && precision != CH_FP32) return fail(CH_EINVAL, "bad precision");
+  double cc, q1, q2;
+  if (!spectral_factor(s, &cc, &q1, &q2)) return fail(CH_EINVAL, "factorisation did not converge");
+  const int k = preroll_length(q1, q2, precision == CH_FP64 ? 1e-17 : 1e-8);
+  if (k < 0) return fail(CH_EINVAL, "decay too slow");
+  if (c) *c = cc;
+  if (p1) *p1 = q1;
+  if (p2) *p2 = q2;
+  if (K) *K = k;
+  return CH_OK;
+}
+
+const char* ch_last_error(void) { return g_last_error.c_str(); }
+
+const char* ch_version(void) { return "ch 0.1 sm_103a"; }
+
+}  // extern "C"

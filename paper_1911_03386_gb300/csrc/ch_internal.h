@@ -1,0 +1,96 @@
+// ch_internal.h -- data layout shared by the CUDA kernels and the host side of libch.
+//
+// Device memory of one handle (all owned by the handle):
+//   C, W        field and row-solve scratch, one contiguous ny x nx block per member at
+//               MemberParams::offset (elements), FP64 or FP32 by the handle's precision;
+//   members     MemberParams[m]   constants of each run (read-only after creation);
+//   state       MemberState[m]    step index, horizon, sampling accumulators;
+//   row_tiles   Tile[]            one CTA of the row kernel per tile (a band of rows);
+//   col_tiles   Tile[]            one CTA of the column kernel per tile (a column panel);
+//   partials    double2[]         FP64 (sum F density, sum dF/dt density) per row band;
+//   series      double[m][cap][4] ring of (t, F, dF/dt, beta) samples per member.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace chk {
+
+constexpr int64_t kUnbounded = INT64_MAX;
+
+struct MemberParams {
+  int64_t offset;        // first element of the member's field in C and W
+  int nx, ny;
+  int kx, ky;            // pre-roll lengths of the x / y recurrences (see ch_kernels.cu)
+  int nbands;            // row tiles of this member = partial slots per sample
+  int rows_p, cols_p;    // threads per line in the row / column sweep
+  int every;             // sampling period in steps
+  int64_t partial_base;  // first partial slot
+  int64_t series_cap;    // samples kept per member (ring)
+  double L, hx, hy, gamma, dt;
+  // chemical potential  mu = C (C^2 - a) - bx (Ce + Cw) - by (Cn + Cs)
+  double a, bx, by;
+  // scaled explicit right-hand side  R' = (mu_e + mu_w) + rho (mu_n + mu_s) + w0 mu,
+  // R = dt lap_h mu = (dt / hx^2) R'
+  double rho, w0;
+  // spectral factor of the cyclic pentadiagonal operator  I + s D^4 = c Q Q^T,
+  // Q y = r  <=>  y_i = r_i + p1 y_{i-1} + p2 y_{i-2}   (indices mod n)
+  double p1x, p2x, cx;
+  double p1y, p2y, cy;
+  // C^{n+1} = C^n + kappa Z,  Z = Q_y^-T Q_y^-1 Q_x^-T Q_x^-1 R',  kappa = dt/(hx^2 cx cy)
+  double kappa;
+  double t1;             // start of the beta time-average window
+  double C0;
+  uint64_t seed, counter_base;
+};
+
+struct MemberState {
+  int64_t step;          // index n of the current field C^n
+  int64_t remaining;     // steps still to run (kUnbounded: no horizon)
+  int active;            // written by the row kernel: member steps in this launch pair
+  int nonfinite;         // set once F or dF/dt is not finite
+  int64_t nsamples;      // samples taken since the last reset
+  int64_t beta_count;
+  double beta_sum;
+  double F, dFdt, beta;  // last sample
+};
+
+struct Tile {
+  int member;
+  int start;             // first row (row tiles) or first column (column tiles)
+  int count;             // rows / columns in the tile
+  int index;             // band / panel number within the member
+};
+
+struct DevView {
+  void* C;
+  void* W;
+  const MemberParams* mp;
+  MemberState* ms;
+  const Tile* row_tiles;
+  const Tile* col_tiles;
+  double2* partials;
+  double* series;
+  double* obs_now;       // [m][3] F, dF/dt, beta of ch_observables
+  int m;
+};
+
+// Launch shapes chosen on the host per handle (see ch_api.cu).
+struct LaunchShape {
+  int rows_threads;      // threads per row-kernel CTA
+  size_t rows_smem;      // dynamic shared memory of the row kernel (max over tiles)
+  int cols_threads;
+  size_t cols_smem;
+};
+
+// Kernel launchers (ch_kernels.cu).  Each returns the launch status.
+cudaError_t launch_init_fields(const DevView& v, int precision, int64_t max_points, cudaStream_t st);
+cudaError_t launch_step(const DevView& v, int precision, int n_row_tiles, int n_col_tiles,
+                        const LaunchShape& sh, cudaStream_t st);
+cudaError_t launch_phase(const DevView& v, int precision, int phase, int n_tiles, const LaunchShape& sh,
+                         cudaStream_t st);
+cudaError_t launch_observe(const DevView& v, int precision, int n_row_tiles,
+                           const LaunchShape& sh, cudaStream_t st);
+cudaError_t set_kernel_smem_limits(int precision, size_t rows_smem, size_t cols_smem);
+
+}  // namespace chk

@@ -1,0 +1,67 @@
+"""Seeded synthetic workloads: member lists, C0 values and request streams.
+
+Pure input generation, shared by the tests, the benchmark and the oracle runs; it holds
+none of the method's arithmetic (the initial fields themselves are drawn inside the
+library and inside the oracle, each from its own SplitMix64).  The shapes follow the
+paper's workload (Sec. 4.1: ensembles of M runs of one size, uniform random initial
+noise about a mean concentration, symmetric and asymmetric mixtures) at the sizes of the
+five workloads below.
+"""
+import math
+
+import numpy as np
+
+BASE_SEED = 1911033860
+TWO_PI = 2.0 * math.pi
+
+# Workload presets (L = 2 pi everywhere; gamma, dt, sizes and horizons per preset).
+SINGLE_64 = dict(name="single-64x64-fp64", nx=64, ny=64, L=TWO_PI, gamma=0.01, dt=1e-3, steps=2000,
+                 C0=[0.0], every=1)
+ENSEMBLE_256 = dict(name="ensemble-256x(256x256)-fp64", nx=256, ny=256, L=TWO_PI, gamma=0.005, dt=1e-3,
+                    steps=20000, C0=[0.0] * 128 + [0.4] * 128, every=100, t1=4.0)
+UNEVEN = dict(name="uneven-64x128^2+32x256^2+8x512^2", gamma=0.005, dt=1e-3, L=TWO_PI, steps=2000,
+              groups=[(64, 128), (32, 256), (8, 512)], C0_cycle=[0.0, 0.2, 0.4])
+SERVING = dict(name="serving-poisson-50/s", rate=50.0, requests=2000, sizes=[64, 128, 256, 512, 1024],
+               horizon=(1000, 50000), C0=(0.0, 0.5), gamma=0.005, dt=1e-3, L=TWO_PI)
+LONG_1024 = dict(name="long-32x(1024x1024)", nx=1024, ny=1024, L=TWO_PI, gamma=0.0025, dt=5e-4,
+                 steps=200000, C0=[0.0] * 16 + [0.3] * 16)
+
+
+def uneven_members(preset=UNEVEN, seed=BASE_SEED):
+    """Member descriptors (dicts for ch_create_batch) of the uneven batch, in group order.
+
+    Every member draws from one SplitMix64 stream (`seed`) at its own counter range.
+    """
+    out = []
+    base = 0
+    k = 0
+    for count, n in preset["groups"]:
+        for _ in range(count):
+            out.append(dict(nx=n, ny=n, L=preset["L"], gamma=preset["gamma"], dt=preset["dt"],
+                            C0=preset["C0_cycle"][k % len(preset["C0_cycle"])], seed=seed, counter_base=base))
+            base += n * n
+            k += 1
+    return out
+
+
+def request_stream(preset=SERVING, seed=BASE_SEED, count=None, rate=None):
+    """Poisson arrivals of single-run requests: list of dicts with arrival time (s), size,
+    horizon (steps), C0 and a per-request seed."""
+    rng = np.random.default_rng(seed)
+    n = count if count is not None else preset["requests"]
+    lam = rate if rate is not None else preset["rate"]
+    gaps = rng.exponential(1.0 / lam, size=n)
+    t = np.cumsum(gaps) - gaps[0]
+    sizes = rng.choice(preset["sizes"], size=n)
+    lo, hi = preset["horizon"]
+    horizons = rng.integers(lo, hi + 1, size=n)
+    c0 = rng.uniform(preset["C0"][0], preset["C0"][1], size=n)
+    seeds = rng.integers(1, 2 ** 63 - 1, size=n, dtype=np.int64)
+    return [dict(arrival=float(t[i]), nx=int(sizes[i]), ny=int(sizes[i]), steps=int(horizons[i]), C0=float(c0[i]),
+                 seed=int(seeds[i]), L=preset["L"], gamma=preset["gamma"], dt=preset["dt"]) for i in range(n)]
+
+
+def random_field(ny, nx, seed, amplitude=0.1, mean=0.0):
+    """A seeded i.i.d. uniform test field (numpy generator), for tests that set fields."""
+    rng = np.random.default_rng(seed)
+    return mean + amplitude * (2.0 * rng.random((ny, nx)) - 1.0)

@@ -1,0 +1,309 @@
+"""GPU path (libch through its C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 fields within 1e-11 of the oracle after 1000 steps of the 64x64
+workload (single run, gamma = 0.01, dt = 1e-3, C0 = 0); single steps within a
+round-off bound; the FP32 form within 1e-4 over 200 steps.  Integer-exact parts (the
+initial field in FP64, step counters, sample times) are compared bit for bit.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import paper_1911_03386_gb300 as ch
+from paper_1911_03386_gb300 import workloads as wl
+from oracle.oracle import get as get_oracle
+
+pytestmark = pytest.mark.gpu
+
+TWO_PI = 2 * math.pi
+SEED = wl.BASE_SEED
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return get_oracle()
+
+
+def ens(nx, ny, C0, gamma=0.01, dt=1e-3, L=TWO_PI, prec=ch.CH_FP64, seed=SEED):
+    return ch.Ensemble.create(nx, ny, L, gamma, dt, C0, seed, prec)
+
+
+# ------------------------------------------------------------------------------------------
+# Initial field
+# ------------------------------------------------------------------------------------------
+def test_initial_field_bit_exact(orc):
+    nx, ny, C0 = 37, 23, [0.0, 0.4, -0.2]
+    with ens(nx, ny, C0) as e:
+        for k, c0 in enumerate(C0):
+            ref = orc.initial_field(nx, ny, c0, SEED, k * nx * ny)
+            assert np.array_equal(e.field(k), ref)
+    with ens(nx, ny, C0, prec=ch.CH_FP32) as e:
+        for k, c0 in enumerate(C0):
+            ref = orc.initial_field(nx, ny, c0, SEED, k * nx * ny).astype(np.float32).astype(np.float64)
+            assert np.array_equal(e.field(k), ref)
+
+
+# ------------------------------------------------------------------------------------------
+# One step: the row kernel (stencil + row solve) and the column kernel on their own
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(48, 40), (64, 64), (5, 7), (33, 130)])
+def test_single_step_rows_and_columns(orc, nx, ny):
+    L, gamma, dt = TWO_PI, 0.01, 1e-3
+    C = np.ascontiguousarray(wl.random_field(ny, nx, 11, amplitude=0.8, mean=0.1))
+    hx, hy = L / nx, L / ny
+    mu, R = orc.rhs(C, hx, hy, gamma, dt)
+    sx = gamma * dt / hx ** 4
+    W_ref = np.stack([orc.penta_solve(sx, R[j]) for j in range(ny)])
+    C_ref = C.copy()
+    orc.step(C_ref, L, gamma, dt)
+    with ens(nx, ny, [0.0], gamma, dt, L) as e:
+        e.set_field(0, C)
+        e.step(1)
+        W = e.last_rows(0)
+        C1 = e.field(0)
+    scaleW = np.max(np.abs(W_ref))
+    assert np.max(np.abs(W - W_ref)) <= 1e-12 * scale_or_one(scaleW)
+    # column kernel alone: the oracle's column solve applied to the GPU's own W
+    sy = gamma * dt / hy ** 4
+    dC_from_W = np.stack([orc.penta_solve(sy, W[:, i]) for i in range(nx)], axis=1)
+    assert np.max(np.abs((C1 - C) - dC_from_W)) <= 1e-12 * scale_or_one(np.max(np.abs(dC_from_W)))
+    assert np.max(np.abs(C1 - C_ref)) <= 1e-13
+
+
+def scale_or_one(x):
+    return x if x > 0 else 1.0
+
+
+# ------------------------------------------------------------------------------------------
+# The 64x64 workload: 1000 steps in FP64 against the oracle
+# ------------------------------------------------------------------------------------------
+def test_parity_single_64_fp64_1000_steps(orc):
+    p = wl.SINGLE_64
+    nsteps, every = 1000, 10
+    C0 = orc.initial_field(p["nx"], p["ny"], 0.0, SEED, 0)
+    ref = orc.run(C0, p["L"], p["gamma"], p["dt"], nsteps, every=every, t1=0.5)
+    with ens(p["nx"], p["ny"], [0.0], p["gamma"], p["dt"], p["L"]) as e:
+        e.set_sampling(every, 0.5, capacity=nsteps // every + 1)
+        e.step(nsteps)
+        C = e.field(0)
+        ser = e.series(0, 1000)
+        avg, cnt = e.beta_avg()
+        assert e.step_index(0) == nsteps
+    err = np.max(np.abs(C - ref.C))
+    print("max|dC| after %d steps: %.3e" % (nsteps, err))
+    assert err <= 1e-11
+    assert ser.shape == ref.series.shape
+    assert np.array_equal(ser[:, 0], ref.series[:, 0])  # sample times bit-exact
+    np.testing.assert_allclose(ser[:, 1], ref.series[:, 1], rtol=1e-11)
+    np.testing.assert_allclose(ser[:, 2], ref.series[:, 2], rtol=1e-9)
+    np.testing.assert_allclose(ser[1:, 3], ref.series[1:, 3], rtol=1e-9)
+    assert ser[0, 3] == 0.0
+    assert cnt[0] == ref.beta_count
+    assert abs(avg[0] - ref.beta_avg) <= 1e-9 * abs(ref.beta_avg)
+
+
+# ------------------------------------------------------------------------------------------
+# Linear amplification of single Fourier modes on a non-square grid (closed form)
+# ------------------------------------------------------------------------------------------
+def test_fourier_mode_amplification_gpu():
+    nx, ny, L, gamma, dt, C0, eps, nsteps = 48, 40, TWO_PI, 0.01, 1e-3, 0.3, 1e-6, 25
+    hx, hy = L / nx, L / ny
+    X, Y = np.meshgrid(np.arange(nx) * hx, np.arange(ny) * hy)
+    sigma, d = gamma * dt, 3 * C0 * C0 - 1
+    with ens(nx, ny, [0.0], gamma, dt, L) as e:
+        for kx, ky in [(1, 0), (0, 3), (2, 5), (11, 7), (24, 20), (4, 19)]:
+            phi = np.cos(kx * X + ky * Y)
+            e.set_field(0, C0 + eps * phi)
+            e.step(nsteps)
+            amp = np.sum((e.field(0) - C0) * phi) / np.sum(phi * phi)
+            ax = 4 / hx ** 2 * math.sin(math.pi * kx / nx) ** 2
+            ay = 4 / hy ** 2 * math.sin(math.pi * ky / ny) ** 2
+            A = ax + ay
+            G = 1 - dt * (A * d + gamma * A * A) / ((1 + sigma * ax * ax) * (1 + sigma * ay * ay))
+            want = eps * G ** nsteps
+            # modes that decay below the spacing of doubles near C0 are not representable
+            assert abs(amp - want) <= 1e-7 * abs(want) + 1e-15, (kx, ky, amp, want)
+
+
+# ------------------------------------------------------------------------------------------
+# Uneven batch: every member against its own oracle run (small, ragged, large s)
+# ------------------------------------------------------------------------------------------
+UNEVEN_SMALL = [
+    dict(nx=5, ny=5, L=TWO_PI, gamma=0.01, dt=1e-3, C0=0.0),
+    dict(nx=7, ny=9, L=1.0, gamma=0.002, dt=1e-3, C0=0.3),      # s large: pre-roll longer than the line
+    dict(nx=33, ny=17, L=TWO_PI, gamma=0.01, dt=1e-3, C0=0.4),
+    dict(nx=64, ny=48, L=TWO_PI, gamma=0.005, dt=1e-3, C0=-0.2),
+    dict(nx=100, ny=37, L=4.0, gamma=0.02, dt=5e-4, C0=0.1),
+    dict(nx=16, ny=130, L=TWO_PI, gamma=0.005, dt=2e-3, C0=0.0),
+]
+
+
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+def test_uneven_batch_members_match_oracle(orc, prec):
+    descs = []
+    base = 0
+    for k, d in enumerate(UNEVEN_SMALL):
+        dd = dict(d, seed=SEED + k, counter_base=base)
+        base += d["nx"] * d["ny"]
+        descs.append(dd)
+    nsteps = 60
+    with ch.Ensemble.batch(descs, prec) as e:
+        e.step(nsteps)
+        for k, d in enumerate(descs):
+            C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
+            ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            tol = 1e-12 if prec == ch.CH_FP64 else 1e-4
+            assert err <= tol, (k, d, err)
+
+
+# ------------------------------------------------------------------------------------------
+# FP32 form against the FP64 oracle
+# ------------------------------------------------------------------------------------------
+def test_fp32_form_200_steps(orc):
+    p = wl.SINGLE_64
+    C0 = orc.initial_field(p["nx"], p["ny"], 0.0, SEED, 0)
+    ref = orc.run(C0, p["L"], p["gamma"], p["dt"], 200)
+    with ens(p["nx"], p["ny"], [0.0], p["gamma"], p["dt"], p["L"], prec=ch.CH_FP32) as e:
+        e.step(200)
+        err = np.max(np.abs(e.field(0) - ref.C))
+    print("FP32 max|dC| after 200 steps: %.3e" % err)
+    assert err <= 1e-4
+
+
+# ------------------------------------------------------------------------------------------
+# Observables on their own; non-finite detection
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+def test_observables_of_current_field(orc, prec):
+    nx, ny, L, gamma, dt = 40, 56, 3.0, 0.02, 1e-3
+    with ens(nx, ny, [0.1, -0.3], gamma, dt, L, prec=prec) as e:
+        e.step(37)
+        F, D, B = e.observables()
+        for k in range(2):
+            C = e.field(k)
+            Fo, Do = orc.field_observables(C, L, gamma)
+            t = 37 * dt
+            # FP64 reductions of the FP64 functional of the stored field in both forms
+            rt = 1e-11
+            assert abs(F[k] - Fo) <= 1e-12 * abs(Fo)
+            assert abs(D[k] - Do) <= rt * abs(Do)
+            assert abs(B[k] - (-(t / Fo) * Do)) <= rt * abs(B[k])
+
+
+def test_nonfinite_run_is_reported():
+    with ens(16, 16, [0.0]) as e:
+        e.set_field(0, np.full((16, 16), 1e120) * np.cos(np.arange(256)).reshape(16, 16))
+        e.step(3)
+        with pytest.raises(ch.ChError) as exc:
+            e.observables()
+        assert exc.value.code == ch.CH_ENONFINITE
+
+
+# ------------------------------------------------------------------------------------------
+# Determinism, graph replay, alone vs in the mix, reset, checkpoint/resume
+# ------------------------------------------------------------------------------------------
+def test_graph_replay_equals_single_launches():
+    with ens(64, 48, [0.0, 0.4]) as a, ens(64, 48, [0.0, 0.4]) as b:
+        a.step(16 * 3 + 5)
+        for _ in range(16 * 3 + 5):
+            b.step(1)
+        for k in range(2):
+            assert np.array_equal(a.field(k), b.field(k))
+
+
+def test_member_alone_equals_member_in_mix():
+    d = dict(nx=64, ny=64, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.4, seed=77, counter_base=0)
+    others = [dict(nx=n, ny=n, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.0, seed=5 + n, counter_base=0)
+              for n in (32, 128, 17)]
+    with ch.Ensemble.batch([d]) as alone, ch.Ensemble.batch(others[:2] + [d] + others[2:]) as mix:
+        alone.step(120)
+        mix.step(120)
+        assert np.array_equal(alone.field(0), mix.field(2))
+
+
+def test_reset_reproduces_run():
+    with ens(32, 32, [0.2]) as e:
+        e.step(40)
+        a = e.field(0)
+        e.reset()
+        assert e.step_index(0) == 0
+        e.step(40)
+        assert np.array_equal(a, e.field(0))
+
+
+def test_checkpoint_resume_bit_exact(tmp_path):
+    path = str(tmp_path / "ck.bin")
+    with ens(32, 40, [0.0, 0.3]) as e:
+        e.set_sampling(5, 0.01, capacity=64)
+        e.step(30)
+        e.save(path)
+        e.step(25)
+        a = [e.field(k) for k in range(2)]
+        sa = e.series(1, 64)
+        e.load(path)
+        assert e.step_index(1) == 30
+        e.step(25)
+        for k in range(2):
+            assert np.array_equal(a[k], e.field(k))
+        assert np.array_equal(sa, e.series(1, 64))
+
+
+def test_zero_steps_and_argument_errors():
+    with ens(8, 8, [0.0]) as e:
+        before = e.field(0)
+        e.step(0)
+        assert np.array_equal(before, e.field(0))
+        with pytest.raises(ch.ChError):
+            e.step(-1)
+        with pytest.raises(ch.ChError):
+            e.field(3)
+        with pytest.raises(ch.ChError):
+            e.set_field(0, np.full((8, 8), np.nan))
+        with pytest.raises(ch.ChError):
+            e.set_sampling(0)
+
+
+def test_runs_on_a_torch_stream():
+    torch = pytest.importorskip("torch")
+    s = torch.cuda.Stream()
+    with ens(32, 32, [0.0]) as a, ens(32, 32, [0.0]) as b:
+        b.set_stream(s.cuda_stream)
+        a.step(40)
+        b.step(40)
+        b.synchronize()
+        assert np.array_equal(a.field(0), b.field(0))
+
+
+# ------------------------------------------------------------------------------------------
+# Full-size workloads in the benchmark's launch configuration, sampled members
+# ------------------------------------------------------------------------------------------
+def test_ensemble_256_full_size_sampled_members(orc):
+    p = wl.ENSEMBLE_256
+    nsteps = 200
+    with ens(p["nx"], p["ny"], p["C0"], p["gamma"], p["dt"], p["L"]) as e:
+        e.set_sampling(p["every"], p["t1"], capacity=4)
+        e.step(nsteps)
+        F, D, B = e.observables()
+        for k in (0, 200):
+            C0 = orc.initial_field(p["nx"], p["ny"], p["C0"][k], SEED, k * p["nx"] * p["ny"])
+            ref = orc.run(C0, p["L"], p["gamma"], p["dt"], nsteps)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            print("member %d max|dC| %.3e" % (k, err))
+            assert err <= 1e-11
+            Fo, Do = orc.field_observables(ref.C, p["L"], p["gamma"])
+            assert abs(F[k] - Fo) <= 1e-11 * abs(Fo)
+        # properties of every member: mass conserved, F decreased
+        for k in range(0, 256, 51):
+            C = e.field(k)
+            C0 = orc.initial_field(p["nx"], p["ny"], p["C0"][k], SEED, k * p["nx"] * p["ny"])
+            assert abs(C.sum() - C0.sum()) <= 1e-9
