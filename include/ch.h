@@ -207,6 +207,34 @@ int ch_load(ch_handle h, const char* path);
  */
 int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, int* K);
 
+/*
+ * Allocation-free step (the paper has no counterpart; this is a deployment aid).
+ * Advance one FP64 field C -- ny*nx doubles in device memory, row-major, owned by the
+ * caller, read and overwritten in place -- by nsteps steps of the same scheme as
+ * ch_step (grid nx x ny over [0,L)^2, gamma, dt), enqueued on `stream` (a cudaStream_t,
+ * NULL for the legacy default stream).  No observables or step counters are kept.
+ *
+ * For callers that cannot call cudaMalloc: code inside a host framework that owns all
+ * device memory through its own pool allocator, real-time loops that forbid an
+ * allocation's synchronisation and latency after start-up, and processes whose device
+ * memory budget is fixed at start.  The call allocates no device memory (on success it
+ * touches no host heap either): its one intermediate, the row-solve result W, lives in a
+ * static device array of 1,048,576 doubles (8 MiB) that every GPU loading libch holds
+ * until the process exits.  So nx*ny must be <= 1,048,576 (e.g. 1024 x 1024); larger
+ * grids are rejected with CH_EINVAL and a message in ch_last_error().
+ *
+ * The first call on each device (with that device current) looks up the array's device
+ * address (cudaGetSymbolAddress) and sets the kernels' shared-memory limits; make that
+ * first call before any stream capture.  All calls on a device share the array, which
+ * keeps the last call's contents; every step overwrites all of W before reading it, so
+ * nothing needs clearing.  Calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on the array: serialise them.
+ * Errors: CH_EINVAL (NULL C, nx or ny < 5, nx*ny above the limit, L/gamma/dt not finite
+ * and > 0, nsteps < 0), CH_ECUDA (set-up or launch failed).
+ */
+int ch_step_field_noalloc(double* C, int nx, int ny, double L, double gamma, double dt, int64_t nsteps,
+                          void* stream);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char* ch_last_error(void);
 

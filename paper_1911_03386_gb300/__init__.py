@@ -17,7 +17,7 @@ __all__ = [
     "ch_create_ensemble", "ch_create_batch", "ch_destroy", "ch_set_stream", "ch_set_sampling",
     "ch_step", "ch_synchronize", "ch_observables", "ch_beta_avg", "ch_series", "ch_get_field",
     "ch_set_field", "ch_set_fields", "ch_get_fields", "ch_launch_phase", "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
-    "ch_debug_last_rows", "ch_save", "ch_load", "ch_penta_factor", "ch_last_error", "ch_version",
+    "ch_debug_last_rows", "ch_save", "ch_load", "ch_penta_factor", "ch_step_field_noalloc", "ch_last_error", "ch_version",
     "Ensemble",
 ]
 
@@ -72,6 +72,7 @@ _SIGS = {
     "ch_save": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_load": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_penta_factor": (_c_int, [_c_dbl, _c_int, _dp, _dp, _dp, _ip]),
+    "ch_step_field_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
     "ch_last_error": (ctypes.c_char_p, []),
     "ch_version": (ctypes.c_char_p, []),
 }
@@ -124,6 +125,12 @@ def ch_penta_factor(s, precision=CH_FP64):
     c, p1, p2, K = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     _check(lib().ch_penta_factor(s, precision, ctypes.byref(c), ctypes.byref(p1), ctypes.byref(p2), ctypes.byref(K)))
     return c.value, p1.value, p2.value, K.value
+
+
+def ch_step_field_noalloc(C_ptr, nx, ny, L, gamma, dt, nsteps, stream_ptr=None):
+    """Advance a caller-owned FP64 device field (address C_ptr) by nsteps steps without
+    allocating anything (scratch in a static 8 MiB device array; nx*ny <= 1048576)."""
+    _check(lib().ch_step_field_noalloc(C_ptr, nx, ny, L, gamma, dt, nsteps, stream_ptr or None))
 
 
 def ch_create_ensemble(nx, ny, L, gamma, dt, C0, seed, precision=CH_FP64):

@@ -14,6 +14,11 @@
 #include "ch.h"
 #include "ch_internal.h"
 
+namespace chk {
+// Error text for ch_last_error() from other translation units of the library.
+void record_error(const char* msg);
+}
+
 using chk::MemberParams;
 using chk::MemberState;
 using chk::Tile;
@@ -118,6 +123,8 @@ int preroll_length(double p1, double p2, double tol) {
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
+
+void chk::record_error(const char* msg) { g_last_error = msg; }
 
 struct ch_ensemble {
   int precision = CH_FP64;
