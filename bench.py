@@ -37,11 +37,13 @@ METRIC = "CH grid-point-steps/s per GB300 (FP32 vs FP64 path); served p50/p99 la
 UNIT = "grid-point-steps/s"
 STEPS_PER_BENCH_STEP = 100
 FP64_PIPE_PEAK = 1.25e12  # FLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
-# Algorithmic work per grid point of one time step of this scheme (the design doc derives them):
-FLOPS_ROWS = 23.0         # mu (9) + R' (6) + forward/backward row recurrences (8)
-FLOPS_COLS = 10.0         # forward/backward column recurrences (8) + update (2)
-BYTES_ROWS = 2            # words per point: read C, write W
-BYTES_COLS = 3            # words per point: read W, read C, write C
+HBM_PEAK = 6694.5e9       # B/s, MEASURED_PEAKS.json hbm_gbs
+# Algorithmic work per grid point of one time step, per kernel (flop, field words moved):
+#   stencil  mu (9) + R' (6) flop; read C, write R'
+#   rowsweep forward/backward row recurrences (8); read R', write W
+#   rows     (fused) stencil + row recurrences (23); read C, write W
+#   cols     column recurrences (8) + update (2); read W, read C, write C
+KERNEL_WORK = {"stencil": (15.0, 2), "rowsweep": (8.0, 2), "rows": (23.0, 2), "cols": (10.0, 3)}
 
 
 # ------------------------------------------------------------------------------------------
@@ -207,21 +209,27 @@ def run_gpu_leg(ch, torch, p, prec, K, W, rank, world, dist, profile_kernels=Tru
     ms = ev0.elapsed_time(ev1)
     avg, cnt = e.beta_avg()
     out = {"ms": ms, "pts": npts * K * STEPS_PER_BENCH_STEP, "clocks": clk.summary(), "beta_avg": avg,
-           "launches": K * STEPS_PER_BENCH_STEP * 2}
+           }
+    out["tuning"] = e.tuning()
+    out["launches"] = K * STEPS_PER_BENCH_STEP * (3 if out["tuning"]["split"] else 2)
     if profile_kernels:
         # Per-kernel durations: events around each phase launch on the engine's stream,
         # over 2 sampling intervals of the same state after the timed region.
+        split = out["tuning"]["split"]
+        names = ["stencil", "rowsweep", "cols"] if split else ["rows", None, "cols"]
         reps = 2 * STEPS_PER_BENCH_STEP
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4 * reps)]
         for r in range(reps):
-            evs[3 * r].record(stream)
-            e.launch_phase(0)
-            evs[3 * r + 1].record(stream)
-            e.launch_phase(1)
-            evs[3 * r + 2].record(stream)
+            for ph in range(3):
+                evs[4 * r + ph].record(stream)
+                e.launch_phase(ph)
+            evs[4 * r + 3].record(stream)
         torch.cuda.synchronize()
-        out["ms_rows"] = sum(evs[3 * r].elapsed_time(evs[3 * r + 1]) for r in range(reps)) / reps
-        out["ms_cols"] = sum(evs[3 * r + 1].elapsed_time(evs[3 * r + 2]) for r in range(reps)) / reps
+        out["kernels"] = {}
+        for ph, name in enumerate(names):
+            if name is None:
+                continue
+            out["kernels"][name] = sum(evs[4 * r + ph].elapsed_time(evs[4 * r + ph + 1]) for r in range(reps)) / reps
     e.close()
     return out
 
@@ -369,29 +377,37 @@ def main():
         return out
 
     npts = len(p["C0"]) * p["nx"] * p["ny"]
-    rows_f = FLOPS_ROWS * npts / (r64["ms_rows"] * 1e-3)
-    cols_f = FLOPS_COLS * npts / (r64["ms_cols"] * 1e-3)
-    dom = "rows" if r64["ms_rows"] >= r64["ms_cols"] else "cols"
-    achieved = rows_f if dom == "rows" else cols_f
-    kname = "rows_kernel<double>" if dom == "rows" else "cols_kernel<double>"
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": FP64_PIPE_PEAK / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PIPE_PEAK,
-                "traffic": ncu_traffic(kname, p["name"]),
-                "peak_source": "FP64 pipe, nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz); no measured FP64 peak",
-                "ms_per_launch": {"rows": r64["ms_rows"], "cols": r64["ms_cols"]},
-                "algorithmic_flops_per_point": {"rows": FLOPS_ROWS, "cols": FLOPS_COLS},
-                "hbm_frac_of_measured": (5 * 8 * npts / ((r64["ms_rows"] + r64["ms_cols"]) * 1e-3)) / 6694.5e9}
+
+    def kernel_roofline(res, bound, elt):
+        ks = res["kernels"]
+        dom = max(ks, key=ks.get)
+        flops, words = KERNEL_WORK[dom]
+        tname = "%s_kernel<%s>" % (dom, "double" if elt == 8 else "float")
+        per_launch = {k: {"ms": v, "achieved_tflops": KERNEL_WORK[k][0] * npts / (v * 1e-3) / 1e12,
+                          "achieved_gbs": KERNEL_WORK[k][1] * elt * npts / (v * 1e-3) / 1e9} for k, v in ks.items()}
+        step_ms = sum(ks.values())
+        if bound == "alu":
+            ach = flops * npts / (ks[dom] * 1e-3)
+            rl = {"bound": "alu", "kernel": tname, "achieved": ach / 1e12, "peak": FP64_PIPE_PEAK / 1e12,
+                  "unit": "TFLOP/s", "frac": ach / FP64_PIPE_PEAK,
+                  "peak_source": "FP64 pipe, nominal 1.25 TFLOP/s of the recipe (152 SMs x 2 DFMA/clk x 2.07 GHz); "
+                                 "no measured FP64 peak in MEASURED_PEAKS.json"}
+        else:
+            ach = words * elt * npts / (ks[dom] * 1e-3)
+            rl = {"bound": "hbm", "kernel": tname, "achieved": ach / 1e9, "peak": HBM_PEAK / 1e9, "unit": "GB/s",
+                  "frac": ach / HBM_PEAK, "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)"}
+        rl["traffic"] = ncu_traffic(tname, p["name"])
+        rl["algorithmic_per_point"] = {"flop": flops, "bytes": words * elt}
+        rl["per_kernel"] = per_launch
+        rl["step_ms_sum_of_kernels"] = step_ms
+        rl["step_frac_of_16B_per_point"] = 2 * 2 * elt * npts / (step_ms * 1e-3) / HBM_PEAK
+        return rl
+
+    roofline = kernel_roofline(r64, "alu", 8)
+    roofline["tuning"] = r64["tuning"]
     if fp32 is not None:
-        hbm = 6694.5e9
-        rows_b = BYTES_ROWS * 4 * npts / (r32["ms_rows"] * 1e-3)
-        cols_b = BYTES_COLS * 4 * npts / (r32["ms_cols"] * 1e-3)
-        d32 = "rows" if r32["ms_rows"] >= r32["ms_cols"] else "cols"
-        fp32["roofline"] = {"bound": "hbm", "kernel": "%s_kernel<float>" % d32,
-                            "achieved": (rows_b if d32 == "rows" else cols_b) / 1e9, "peak": 6694.5, "unit": "GB/s",
-                            "frac": (rows_b if d32 == "rows" else cols_b) / hbm, "peak_source": "measured hbm_gbs",
-                            "traffic": ncu_traffic("%s_kernel<float>" % d32, p["name"]),
-                            "ms_per_launch": {"rows": r32["ms_rows"], "cols": r32["ms_cols"]},
-                            "step_frac_of_16B_per_point": 16 * npts / ((r32["ms_rows"] + r32["ms_cols"]) * 1e-3) / hbm}
+        fp32["roofline"] = kernel_roofline(r32, "hbm", 4)
+        fp32["roofline"]["tuning"] = r32["tuning"]
         s64, s32 = beta_stats(avg64), beta_stats(avg32)
         fp32["beta_avg_vs_fp64"] = {k: {"fp32": s32[k]["mean"], "fp64": s64[k]["mean"], "se_fp64": s64[k]["se"],
                                         "within_one_se": abs(s32[k]["mean"] - s64[k]["mean"]) <= s64[k]["se"]}

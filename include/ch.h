@@ -161,13 +161,51 @@ int ch_set_fields(ch_handle h, const double* in);
 int ch_get_fields(ch_handle h, double* out);
 
 /*
- * Launch one phase of a step for every member, on the handle's stream: phase 0 = the row
- * kernel (13-point stencil, observables on sample steps, row sweep), phase 1 = the column
- * kernel (column sweep, update, sample finalisation, step counter).  Phase 0 then phase 1
- * is exactly one ch_step(h, 1); the split exists so callers can time each kernel with
- * events on the stream.  Errors: CH_EINVAL (phase), CH_ECUDA.
+ * Launch one phase of a step for every member, on the handle's stream: phase 0 = the
+ * 13-point stencil (observables on sample steps), fused with the row sweep in the fused
+ * form; phase 1 = the row sweep in the split form (nothing in the fused form); phase 2 =
+ * the column kernel (column sweep, update, sample finalisation, step counter).  Phases 0,
+ * 1, 2 in order are exactly one ch_step(h, 1); they exist separately so callers can time
+ * each kernel with events on the stream.  Errors: CH_EINVAL (phase), CH_ECUDA.
  */
 int ch_launch_phase(ch_handle h, int phase);
+
+/*
+ * Launch shape of a handle's kernels (no effect on results beyond round-off order within
+ * a line's recurrence chunks; every choice is checked by the parity tests).  Fields <= 0
+ * (split: -1) take the precision's default.
+ *   split       1: stencil and row sweep as separate kernels (default for CH_FP64: all
+ *               threads of the stencil kernel do FP64 work, the sweeps run as many
+ *               independent recurrences per SM); 0: one fused row kernel (default for
+ *               CH_FP32: R' stays on chip, 5 words of traffic per point and step).
+ *   rows_band   rows per stencil / fused CTA (default 16 FP64, 32 FP32).
+ *   rows_p      fused form: threads per row in the row sweep (chunks pre-rolled alone).
+ *   sweep_band  split form: rows (one thread each) per row-sweep CTA (default 32).
+ *   cols_panel  columns per column CTA (default 32 FP64, 16 FP32).
+ *   cols_p      threads per column; 1 = in-place sweep with half the shared memory.
+ *   threads     threads per stencil / fused / column CTA, multiple of 32, <= 512
+ *               (default 512 FP64, 256 FP32).
+ *   stream      split form only: 1 = streaming sweeps (a warp streams 32 lines through
+ *               small double-buffered tiles or straight from global memory, the pass
+ *               intermediate kept in the scratch field), so recurrences in flight are not
+ *               limited by shared memory; 0 = whole lines resident in shared memory
+ *               (sweep_band, cols_panel, cols_p apply).  Default: 1 for CH_FP64.
+ * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
+ * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
+ * size, lines too long for shared memory).
+ */
+typedef struct {
+  int split;
+  int rows_band;
+  int rows_p;
+  int sweep_band;
+  int cols_panel;
+  int cols_p;
+  int threads;
+  int stream;
+} ch_tuning;
+int ch_set_tuning(ch_handle h, const ch_tuning* t); /* NULL restores the defaults */
+int ch_get_tuning(ch_handle h, ch_tuning* t);       /* shape in effect (member 0's values) */
 
 /* Step index n of member k (t = n dt). */
 int ch_get_step(ch_handle h, int member, int64_t* n);
@@ -180,11 +218,12 @@ int ch_num_members(ch_handle h, int* m);
 int ch_member_shape(ch_handle h, int member, int* nx, int* ny);
 
 /*
- * After a ch_step, copy member k's row-solve output W = (I + s D_x^4)^-1 R of the last
- * step, R = dt lap_h mu (the intermediate of the factorised step), into out (host,
- * ny*nx doubles).  For testing the row kernel on its own.
+ * Row-solve output of the current fields, for testing the row phase on its own: runs the
+ * stencil and row-sweep phases (not the column phase; fields, step indices and samples
+ * are unchanged) and copies member k's W = (I + s D_x^4)^-1 R, R = dt lap_h mu, into out
+ * (host, ny*nx doubles).  Synchronises.
  */
-int ch_debug_last_rows(ch_handle h, int member, double* out);
+int ch_debug_row_solve(ch_handle h, int member, double* out);
 
 /*
  * Checkpoint / resume: write or read every field, step index, sample series and

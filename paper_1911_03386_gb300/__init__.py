@@ -16,8 +16,9 @@ __all__ = [
     "CH_EBUSY", "CH_ENOTFOUND", "CH_FP64", "CH_FP32", "ChError", "MemberDesc", "lib", "lib_path",
     "ch_create_ensemble", "ch_create_batch", "ch_destroy", "ch_set_stream", "ch_set_sampling",
     "ch_step", "ch_synchronize", "ch_observables", "ch_beta_avg", "ch_series", "ch_get_field",
-    "ch_set_field", "ch_set_fields", "ch_get_fields", "ch_launch_phase", "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
-    "ch_debug_last_rows", "ch_save", "ch_load", "ch_penta_factor", "ch_step_field_noalloc", "ch_last_error", "ch_version",
+    "ch_set_field", "ch_set_fields", "ch_get_fields", "ch_launch_phase", "ch_set_tuning", "ch_get_tuning", "Tuning",
+    "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
+    "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_step_field_noalloc", "ch_last_error", "ch_version",
     "Ensemble",
 ]
 
@@ -40,6 +41,16 @@ class MemberDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("L", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("C0", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("counter_base", ctypes.c_uint64)]
+
+
+class Tuning(ctypes.Structure):
+    """ch_tuning: launch shape of a handle's kernels (fields <= 0 / split -1: default)."""
+    _fields_ = [("split", ctypes.c_int), ("rows_band", ctypes.c_int), ("rows_p", ctypes.c_int),
+                ("sweep_band", ctypes.c_int), ("cols_panel", ctypes.c_int), ("cols_p", ctypes.c_int),
+                ("threads", ctypes.c_int), ("stream", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _c_int, _c_dbl, _c_i64, _c_u64, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
@@ -65,10 +76,12 @@ _SIGS = {
     "ch_set_fields": (_c_int, [_vp, _vp]),
     "ch_get_fields": (_c_int, [_vp, _vp]),
     "ch_launch_phase": (_c_int, [_vp, _c_int]),
+    "ch_set_tuning": (_c_int, [_vp, ctypes.POINTER(Tuning)]),
+    "ch_get_tuning": (_c_int, [_vp, ctypes.POINTER(Tuning)]),
     "ch_reset": (_c_int, [_vp]),
     "ch_num_members": (_c_int, [_vp, _ip]),
     "ch_member_shape": (_c_int, [_vp, _c_int, _ip, _ip]),
-    "ch_debug_last_rows": (_c_int, [_vp, _c_int, _dp]),
+    "ch_debug_row_solve": (_c_int, [_vp, _c_int, _dp]),
     "ch_save": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_load": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_penta_factor": (_c_int, [_c_dbl, _c_int, _dp, _dp, _dp, _ip]),
@@ -236,14 +249,26 @@ def ch_launch_phase(h, phase):
     _check(lib().ch_launch_phase(h, phase))
 
 
+def ch_set_tuning(h, split=-1, rows_band=0, rows_p=0, sweep_band=0, cols_panel=0, cols_p=0, threads=0, stream=-1):
+    t = Tuning(split, rows_band, rows_p, sweep_band, cols_panel, cols_p, threads, stream)
+    _check(lib().ch_set_tuning(h, ctypes.byref(t)))
+
+
+def ch_get_tuning(h):
+    t = Tuning()
+    _check(lib().ch_get_tuning(h, ctypes.byref(t)))
+    return t.as_dict()
+
+
 def ch_reset(h):
     _check(lib().ch_reset(h))
 
 
-def ch_debug_last_rows(h, member):
+def ch_debug_row_solve(h, member):
+    """W = (I + s D_x^4)^-1 dt lap_h mu of member's current field (no state change)."""
     nx, ny = ch_member_shape(h, member)
     out = np.empty((ny, nx))
-    _check(lib().ch_debug_last_rows(h, member, _ptr(out)))
+    _check(lib().ch_debug_row_solve(h, member, _ptr(out)))
     return out
 
 
@@ -323,14 +348,20 @@ class Ensemble:
     def launch_phase(self, phase):
         ch_launch_phase(self.h, phase)
 
+    def set_tuning(self, **kw):
+        ch_set_tuning(self.h, **kw)
+
+    def tuning(self):
+        return ch_get_tuning(self.h)
+
     def step_index(self, member=0):
         return ch_get_step(self.h, member)
 
     def reset(self):
         ch_reset(self.h)
 
-    def last_rows(self, member):
-        return ch_debug_last_rows(self.h, member)
+    def row_solve(self, member):
+        return ch_debug_row_solve(self.h, member)
 
     def set_stream(self, stream_ptr):
         ch_set_stream(self.h, stream_ptr)

@@ -43,8 +43,6 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory per CTA on sm_103a
-constexpr int kRowsThreads = 256;
-constexpr int kColsThreads = 256;
 constexpr int kGraphSteps = 16;
 
 // ---------------------------------------------------------------------------------------
@@ -133,8 +131,9 @@ struct ch_ensemble {
   int device = 0;
   std::vector<MemberParams> hp;
   std::vector<MemberState> hs0;  // initial state (for reset)
-  std::vector<Tile> rt, ct;
+  std::vector<Tile> rt, st, ct;   // stencil/fused bands, row-sweep bands, column panels
   chk::LaunchShape shape{};
+  ch_tuning tuning{};             // as requested (0 / -1 = default)
   int64_t total_points = 0, max_points = 0;
   int64_t total_bands = 0;
   int every = 1;
@@ -146,7 +145,9 @@ struct ch_ensemble {
   MemberParams* dmp = nullptr;
   MemberState* dms = nullptr;
   Tile* drt = nullptr;
+  Tile* dst = nullptr;
   Tile* dct = nullptr;
+  size_t cap_rt = 0, cap_st = 0, cap_ct = 0, cap_part = 0;  // device array capacities
   double2* dpart = nullptr;
   double* dseries = nullptr;
   double* dobs = nullptr;
@@ -163,6 +164,7 @@ struct ch_ensemble {
     v.mp = dmp;
     v.ms = dms;
     v.row_tiles = drt;
+    v.sweep_tiles = dst;
     v.col_tiles = dct;
     v.partials = dpart;
     v.series = dseries;
@@ -187,6 +189,7 @@ void free_device(ch_ensemble* h) {
   cudaFree(h->dmp);
   cudaFree(h->dms);
   cudaFree(h->drt);
+  cudaFree(h->dst);
   cudaFree(h->dct);
   cudaFree(h->dpart);
   cudaFree(h->dseries);
@@ -194,7 +197,8 @@ void free_device(ch_ensemble* h) {
   h->C = h->W = nullptr;
   h->dmp = nullptr;
   h->dms = nullptr;
-  h->drt = h->dct = nullptr;
+  h->drt = h->dst = h->dct = nullptr;
+  h->cap_rt = h->cap_st = h->cap_ct = h->cap_part = 0;
   h->dpart = nullptr;
   h->dseries = h->dobs = nullptr;
 }
@@ -259,40 +263,114 @@ size_t rows_smem_bytes(int nr, int nx, size_t elt, int threads) {
   return b + (size_t)2 * (threads / 32) * sizeof(double);
 }
 
-size_t cols_smem_bytes(int nc, int ny, size_t elt) { return (size_t)2 * ny * (nc + 1) * elt; }
+size_t sweep_smem_bytes(int nr, int nx, size_t elt) { return (size_t)nr * (nx + 1) * elt; }
 
-int build_tiles(ch_ensemble* h) {
+size_t cols_smem_bytes(int nc, int ny, size_t elt, bool inplace) {
+  return (size_t)(inplace ? 1 : 2) * ny * (nc + 1) * elt;
+}
+
+int round_warps(int t) { return ((t + 31) / 32) * 32; }
+
+// Tiles and launch shapes from the tuning request (fields <= 0 take the defaults of the
+// precision: FP64 split form with one thread per line, FP32 fused form with chunked
+// sweeps).  Band heights and panel widths shrink per member until they fit the shared
+// memory; a member's tiles depend only on its size, the precision and the tuning.
+int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   const bool f64 = h->precision == CH_FP64;
-  h->rt.clear();
-  h->ct.clear();
-  h->shape.rows_threads = kRowsThreads;
-  h->shape.cols_threads = kColsThreads;
-  h->shape.rows_smem = 0;
-  h->shape.cols_smem = 0;
+  const int split = t.split >= 0 ? (t.split ? 1 : 0) : (f64 ? 1 : 0);
+  const int threads = t.threads > 0 ? t.threads : (f64 ? 512 : 256);
+  if (threads % 32 || threads > 512) return fail(CH_EINVAL, "threads must be a multiple of 32, at most 512");
+  const int want_br = t.rows_band > 0 ? t.rows_band : (f64 ? 16 : 32);
+  const int want_bs = t.sweep_band > 0 ? t.sweep_band : 32;
+  const int want_bc = t.cols_panel > 0 ? t.cols_panel : (f64 ? 32 : 16);
+  if (t.sweep_band > 512 || want_bc * std::max(1, t.cols_p) > threads || want_br * std::max(1, t.rows_p) > threads)
+    return fail(CH_EINVAL, "band/panel times threads per line exceeds the CTA size");
+  const bool inplace = t.cols_p > 0 ? t.cols_p == 1 : f64;
+  const int stream = split ? (t.stream >= 0 ? (t.stream ? 1 : 0) : (f64 ? 1 : 0)) : 0;
+  std::vector<Tile> rt, st, ct;
+  chk::LaunchShape sh{};
+  sh.split = split;
+  sh.stream = stream;
+  sh.cols_inplace = inplace ? 1 : 0;
+  sh.rows_threads = threads;
+  sh.cols_threads = threads;
+  sh.sweep_threads = 0;
   int64_t part = 0;
   for (int k = 0; k < h->m; ++k) {
     MemberParams& p = h->hp[k];
-    // rows: band height and threads per row
-    int br = std::min(p.ny, f64 ? 16 : 32);
-    while (br > 1 && rows_smem_bytes(br, p.nx, h->elt, kRowsThreads) > kSmemMax) br = (br + 1) / 2;
-    if (rows_smem_bytes(br, p.nx, h->elt, kRowsThreads) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
-    p.rows_p = f64 ? 1 : std::max(1, std::min(kRowsThreads / br, p.nx / 64));
-    // columns: panel width and threads per column
-    int bc = std::min(p.nx, f64 ? 16 : 32);
-    while (bc > 1 && cols_smem_bytes(bc, p.ny, h->elt) > kSmemMax) bc = (bc + 1) / 2;
-    if (cols_smem_bytes(bc, p.ny, h->elt) > kSmemMax) return fail(CH_EINVAL, "column too long for shared memory");
-    p.cols_p = f64 ? 1 : std::max(1, std::min(kColsThreads / bc, p.ny / 64));
+    int br = std::min(p.ny, want_br);
+    while (br > 1 && rows_smem_bytes(br, p.nx, h->elt, threads) > kSmemMax) br = (br + 1) / 2;
+    if (rows_smem_bytes(br, p.nx, h->elt, threads) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
+    p.rows_p = t.rows_p > 0 ? t.rows_p : (f64 ? 1 : std::max(1, std::min(threads / br, p.nx / 32)));
+    if (br * p.rows_p > threads) p.rows_p = std::max(1, threads / br);
+    int bs = stream ? std::min(p.ny, 32) : std::min(p.ny, want_bs);
+    while (bs > 1 && !stream && sweep_smem_bytes(bs, p.nx, h->elt) > kSmemMax) bs = (bs + 1) / 2;
+    int bc = stream ? std::min(p.nx, 32) : std::min(p.nx, want_bc);
+    while (bc > 1 && !stream && cols_smem_bytes(bc, p.ny, h->elt, inplace) > kSmemMax) bc = (bc + 1) / 2;
+    if (!stream && cols_smem_bytes(bc, p.ny, h->elt, inplace) > kSmemMax)
+      return fail(CH_EINVAL, "column too long for shared memory");
+    p.cols_p = inplace ? 1 : (t.cols_p > 0 ? t.cols_p : std::max(1, std::min(threads / bc, p.ny / 32)));
+    if (bc * p.cols_p > threads) p.cols_p = std::max(1, threads / bc);
     int b = 0;
-    for (int j0 = 0; j0 < p.ny; j0 += br, ++b) h->rt.push_back(Tile{k, j0, std::min(br, p.ny - j0), b});
+    for (int j0 = 0; j0 < p.ny; j0 += br, ++b) rt.push_back(Tile{k, j0, std::min(br, p.ny - j0), b});
     p.nbands = b;
     p.partial_base = part;
     part += b;
+    if (split) {
+      int q = 0;
+      for (int j0 = 0; j0 < p.ny; j0 += bs, ++q) st.push_back(Tile{k, j0, std::min(bs, p.ny - j0), q});
+      if (!stream) {
+        sh.sweep_smem = std::max(sh.sweep_smem, sweep_smem_bytes(bs, p.nx, h->elt));
+        sh.sweep_threads = std::max(sh.sweep_threads, std::max(128, round_warps(bs)));
+      }
+    }
     int q = 0;
-    for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) h->ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
-    h->shape.rows_smem = std::max(h->shape.rows_smem, rows_smem_bytes(br, p.nx, h->elt, kRowsThreads));
-    h->shape.cols_smem = std::max(h->shape.cols_smem, cols_smem_bytes(bc, p.ny, h->elt));
+    for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
+    sh.rows_smem = std::max(sh.rows_smem, rows_smem_bytes(br, p.nx, h->elt, threads));
+    if (!stream) sh.cols_smem = std::max(sh.cols_smem, cols_smem_bytes(bc, p.ny, h->elt, inplace));
   }
+  if (sh.sweep_threads > 512) return fail(CH_EINVAL, "row-sweep band above 512 rows");
+  sh.n_row_tiles = (int)rt.size();
+  sh.n_sweep_tiles = (int)st.size();
+  sh.n_col_tiles = (int)ct.size();
+  h->rt.swap(rt);
+  h->st.swap(st);
+  h->ct.swap(ct);
+  h->shape = sh;
   h->total_bands = part;
+  h->tuning = t;
+  return CH_OK;
+}
+
+// (Re)allocate the device tile tables and partial slots for the current tiles, upload
+// them and the member parameters.  The caller has synchronised the stream.
+int upload_tiles(ch_ensemble* h) {
+  auto ensure = [&](void** p, size_t& cap, size_t need, size_t elt) -> cudaError_t {
+    need = std::max<size_t>(need, 1);
+    if (need <= cap) return cudaSuccess;
+    cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(p, need * elt);
+    if (e == cudaSuccess) cap = need;
+    return e;
+  };
+  cudaError_t e;
+  if ((e = ensure((void**)&h->drt, h->cap_rt, h->rt.size(), sizeof(Tile))) != cudaSuccess ||
+      (e = ensure((void**)&h->dst, h->cap_st, h->st.size(), sizeof(Tile))) != cudaSuccess ||
+      (e = ensure((void**)&h->dct, h->cap_ct, h->ct.size(), sizeof(Tile))) != cudaSuccess ||
+      (e = ensure((void**)&h->dpart, h->cap_part, (size_t)h->total_bands, sizeof(double2))) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? CH_ENOMEM : CH_ECUDA, std::string("tile tables: ") + cudaGetErrorString(e));
+  }
+  CH_CUDA(cudaMemcpyAsync(h->drt, h->rt.data(), sizeof(Tile) * h->rt.size(), cudaMemcpyHostToDevice, h->stream), "tiles");
+  if (!h->st.empty())
+    CH_CUDA(cudaMemcpyAsync(h->dst, h->st.data(), sizeof(Tile) * h->st.size(), cudaMemcpyHostToDevice, h->stream), "tiles");
+  CH_CUDA(cudaMemcpyAsync(h->dct, h->ct.data(), sizeof(Tile) * h->ct.size(), cudaMemcpyHostToDevice, h->stream), "tiles");
+  CH_CUDA(cudaMemsetAsync(h->dpart, 0, sizeof(double2) * std::max<int64_t>(h->total_bands, 1), h->stream), "partials");
+  CH_CUDA(cudaMemcpyAsync(h->dmp, h->hp.data(), sizeof(MemberParams) * h->m, cudaMemcpyHostToDevice, h->stream),
+          "upload member parameters");
+  CH_CUDA(cudaStreamSynchronize(h->stream), "upload tiles");
   return CH_OK;
 }
 
@@ -340,7 +418,12 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
     h->max_points = std::max(h->max_points, np);
   }
   h->total_points = off;
-  int rc = build_tiles(h);
+  ch_tuning defaults;
+  defaults.split = -1;
+  defaults.rows_band = defaults.rows_p = defaults.sweep_band = defaults.cols_panel = defaults.cols_p = 0;
+  defaults.threads = 0;
+  defaults.stream = -1;
+  int rc = build_tiles(h, defaults);
   if (rc) {
     delete h;
     return rc;
@@ -358,9 +441,6 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
   if ((e = alloc(&h->C, h->elt * off)) != cudaSuccess || (e = alloc(&h->W, h->elt * off)) != cudaSuccess ||
       (e = alloc((void**)&h->dmp, sizeof(MemberParams) * m)) != cudaSuccess ||
       (e = alloc((void**)&h->dms, sizeof(MemberState) * m)) != cudaSuccess ||
-      (e = alloc((void**)&h->drt, sizeof(Tile) * h->rt.size())) != cudaSuccess ||
-      (e = alloc((void**)&h->dct, sizeof(Tile) * h->ct.size())) != cudaSuccess ||
-      (e = alloc((void**)&h->dpart, sizeof(double2) * h->total_bands)) != cudaSuccess ||
       (e = alloc((void**)&h->dobs, sizeof(double) * 3 * m)) != cudaSuccess) {
     free_device(h);
     cudaStreamDestroy(h->own);
@@ -369,18 +449,13 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
     return fail(e == cudaErrorMemoryAllocation ? CH_ENOMEM : CH_ECUDA,
                 std::string("device allocation: ") + cudaGetErrorString(e));
   }
-  if ((e = chk::set_kernel_smem_limits(precision, h->shape.rows_smem, h->shape.cols_smem)) != cudaSuccess ||
-      (e = cudaMemsetAsync(h->W, 0, h->elt * off, h->stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h->drt, h->rt.data(), sizeof(Tile) * h->rt.size(), cudaMemcpyHostToDevice, h->stream)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(h->dct, h->ct.data(), sizeof(Tile) * h->ct.size(), cudaMemcpyHostToDevice, h->stream)) !=
-          cudaSuccess ||
-      (e = cudaMemsetAsync(h->dpart, 0, sizeof(double2) * h->total_bands, h->stream)) != cudaSuccess) {
+  if ((e = chk::set_kernel_smem_limits(precision)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->W, 0, h->elt * off, h->stream)) != cudaSuccess) {
     int r = cuda_fail(e, "handle set-up");
     ch_destroy(h);
     return r;
   }
-  if ((rc = upload_params(h)) || (rc = reset_state(h))) {
+  if ((rc = upload_tiles(h)) || (rc = reset_state(h))) {
     ch_destroy(h);
     return rc;
   }
@@ -404,7 +479,7 @@ int check_member(ch_handle h, int member) {
 int launch_steps_direct(ch_ensemble* h, int64_t n) {
   const chk::DevView v = h->view();
   for (int64_t i = 0; i < n; ++i) {
-    cudaError_t e = chk::launch_step(v, h->precision, (int)h->rt.size(), (int)h->ct.size(), h->shape, h->stream);
+    cudaError_t e = chk::launch_step(v, h->precision, h->shape, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
   }
   return CH_OK;
@@ -418,7 +493,7 @@ int ensure_graph(ch_ensemble* h) {
   const chk::DevView v = h->view();
   cudaError_t le = cudaSuccess;
   for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i)
-    le = chk::launch_step(v, h->precision, (int)h->rt.size(), (int)h->ct.size(), h->shape, h->stream);
+    le = chk::launch_step(v, h->precision, h->shape, h->stream);
   e = cudaStreamEndCapture(h->stream, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -555,7 +630,7 @@ int ch_synchronize(ch_handle h) {
 
 int ch_observables(ch_handle h, double* F, double* dFdt, double* beta) {
   if (int rc = check_handle(h)) return rc;
-  CH_CUDA(chk::launch_observe(h->view(), h->precision, (int)h->rt.size(), h->shape, h->stream), "observe launch");
+  CH_CUDA(chk::launch_observe(h->view(), h->precision, h->shape, h->stream), "observe launch");
   std::vector<double> o(3 * (size_t)h->m);
   if (int rc = copy_out(h, o.data(), h->dobs, sizeof(double) * o.size(), "read observables")) return rc;
   bool bad = false;
@@ -690,9 +765,48 @@ int ch_get_fields(ch_handle h, double* out) {
 
 int ch_launch_phase(ch_handle h, int phase) {
   if (int rc = check_handle(h)) return rc;
-  if (phase != 0 && phase != 1) return fail(CH_EINVAL, "phase must be 0 (rows) or 1 (columns)");
-  const int n = phase == 0 ? (int)h->rt.size() : (int)h->ct.size();
-  CH_CUDA(chk::launch_phase(h->view(), h->precision, phase, n, h->shape, h->stream), "phase launch");
+  if (phase < 0 || phase > 2) return fail(CH_EINVAL, "phase must be 0, 1 or 2");
+  CH_CUDA(chk::launch_phase(h->view(), h->precision, phase, h->shape, h->stream), "phase launch");
+  return CH_OK;
+}
+
+int ch_set_tuning(ch_handle h, const ch_tuning* t) {
+  if (int rc = check_handle(h)) return rc;
+  ch_tuning req;
+  if (t) {
+    req = *t;
+  } else {
+    req.split = -1;
+    req.rows_band = req.rows_p = req.sweep_band = req.cols_panel = req.cols_p = req.threads = 0;
+    req.stream = -1;
+  }
+  if (req.rows_band < 0 || req.rows_p < 0 || req.sweep_band < 0 || req.cols_panel < 0 || req.cols_p < 0 ||
+      req.threads < 0 || req.split < -1 || req.split > 1 || req.stream < -1 || req.stream > 1)
+    return fail(CH_EINVAL, "tuning fields must be >= 0 (split, stream: -1, 0 or 1)");
+  CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
+  const std::vector<MemberParams> saved = h->hp;
+  const ch_tuning old = h->tuning;
+  if (int rc = build_tiles(h, req)) {
+    h->hp = saved;
+    build_tiles(h, old);
+    return rc;
+  }
+  drop_graph(h);
+  return upload_tiles(h);
+}
+
+int ch_get_tuning(ch_handle h, ch_tuning* t) {
+  if (int rc = check_handle(h)) return rc;
+  if (!t) return fail(CH_EINVAL, "t is NULL");
+  // the shape in effect, with per-member values of member 0
+  t->split = h->shape.split;
+  t->rows_band = h->rt.empty() ? 0 : h->rt[0].count;
+  t->rows_p = h->hp[0].rows_p;
+  t->sweep_band = h->st.empty() ? 0 : h->st[0].count;
+  t->cols_panel = h->ct.empty() ? 0 : h->ct[0].count;
+  t->cols_p = h->hp[0].cols_p;
+  t->threads = h->shape.rows_threads;
+  t->stream = h->shape.stream;
   return CH_OK;
 }
 
@@ -725,9 +839,12 @@ int ch_member_shape(ch_handle h, int member, int* nx, int* ny) {
   return CH_OK;
 }
 
-int ch_debug_last_rows(ch_handle h, int member, double* out) {
+int ch_debug_row_solve(ch_handle h, int member, double* out) {
   if (int rc = check_member(h, member)) return rc;
   if (!out) return fail(CH_EINVAL, "out is NULL");
+  // phases 0 and 1 only touch W, the band partials and the members' active flags
+  CH_CUDA(chk::launch_phase(h->view(), h->precision, 0, h->shape, h->stream), "row phase");
+  CH_CUDA(chk::launch_phase(h->view(), h->precision, 1, h->shape, h->stream), "row phase");
   const MemberParams& p = h->hp[member];
   const int64_t np = (int64_t)p.nx * p.ny;
   const double scale = p.dt / (p.hx * p.hx * p.cx);

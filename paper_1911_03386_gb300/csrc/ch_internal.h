@@ -5,7 +5,8 @@
 //               MemberParams::offset (elements), FP64 or FP32 by the handle's precision;
 //   members     MemberParams[m]   constants of each run (read-only after creation);
 //   state       MemberState[m]    step index, horizon, sampling accumulators;
-//   row_tiles   Tile[]            one CTA of the row kernel per tile (a band of rows);
+//   row_tiles   Tile[]            one CTA of the stencil (or fused row) kernel per band of rows;
+//   sweep_tiles Tile[]            one CTA of the row-sweep kernel per band (split form);
 //   col_tiles   Tile[]            one CTA of the column kernel per tile (a column panel);
 //   partials    double2[]         FP64 (sum F density, sum dF/dt density) per row band;
 //   series      double[m][cap][4] ring of (t, F, dF/dt, beta) samples per member.
@@ -68,6 +69,7 @@ struct DevView {
   const MemberParams* mp;
   MemberState* ms;
   const Tile* row_tiles;
+  const Tile* sweep_tiles;
   const Tile* col_tiles;
   double2* partials;
   double* series;
@@ -77,20 +79,24 @@ struct DevView {
 
 // Launch shapes chosen on the host per handle (see ch_api.cu).
 struct LaunchShape {
-  int rows_threads;      // threads per row-kernel CTA
-  size_t rows_smem;      // dynamic shared memory of the row kernel (max over tiles)
+  int split;             // 1: stencil_kernel + rowsweep_kernel, 0: fused rows_kernel
+  int stream;            // 1 (split only): rowstream_kernel + colstream_kernel, 32-line tiles
+  int cols_inplace;      // 1: cols_kernel<T, true> (one thread per column)
+  int n_row_tiles, n_sweep_tiles, n_col_tiles;
+  int rows_threads;      // threads per stencil / fused CTA
+  size_t rows_smem;      // dynamic shared memory (max over tiles)
+  int sweep_threads;
+  size_t sweep_smem;
   int cols_threads;
   size_t cols_smem;
 };
 
 // Kernel launchers (ch_kernels.cu).  Each returns the launch status.
 cudaError_t launch_init_fields(const DevView& v, int precision, int64_t max_points, cudaStream_t st);
-cudaError_t launch_step(const DevView& v, int precision, int n_row_tiles, int n_col_tiles,
-                        const LaunchShape& sh, cudaStream_t st);
-cudaError_t launch_phase(const DevView& v, int precision, int phase, int n_tiles, const LaunchShape& sh,
-                         cudaStream_t st);
-cudaError_t launch_observe(const DevView& v, int precision, int n_row_tiles,
-                           const LaunchShape& sh, cudaStream_t st);
-cudaError_t set_kernel_smem_limits(int precision, size_t rows_smem, size_t cols_smem);
+// One step = phases 0 (stencil or fused rows), 1 (row sweep, split form only), 2 (columns).
+cudaError_t launch_step(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st);
+cudaError_t launch_phase(const DevView& v, int precision, int phase, const LaunchShape& sh, cudaStream_t st);
+cudaError_t launch_observe(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st);
+cudaError_t set_kernel_smem_limits(int precision);
 
 }  // namespace chk

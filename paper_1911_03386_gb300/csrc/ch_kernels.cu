@@ -1,21 +1,32 @@
 // ch_kernels.cu -- sm_103a kernels of one Cahn-Hilliard step (delta-form factorised ADI).
 //
-// One step of every member is two launches:
-//   rows_kernel  (one CTA per band of rows of one member)
-//     C rows j0-2 .. j0+nr+1  --(smem)-->  mu = C^3 - C - gamma lap_h C  on rows j0-1..j0+nr
-//     [sample steps] FP64 partial sums of the F and dF/dt densities (Sec. 1 Eq. (4))
-//     R' = scaled dt lap_h mu (the 13-point explicit right-hand side, Sec. 1 Eq. (3))
-//     row sweep  W' = Q_x^-T Q_x^-1 R'  (cyclic, pre-rolled second-order recurrences)
-//     W' rows --> global scratch W
-//   cols_kernel  (one CTA per panel of columns of one member)
-//     W' panel --(smem)--> column sweep  Z = Q_y^-T Q_y^-1 W'  -->  C += kappa Z
-//     [panel 0] finalise the member's sample (F, dF/dt, beta, window average) and
-//     advance its step counter.
+// A step of every member is one of two launch sequences (chosen per handle):
+//
+//   fused   rows_kernel   C rows (+2 halo) --smem--> mu --> R' --> row sweep --> W
+//           cols_kernel   W panel --smem--> column sweep --> C += kappa Z
+//   split   stencil_kernel   C rows (+2 halo) --smem--> mu --> R' --> W (global)
+//           rowsweep_kernel  W rows --smem--> row sweep in place --> W
+//           cols_kernel      as above
+//
+// rows_kernel keeps R' on chip (5 words of traffic per point and step: read C, write W,
+// read W, read C, write C), the bandwidth-lean form used for FP32.  The split form moves
+// two more words (R' written and read back) but lets every thread of the stencil kernel
+// do FP64 work and lets the row sweeps run as many full warps of independent recurrences
+// per SM: the form used for FP64, which is bound by GB300's FP64 pipe (2 DFMA per SM per
+// clock), not by HBM.
+//
+//   mu = C^3 - C - gamma lap_h C = C (C^2 - a) - bx (Ce + Cw) - by (Cn + Cs)
+//   R' = (mu_e + mu_w) + rho (mu_n + mu_s) + w0 mu       (R = dt lap_h mu = dt/hx^2 R')
+//
+// On sample steps the stencil phase also writes FP64 partial sums of the F and dF/dt
+// densities (Sec. 1 Eq. (4)) per row band, and the column kernel's panel-0 CTA of each
+// member reduces them in fixed order into F, dF/dt, beta (Eq. (6)) and the beta window
+// average, then advances the member's step counter.
 //
 // The cyclic solve.  I + s D^4 (stencil [s, -4s, 1+6s, -4s, s], periodic) factors as
 // c Q Q^T with Q the circulant of q(z) = 1 - p1 z - p2 z^2 whose roots lie outside the
-// unit circle (spectral factorisation; the host computes p1, p2, c in FP64 as the fixed
-// point of the band LDL^T recurrences).  Q y = r is the periodic recurrence
+// unit circle (spectral factorisation, computed on the host in FP64).  Q y = r is the
+// periodic recurrence
 //     y_i = r_i + p1 y_{i-1} + p2 y_{i-2}      (i mod n),
 // Q^T x = y the same recurrence run backwards.  Its impulse response decays like
 // |root|^-k, so the periodic solution at i equals the recurrence started from a zero
@@ -24,8 +35,9 @@
 // powers of the companion matrix.  A thread that owns the chunk [c0, c1) of a line
 // therefore needs nothing from the other threads: it pre-rolls over the K points before
 // c0 (forward) or after c1 (backward).  This costs 2 FMA per point per pass plus 2K per
-// chunk, against ~9 FMA per point for a band LDL^T + Woodbury corner correction, which
-// matters because the FP64 path is bound by the FP64 pipe on GB300.
+// chunk, against ~9 FMA per point for a band LDL^T + Woodbury corner correction.  With
+// one chunk per line the sweep can run in place (the pre-roll reads precede every write
+// they depend on).
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -61,6 +73,39 @@ __global__ void init_fields_kernel(DevView v) {
       const double noise = __dmul_rn(0.1, __dsub_rn(__dmul_rn(2.0, u), 1.0));
       C[p] = (T)__dadd_rn(P.C0, noise);
     }
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, element-sized), so that a CTA has all
+// of its tile's loads in flight at once.
+// -------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Rows j_first .. j_first+nrows-1 (periodic in j) of an ny x nx field -> shared rows of
+// pitch ld, one warp per row.  The caller waits (cp_async_wait_all + __syncthreads).
+template <typename T>
+__device__ __forceinline__ void load_rows_async(T* dst, int ld, const T* __restrict__ field, int nx, int ny,
+                                                int j_first, int nrows) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int r = warp; r < nrows; r += nwarps) {
+    int j = j_first + r;
+    if (j < 0) j += ny;
+    if (j >= ny) j -= ny;
+    const T* src = field + (int64_t)j * nx;
+    T* d = dst + (size_t)r * ld;
+    for (int i = lane; i < nx; i += 32) cp_async_elem(d + i, src + i);
   }
 }
 
@@ -106,11 +151,12 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 }
 
 // Forward recurrence y_i = r_i + p1 y_{i-1} + p2 y_{i-2} on the chunk [c0, c1) of a
-// periodic line of n points stored with element stride `es` starting at `in`; the state
-// is pre-rolled from zero over the K points before c0 (cyclically).
+// periodic line of n points stored with element stride `es`; the state is pre-rolled
+// from zero over the K points before c0 (cyclically).  `in` and `out` may be the same
+// line when [c0, c1) is the whole line.
 template <typename T>
-__device__ __forceinline__ void sweep_forward(const T* __restrict__ in, T* __restrict__ out,
-                                              int es, int n, int c0, int c1, int K, T p1, T p2) {
+__device__ __forceinline__ void sweep_forward(const T* in, T* out, int es, int n, int c0, int c1, int K, T p1,
+                                              T p2) {
   T y1 = T(0), y2 = T(0);
   int k = wrap_index(c0 - K, n);
   for (int q = 0; q < K; ++q) {
@@ -128,10 +174,10 @@ __device__ __forceinline__ void sweep_forward(const T* __restrict__ in, T* __res
 }
 
 // Backward recurrence x_i = y_i + p1 x_{i+1} + p2 x_{i+2} on [c0, c1), pre-rolled over the
-// K points after c1 (cyclically).
+// K points after c1 (cyclically).  In place allowed for a whole line, as above.
 template <typename T>
-__device__ __forceinline__ void sweep_backward(const T* __restrict__ in, T* __restrict__ out,
-                                               int es, int n, int c0, int c1, int K, T p1, T p2) {
+__device__ __forceinline__ void sweep_backward(const T* in, T* out, int es, int n, int c0, int c1, int K, T p1,
+                                               T p2) {
   T x1 = T(0), x2 = T(0);
   int k = wrap_index(c1 - 1 + K, n);
   for (int q = 0; q < K; ++q) {
@@ -148,11 +194,127 @@ __device__ __forceinline__ void sweep_backward(const T* __restrict__ in, T* __re
   }
 }
 
+// mu on nrows rows: Ms row r <- C tile row r+1 (C tile rows r .. r+2 are read).
+template <typename T>
+__device__ __forceinline__ void compute_mu(const T* Cs, T* Ms, int ld, int nx, int nrows, T a, T bx, T by) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int r = warp; r < nrows; r += nwarps) {
+    const T* c0 = Cs + (size_t)(r + 1) * ld;
+    const T* cm = c0 - ld;
+    const T* cp = c0 + ld;
+    T* mrow = Ms + (size_t)r * ld;
+    for (int i = lane; i < nx; i += 32) {
+      const int ie = (i + 1 == nx) ? 0 : i + 1;
+      const int iw = (i == 0) ? nx - 1 : i - 1;
+      const T c = c0[i];
+      const T u = c * fma(c, c, -a);
+      mrow[i] = fma(-by, cp[i] + cm[i], fma(-bx, c0[ie] + c0[iw], u));
+    }
+  }
+}
+
+// FP64 partial sums of the F and dF/dt densities over the band's nr rows (C tile rows
+// 2..nr+1, mu rows 1..nr), reduced in fixed order; thread 0 stores them.
+template <typename T>
+__device__ __forceinline__ void band_partials(const T* Cs, const T* Ms, int ld, int nx, int nr, const MemberParams& P,
+                                              double2* slot, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  double sF = 0.0, sD = 0.0;
+  const double hxi = 1.0 / P.hx, hyi = 1.0 / P.hy, hg = 0.5 * P.gamma;
+  for (int r = warp; r < nr; r += nwarps) {
+    const T* c0 = Cs + (size_t)(r + 2) * ld;
+    const T* cp = c0 + ld;
+    const T* m0 = Ms + (size_t)(r + 1) * ld;
+    const T* mp = m0 + ld;
+    for (int i = lane; i < nx; i += 32) {
+      const int ie = (i + 1 == nx) ? 0 : i + 1;
+      const double c = (double)c0[i];
+      const double gx = ((double)c0[ie] - c) * hxi;
+      const double gy = ((double)cp[i] - c) * hyi;
+      const double w = c * c - 1.0;
+      sF += 0.25 * w * w + hg * (gx * gx + gy * gy);
+      double mu, mue, mun;
+      if (sizeof(T) == sizeof(double)) {
+        mu = (double)m0[i];
+        mue = (double)m0[ie];
+        mun = (double)mp[i];
+      } else {
+        mu = mu64_at(Cs, ld, r + 2, i, nx, P.a, P.bx, P.by);
+        mue = mu64_at(Cs, ld, r + 2, ie, nx, P.a, P.bx, P.by);
+        mun = mu64_at(Cs, ld, r + 3, i, nx, P.a, P.bx, P.by);
+      }
+      const double mx = (mue - mu) * hxi;
+      const double my = (mun - mu) * hyi;
+      sD += mx * mx + my * my;
+    }
+  }
+  block_sum2(sF, sD, red);
+  if (threadIdx.x == 0) *slot = make_double2(sF, sD);
+}
+
+// R' of one grid point from the mu tile (row pointer m0 = band row r + 1).
+template <typename T>
+__device__ __forceinline__ T rprime_at(const T* m0, int ld, int i, int nx, T rho, T w0) {
+  const int ie = (i + 1 == nx) ? 0 : i + 1;
+  const int iw = (i == 0) ? nx - 1 : i - 1;
+  return fma(w0, m0[i], fma(rho, m0[i + ld] + m0[i - ld], m0[ie] + m0[iw]));
+}
+
+// Active flag and sample decision of a stencil-phase CTA.
+__device__ __forceinline__ bool stencil_prologue(const Tile& tl, MemberState* st, const MemberParams& P, bool& sample) {
+  const bool active = st->remaining > 0;
+  if (tl.index == 0 && threadIdx.x == 0) st->active = active ? 1 : 0;
+  sample = (st->step % P.every) == 0;
+  return active;
+}
+
+__device__ __forceinline__ double* red_buffer(unsigned char* smem, size_t tile_bytes) {
+  return reinterpret_cast<double*>(smem + ((tile_bytes + 15) & ~(size_t)15));
+}
+
+// Sample finalisation of one member (called once per member and step by the column phase,
+// after the stencil phase wrote the band partials): F, dF/dt, beta, series, window
+// average; then the step counter and horizon advance.
+__device__ __forceinline__ void finalize_sample(const DevView& v, int member, MemberState* st, const MemberParams& P) {
+  const int64_t n = st->step;
+  if (n % P.every == 0) {
+    double sF = 0.0, sD = 0.0;
+    for (int b = 0; b < P.nbands; ++b) {
+      const double2 pr = v.partials[P.partial_base + b];
+      sF += pr.x;
+      sD += pr.y;
+    }
+    const double hh = P.hx * P.hy;
+    const double F = hh * sF;
+    const double dFdt = -(hh * sD);
+    const double t = (double)n * P.dt;
+    const double beta = -(t / F) * dFdt;
+    st->F = F;
+    st->dFdt = dFdt;
+    st->beta = beta;
+    if (!isfinite(F) || !isfinite(dFdt)) st->nonfinite = 1;
+    if (P.series_cap > 0) {
+      double* s = v.series + ((size_t)member * P.series_cap + (size_t)(st->nsamples % P.series_cap)) * 4;
+      s[0] = t;
+      s[1] = F;
+      s[2] = dFdt;
+      s[3] = beta;
+    }
+    st->nsamples += 1;
+    if (t >= P.t1) {
+      st->beta_sum += beta;
+      st->beta_count += 1;
+    }
+  }
+  st->step = n + 1;
+  if (st->remaining != kUnbounded) st->remaining -= 1;
+}
+
 // -------------------------------------------------------------------------------------
-// Row kernel: stencil + observables + row sweep for a band of rows of one member.
-// Shared memory: Cs = (nr+4) rows of C (halo 2), Ms = (nr+2) rows of mu, row pitch nx+1,
-// then a small FP64 reduction buffer.  Cs is reused for R' and then for W', Ms for the
-// forward-sweep output.
+// Fused row kernel: stencil + observables + row sweep for a band of rows of one member.
+// Shared memory: Cs = (nr+4) rows of C (halo 2), Ms = (nr+2) rows of mu, pitch nx+1, then
+// the FP64 reduction buffer.  Cs is reused for R' and then for W', Ms for the forward
+// sweep output.
 // -------------------------------------------------------------------------------------
 template <typename T, bool OBS_ONLY>
 __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
@@ -161,108 +323,36 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
   const MemberParams& P = v.mp[tl.member];
   MemberState* st = v.ms + tl.member;
   bool sample = true;
-  if (!OBS_ONLY) {
-    const bool active = st->remaining > 0;
-    if (tl.index == 0 && threadIdx.x == 0) st->active = active ? 1 : 0;
-    if (!active) return;
-    sample = (st->step % P.every) == 0;
-  }
+  if (!OBS_ONLY && !stencil_prologue(tl, st, P, sample)) return;
   const int nx = P.nx, ny = P.ny, j0 = tl.start, nr = tl.count;
   const int ld = nx + 1;
   T* Cs = reinterpret_cast<T*>(smem);
   T* Ms = Cs + (size_t)(nr + 4) * ld;
-  double* red = reinterpret_cast<double*>(
-      smem + ((((size_t)(2 * nr + 6) * ld * sizeof(T)) + 15) & ~(size_t)15));
+  double* red = red_buffer(smem, (size_t)(2 * nr + 6) * ld * sizeof(T));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-  // 1. C rows j0-2 .. j0+nr+1 (periodic in j), one warp per row, coalesced.
-  {
-    const T* __restrict__ C = static_cast<const T*>(v.C) + P.offset;
-    for (int r = warp; r < nr + 4; r += nwarps) {
-      int j = j0 - 2 + r;
-      if (j < 0) j += ny;
-      if (j >= ny) j -= ny;
-      const T* src = C + (int64_t)j * nx;
-      T* dst = Cs + (size_t)r * ld;
-      for (int i = lane; i < nx; i += 32) dst[i] = src[i];
-    }
-  }
+  load_rows_async<T>(Cs, ld, static_cast<const T*>(v.C) + P.offset, nx, ny, j0 - 2, nr + 4);
+  cp_async_wait_all();
   __syncthreads();
-
-  // 2. mu on rows j0-1 .. j0+nr  (Ms row r <-> Cs row r+1).
-  {
-    const T a = (T)P.a, bx = (T)P.bx, by = (T)P.by;
-    for (int r = warp; r < nr + 2; r += nwarps) {
-      const T* c0 = Cs + (size_t)(r + 1) * ld;
-      const T* cm = c0 - ld;
-      const T* cp = c0 + ld;
-      T* mrow = Ms + (size_t)r * ld;
-      for (int i = lane; i < nx; i += 32) {
-        const int ie = (i + 1 == nx) ? 0 : i + 1;
-        const int iw = (i == 0) ? nx - 1 : i - 1;
-        const T c = c0[i];
-        const T u = c * fma(c, c, -a);
-        mrow[i] = fma(-by, cp[i] + cm[i], fma(-bx, c0[ie] + c0[iw], u));
-      }
-    }
-  }
+  compute_mu<T>(Cs, Ms, ld, nx, nr + 2, (T)P.a, (T)P.bx, (T)P.by);
   __syncthreads();
-
-  // 3. Sample steps: FP64 partial sums of the F and dF/dt densities over the band's rows.
   if (sample) {
-    double sF = 0.0, sD = 0.0;
-    const double hxi = 1.0 / P.hx, hyi = 1.0 / P.hy, hg = 0.5 * P.gamma;
-    for (int r = warp; r < nr; r += nwarps) {
-      const T* c0 = Cs + (size_t)(r + 2) * ld;
-      const T* cp = c0 + ld;
-      const T* m0 = Ms + (size_t)(r + 1) * ld;
-      const T* mp = m0 + ld;
-      for (int i = lane; i < nx; i += 32) {
-        const int ie = (i + 1 == nx) ? 0 : i + 1;
-        const double c = (double)c0[i];
-        const double gx = ((double)c0[ie] - c) * hxi;
-        const double gy = ((double)cp[i] - c) * hyi;
-        const double w = c * c - 1.0;
-        sF += 0.25 * w * w + hg * (gx * gx + gy * gy);
-        double mu, mue, mun;
-        if (sizeof(T) == sizeof(double)) {
-          mu = (double)m0[i];
-          mue = (double)m0[ie];
-          mun = (double)mp[i];
-        } else {
-          mu = mu64_at(Cs, ld, r + 2, i, nx, P.a, P.bx, P.by);
-          mue = mu64_at(Cs, ld, r + 2, ie, nx, P.a, P.bx, P.by);
-          mun = mu64_at(Cs, ld, r + 3, i, nx, P.a, P.bx, P.by);
-        }
-        const double mx = (mue - mu) * hxi;
-        const double my = (mun - mu) * hyi;
-        sD += mx * mx + my * my;
-      }
-    }
-    block_sum2(sF, sD, red);
-    if (threadIdx.x == 0) v.partials[P.partial_base + tl.index] = make_double2(sF, sD);
+    band_partials<T>(Cs, Ms, ld, nx, nr, P, v.partials + P.partial_base + tl.index, red);
     __syncthreads();
   }
   if (OBS_ONLY) return;
 
-  // 4. R' = (mu_e + mu_w) + rho (mu_n + mu_s) + w0 mu on rows j0 .. j0+nr-1 -> Cs rows 0..
   {
     const T rho = (T)P.rho, w0 = (T)P.w0;
     for (int r = warp; r < nr; r += nwarps) {
       const T* m0 = Ms + (size_t)(r + 1) * ld;
-      const T* mm = m0 - ld;
-      const T* mp = m0 + ld;
       T* out = Cs + (size_t)r * ld;
-      for (int i = lane; i < nx; i += 32) {
-        const int ie = (i + 1 == nx) ? 0 : i + 1;
-        const int iw = (i == 0) ? nx - 1 : i - 1;
-        out[i] = fma(w0, m0[i], fma(rho, mp[i] + mm[i], m0[ie] + m0[iw]));
-      }
+      for (int i = lane; i < nx; i += 32) out[i] = rprime_at<T>(m0, ld, i, nx, rho, w0);
     }
   }
   __syncthreads();
 
-  // 5. Row sweep: sweep_p threads per row, each owning a chunk of the row.
+  // Row sweep: rows_p threads per row, each owning a chunk of the row.
   const int sweep_p = P.rows_p;
   const int nsweep = nr * sweep_p;
   const int chunk = (nx + sweep_p - 1) / sweep_p;
@@ -276,7 +366,6 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
   if (sweeper) sweep_backward<T>(Ms + (size_t)row * ld, Cs + (size_t)row * ld, 1, nx, c0, c1, P.kx, p1, p2);
   __syncthreads();
 
-  // 6. W' rows -> global scratch.
   {
     T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
     for (int r = warp; r < nr; r += nwarps) {
@@ -288,10 +377,77 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
 }
 
 // -------------------------------------------------------------------------------------
-// Column kernel: column sweep and update for a panel of columns of one member.
-// Shared memory: Ws and Ys, ny rows of nc+1 elements each.
+// Split form, kernel 1: stencil + observables of a band, R' written to the W scratch.
 // -------------------------------------------------------------------------------------
 template <typename T>
+__global__ void __launch_bounds__(512) stencil_kernel(DevView v) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tile tl = v.row_tiles[blockIdx.x];
+  const MemberParams& P = v.mp[tl.member];
+  MemberState* st = v.ms + tl.member;
+  bool sample = true;
+  if (!stencil_prologue(tl, st, P, sample)) return;
+  const int nx = P.nx, ny = P.ny, j0 = tl.start, nr = tl.count;
+  const int ld = nx + 1;
+  T* Cs = reinterpret_cast<T*>(smem);
+  T* Ms = Cs + (size_t)(nr + 4) * ld;
+  double* red = red_buffer(smem, (size_t)(2 * nr + 6) * ld * sizeof(T));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+
+  load_rows_async<T>(Cs, ld, static_cast<const T*>(v.C) + P.offset, nx, ny, j0 - 2, nr + 4);
+  cp_async_wait_all();
+  __syncthreads();
+  compute_mu<T>(Cs, Ms, ld, nx, nr + 2, (T)P.a, (T)P.bx, (T)P.by);
+  __syncthreads();
+  if (sample) band_partials<T>(Cs, Ms, ld, nx, nr, P, v.partials + P.partial_base + tl.index, red);
+
+  T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
+  const T rho = (T)P.rho, w0 = (T)P.w0;
+  for (int r = warp; r < nr; r += nwarps) {
+    const T* m0 = Ms + (size_t)(r + 1) * ld;
+    T* dst = W + (int64_t)(j0 + r) * nx;
+    for (int i = lane; i < nx; i += 32) dst[i] = rprime_at<T>(m0, ld, i, nx, rho, w0);
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// Split form, kernel 2: row sweep of a band of rows, one thread per row, in place in
+// shared memory (pitch nx+1).
+// -------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) rowsweep_kernel(DevView v) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tile tl = v.sweep_tiles[blockIdx.x];
+  if (!v.ms[tl.member].active) return;
+  const MemberParams& P = v.mp[tl.member];
+  const int nx = P.nx, j0 = tl.start, nr = tl.count;
+  const int ld = nx + 1;
+  T* Bs = reinterpret_cast<T*>(smem);
+  T* W = static_cast<T*>(v.W) + P.offset;
+  load_rows_async<T>(Bs, ld, W, nx, P.ny, j0, nr);
+  cp_async_wait_all();
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    T* line = Bs + (size_t)threadIdx.x * ld;
+    const T p1 = (T)P.p1x, p2 = (T)P.p2x;
+    sweep_forward<T>(line, line, 1, nx, 0, nx, P.kx, p1, p2);
+    sweep_backward<T>(line, line, 1, nx, 0, nx, P.kx, p1, p2);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int r = warp; r < nr; r += nwarps) {
+    const T* src = Bs + (size_t)r * ld;
+    T* dst = W + (int64_t)(j0 + r) * nx;
+    for (int i = lane; i < nx; i += 32) dst[i] = src[i];
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// Column kernel: column sweep and update for a panel of columns of one member.
+// Shared memory: Ws (and Ys unless INPLACE), ny rows of nc+1 elements each.  INPLACE
+// needs one thread per column (cols_p == 1).
+// -------------------------------------------------------------------------------------
+template <typename T, bool INPLACE>
 __global__ void __launch_bounds__(512) cols_kernel(DevView v) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Tile tl = v.col_tiles[blockIdx.x];
@@ -301,18 +457,19 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v) {
   const int nx = P.nx, ny = P.ny, i0 = tl.start, nc = tl.count;
   const int ldc = nc + 1;
   T* Ws = reinterpret_cast<T*>(smem);
-  T* Ys = Ws + (size_t)ny * ldc;
+  T* Ys = INPLACE ? Ws : Ws + (size_t)ny * ldc;
 
   {
     const T* __restrict__ W = static_cast<const T*>(v.W) + P.offset;
     for (int idx = threadIdx.x; idx < ny * nc; idx += blockDim.x) {
       const int j = idx / nc, c = idx - j * nc;
-      Ws[(size_t)j * ldc + c] = W[(int64_t)j * nx + i0 + c];
+      cp_async_elem(Ws + (size_t)j * ldc + c, W + (int64_t)j * nx + i0 + c);
     }
+    cp_async_wait_all();
   }
   __syncthreads();
 
-  const int sweep_p = P.cols_p;
+  const int sweep_p = INPLACE ? 1 : P.cols_p;
   const int nsweep = nc * sweep_p;
   const int chunk = (ny + sweep_p - 1) / sweep_p;
   const int col = threadIdx.x % nc;
@@ -321,7 +478,7 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v) {
   const bool sweeper = threadIdx.x < nsweep && c0 < c1;
   const T p1 = (T)P.p1y, p2 = (T)P.p2y;
   if (sweeper) sweep_forward<T>(Ws + col, Ys + col, ldc, ny, c0, c1, P.ky, p1, p2);
-  __syncthreads();
+  if (!INPLACE) __syncthreads();
   if (sweeper) sweep_backward<T>(Ys + col, Ws + col, ldc, ny, c0, c1, P.ky, p1, p2);
   __syncthreads();
 
@@ -335,42 +492,160 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v) {
     }
   }
 
-  // Panel 0 finalises the member's sample of this step (partials written by the row
-  // kernel of the same step) and advances the member's step counter.  No other CTA of
+  // Panel 0 finalises the member's sample of this step (partials written by the stencil
+  // phase of the same step) and advances the member's step counter.  No other CTA of
   // this launch reads or writes the member's state.
-  if (tl.index == 0 && threadIdx.x == 0) {
-    const int64_t n = st->step;
-    if (n % P.every == 0) {
-      double sF = 0.0, sD = 0.0;
-      for (int b = 0; b < P.nbands; ++b) {
-        const double2 pr = v.partials[P.partial_base + b];
-        sF += pr.x;
-        sD += pr.y;
-      }
-      const double hh = P.hx * P.hy;
-      const double F = hh * sF;
-      const double dFdt = -(hh * sD);
-      const double t = (double)n * P.dt;
-      const double beta = -(t / F) * dFdt;
-      st->F = F;
-      st->dFdt = dFdt;
-      st->beta = beta;
-      if (!isfinite(F) || !isfinite(dFdt)) st->nonfinite = 1;
-      if (P.series_cap > 0) {
-        double* s = v.series + ((size_t)tl.member * P.series_cap + (size_t)(st->nsamples % P.series_cap)) * 4;
-        s[0] = t;
-        s[1] = F;
-        s[2] = dFdt;
-        s[3] = beta;
-      }
-      st->nsamples += 1;
-      if (t >= P.t1) {
-        st->beta_sum += beta;
-        st->beta_count += 1;
+  if (tl.index == 0 && threadIdx.x == 0) finalize_sample(v, tl.member, st, P);
+}
+
+// -------------------------------------------------------------------------------------
+// Streaming sweeps (split form).  Lines are not held on chip: each warp owns 32 lines (one
+// per lane) and streams them, so the number of recurrences in flight per SM is bounded by
+// registers rather than by shared memory.  The intermediate y of the two-pass solve lives
+// in the W scratch (in place: W holds R' -> y -> W' in the row sweep, W' -> y in the
+// column sweep).  Pre-roll reads of a pass always precede that pass's writes to the same
+// elements: the forward pass pre-rolls over the line's end and writes front to back; the
+// backward pass pre-rolls over the line's start and writes back to front.
+// -------------------------------------------------------------------------------------
+constexpr int kStreamWarps = 4;  // warps per CTA of the streaming sweeps
+constexpr int kUnroll = 8;       // loads issued ahead of the recurrence in the column sweep
+
+constexpr size_t rowstream_smem_bytes(size_t elt) { return (size_t)kStreamWarps * 2 * 32 * 33 * elt; }
+
+// Sequence position q of a pass -> column/row index: positions 0..K-1 are the pre-roll,
+// K..K+n-1 the line itself.  Forward: pre-roll over indices -K..-1 (mod n), then 0..n-1.
+// Backward: pre-roll over n-1+K..n (mod n), then n-1..0.
+__device__ __forceinline__ int fwd_index(int q, int K, int n) { return q < K ? wrap_index(q - K, n) : q - K; }
+__device__ __forceinline__ int bwd_index(int q, int K, int n) {
+  return q < K ? wrap_index(n - 1 + K - q, n) : n - 1 - (q - K);
+}
+
+// Column sweep + update, one thread per column, straight from global memory (a warp reads
+// 32 consecutive elements of a row per access).  Tiles: 32-column groups; kStreamWarps
+// groups per CTA.
+template <typename T>
+__global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v, int ntiles) {
+  const int wt = blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
+  if (wt >= ntiles) return;
+  const Tile tl = v.col_tiles[wt];
+  MemberState* st = v.ms + tl.member;
+  if (!st->active) return;
+  const MemberParams& P = v.mp[tl.member];
+  const int lane = threadIdx.x & 31;
+  const int nx = P.nx, ny = P.ny, K = P.ky;
+  if (lane < tl.count) {
+    T* Wc = static_cast<T*>(v.W) + P.offset + tl.start + lane;
+    T* Cc = static_cast<T*>(v.C) + P.offset + tl.start + lane;
+    const T p1 = (T)P.p1y, p2 = (T)P.p2y, kap = (T)P.kappa;
+    const int len = K + ny;
+    // forward: y_j = W'_j + p1 y_{j-1} + p2 y_{j-2}; y written over W'
+    T y1 = T(0), y2 = T(0);
+    for (int q0 = 0; q0 < len; q0 += kUnroll) {
+      T r[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (q0 + u < len) r[u] = Wc[(int64_t)fwd_index(q0 + u, K, ny) * nx];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (q0 + u < len) {
+          const T y = fma(p1, y1, fma(p2, y2, r[u]));
+          y2 = y1;
+          y1 = y;
+          if (q0 + u >= K) Wc[(int64_t)(q0 + u - K) * nx] = y;
+        }
       }
     }
-    st->step = n + 1;
-    if (st->remaining != kUnbounded) st->remaining -= 1;
+    // backward: x_j = y_j + p1 x_{j+1} + p2 x_{j+2};  C_j += kappa x_j
+    T x1 = T(0), x2 = T(0);
+    for (int q0 = 0; q0 < len; q0 += kUnroll) {
+      T r[kUnroll], c[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (q0 + u < len) {
+          const int j = bwd_index(q0 + u, K, ny);
+          r[u] = Wc[(int64_t)j * nx];
+          if (q0 + u >= K) c[u] = Cc[(int64_t)j * nx];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (q0 + u < len) {
+          const T x = fma(p1, x1, fma(p2, x2, r[u]));
+          x2 = x1;
+          x1 = x;
+          if (q0 + u >= K) Cc[(int64_t)(ny - 1 - (q0 + u - K)) * nx] = fma(kap, x, c[u]);
+        }
+      }
+    }
+  }
+  if (tl.index == 0 && lane == 0) finalize_sample(v, tl.member, st, P);
+}
+
+// Row sweep, one thread per row, streaming 32-column chunks of the warp's 32 rows
+// through a double-buffered shared tile (pitch 33, conflict-free for both the row-wise
+// cp.async fill and the per-thread column walk).  Tiles: 32-row groups.
+template <typename T>
+__global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v, int ntiles) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kStreamWarps + w;
+  if (wt >= ntiles) return;
+  const Tile tl = v.sweep_tiles[wt];
+  if (!v.ms[tl.member].active) return;
+  const MemberParams& P = v.mp[tl.member];
+  const int nx = P.nx, K = P.kx, nr = tl.count;
+  T* Wb = static_cast<T*>(v.W) + P.offset + (int64_t)tl.start * nx;
+  const T p1 = (T)P.p1x, p2 = (T)P.p2x;
+  const int len = K + nx;
+  const int nchunks = (len + 31) / 32;
+  // this warp's two 32 x 33 buffers
+  T (*buf)[32][33] = reinterpret_cast<T (*)[32][33]>(reinterpret_cast<T*>(smem) + (size_t)w * 2 * 32 * 33);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      // the backward pass reads (through cp.async) what other lanes stored in the forward pass
+      __threadfence_block();
+      __syncwarp();
+    }
+    // prefetch chunk 0
+    auto issue = [&](int ch, int b) {
+      const int q = ch * 32 + lane;
+      if (q < len) {
+        const int col = pass == 0 ? fwd_index(q, K, nx) : bwd_index(q, K, nx);
+        for (int r = 0; r < nr; ++r) cp_async_elem(&buf[b][r][lane], Wb + (int64_t)r * nx + col);
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    issue(0, 0);
+    T s1 = T(0), s2 = T(0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int b = ch & 1;
+      if (ch + 1 < nchunks) {
+        issue(ch + 1, b ^ 1);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      }
+      __syncwarp();
+      const int qbase = ch * 32;
+      const int cnt = min(32, len - qbase);
+      if (lane < nr) {
+        T* row = buf[b][lane];
+        for (int u = 0; u < cnt; ++u) {
+          const T val = fma(p1, s1, fma(p2, s2, row[u]));
+          s2 = s1;
+          s1 = val;
+          row[u] = val;
+        }
+      }
+      __syncwarp();
+      // write back the positions that belong to the line itself (not the pre-roll)
+      const int q = qbase + lane;
+      if (q < len && q >= K) {
+        const int col = pass == 0 ? q - K : nx - 1 - (q - K);
+        for (int r = 0; r < nr; ++r) Wb[(int64_t)r * nx + col] = buf[b][r][lane];
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -395,49 +670,75 @@ __global__ void obs_finalize_kernel(DevView v) {
 }
 
 template <typename T>
-cudaError_t step_impl(const DevView& v, int n_row_tiles, int n_col_tiles, const LaunchShape& sh,
-                      cudaStream_t st) {
-  rows_kernel<T, false><<<n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  cols_kernel<T><<<n_col_tiles, sh.cols_threads, sh.cols_smem, st>>>(v);
+cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaStream_t st) {
+  switch (phase) {
+    case 0:
+      if (sh.split)
+        stencil_kernel<T><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
+      else
+        rows_kernel<T, false><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
+      break;
+    case 1:
+      if (!sh.split) return cudaSuccess;
+      if (sh.stream)
+        rowstream_kernel<T><<<(sh.n_sweep_tiles + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps,
+                              rowstream_smem_bytes(sizeof(T)), st>>>(v, sh.n_sweep_tiles);
+      else
+        rowsweep_kernel<T><<<sh.n_sweep_tiles, sh.sweep_threads, sh.sweep_smem, st>>>(v);
+      break;
+    default:
+      if (sh.stream)
+        colstream_kernel<T><<<(sh.n_col_tiles + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps, 0, st>>>(
+            v, sh.n_col_tiles);
+      else if (sh.cols_inplace)
+        cols_kernel<T, true><<<sh.n_col_tiles, sh.cols_threads, sh.cols_smem, st>>>(v);
+      else
+        cols_kernel<T, false><<<sh.n_col_tiles, sh.cols_threads, sh.cols_smem, st>>>(v);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t phase_impl(const DevView& v, int phase, int n_tiles, const LaunchShape& sh, cudaStream_t st) {
-  if (phase == 0)
-    rows_kernel<T, false><<<n_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
-  else
-    cols_kernel<T><<<n_tiles, sh.cols_threads, sh.cols_smem, st>>>(v);
-  return cudaGetLastError();
+cudaError_t step_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
+  for (int ph = 0; ph < 3; ++ph) {
+    cudaError_t e = phase_impl<T>(v, ph, sh, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t observe_impl(const DevView& v, int n_row_tiles, const LaunchShape& sh, cudaStream_t st) {
-  rows_kernel<T, true><<<n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
+cudaError_t observe_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
+  rows_kernel<T, true><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   obs_finalize_kernel<<<(v.m + 127) / 128, 128, 0, st>>>(v);
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t smem_limits_impl() {
+  const int limit = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(rows_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(rows_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(stencil_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(rowsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(cols_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(rowstream_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(cols_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+}
+
 }  // namespace
 
-cudaError_t set_kernel_smem_limits(int precision, size_t rows_smem, size_t cols_smem) {
-  cudaError_t e;
-  if (precision == 0) {
-    e = cudaFuncSetAttribute(rows_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(rows_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(cols_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem);
-  }
-  e = cudaFuncSetAttribute(rows_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(rows_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(cols_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem);
+cudaError_t set_kernel_smem_limits(int precision) {
+  return precision == 0 ? smem_limits_impl<double>() : smem_limits_impl<float>();
 }
 
 cudaError_t launch_init_fields(const DevView& v, int precision, int64_t max_points, cudaStream_t st) {
@@ -451,21 +752,16 @@ cudaError_t launch_init_fields(const DevView& v, int precision, int64_t max_poin
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(const DevView& v, int precision, int n_row_tiles, int n_col_tiles,
-                        const LaunchShape& sh, cudaStream_t st) {
-  return precision == 0 ? step_impl<double>(v, n_row_tiles, n_col_tiles, sh, st)
-                        : step_impl<float>(v, n_row_tiles, n_col_tiles, sh, st);
+cudaError_t launch_step(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st) {
+  return precision == 0 ? step_impl<double>(v, sh, st) : step_impl<float>(v, sh, st);
 }
 
-cudaError_t launch_phase(const DevView& v, int precision, int phase, int n_tiles, const LaunchShape& sh,
-                         cudaStream_t st) {
-  return precision == 0 ? phase_impl<double>(v, phase, n_tiles, sh, st) : phase_impl<float>(v, phase, n_tiles, sh, st);
+cudaError_t launch_phase(const DevView& v, int precision, int phase, const LaunchShape& sh, cudaStream_t st) {
+  return precision == 0 ? phase_impl<double>(v, phase, sh, st) : phase_impl<float>(v, phase, sh, st);
 }
 
-cudaError_t launch_observe(const DevView& v, int precision, int n_row_tiles, const LaunchShape& sh,
-                           cudaStream_t st) {
-  return precision == 0 ? observe_impl<double>(v, n_row_tiles, sh, st)
-                        : observe_impl<float>(v, n_row_tiles, sh, st);
+cudaError_t launch_observe(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st) {
+  return precision == 0 ? observe_impl<double>(v, sh, st) : observe_impl<float>(v, sh, st);
 }
 
 }  // namespace chk

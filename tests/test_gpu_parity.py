@@ -67,8 +67,9 @@ def test_single_step_rows_and_columns(orc, nx, ny):
     orc.step(C_ref, L, gamma, dt)
     with ens(nx, ny, [0.0], gamma, dt, L) as e:
         e.set_field(0, C)
+        W = e.row_solve(0)
+        assert np.array_equal(e.field(0), C) and e.step_index(0) == 0
         e.step(1)
-        W = e.last_rows(0)
         C1 = e.field(0)
     scaleW = np.max(np.abs(W_ref))
     assert np.max(np.abs(W - W_ref)) <= 1e-12 * scale_or_one(scaleW)
@@ -307,3 +308,54 @@ def test_ensemble_256_full_size_sampled_members(orc):
             C = e.field(k)
             C0 = orc.initial_field(p["nx"], p["ny"], p["C0"][k], SEED, k * p["nx"] * p["ny"])
             assert abs(C.sum() - C0.sum()) <= 1e-9
+
+
+# ------------------------------------------------------------------------------------------
+# Every launch shape gives the oracle's result (tuning changes only the round-off order)
+# ------------------------------------------------------------------------------------------
+TUNINGS = [
+    dict(split=0), dict(split=1), dict(split=1, rows_band=3, sweep_band=5, cols_panel=7, cols_p=1),
+    dict(split=0, rows_band=8, rows_p=4, cols_panel=16, cols_p=4, threads=128),
+    dict(split=1, rows_band=32, sweep_band=64, cols_panel=64, cols_p=2, threads=512),
+    dict(split=0, rows_band=2, rows_p=1, cols_panel=8, cols_p=8, threads=64),
+    dict(split=1, stream=1), dict(split=1, stream=1, rows_band=4, threads=128),
+    dict(split=1, stream=0, sweep_band=32, cols_panel=32, cols_p=1),
+]
+
+
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+@pytest.mark.parametrize("tuning", TUNINGS, ids=[str(i) for i in range(len(TUNINGS))])
+def test_every_tuning_matches_oracle(orc, prec, tuning):
+    descs = []
+    base = 0
+    for k, d in enumerate(UNEVEN_SMALL[:4] + [dict(nx=96, ny=80, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.2)]):
+        descs.append(dict(d, seed=SEED + 7 * k, counter_base=base))
+        base += d["nx"] * d["ny"]
+    nsteps = 40
+    with ch.Ensemble.batch(descs, prec) as e:
+        e.set_tuning(**tuning)
+        e.set_sampling(10, 0.0, capacity=8)
+        e.step(nsteps)
+        F, D, B = e.observables()
+        for k, d in enumerate(descs):
+            C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
+            ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps, every=10)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            assert err <= (1e-12 if prec == ch.CH_FP64 else 1e-4), (k, err)
+            ser = e.series(k, 8)
+            np.testing.assert_allclose(ser[:, 1], ref.series[:, 1], rtol=1e-11 if prec == ch.CH_FP64 else 1e-5)
+
+
+def test_tuning_round_trip_and_errors():
+    with ens(64, 48, [0.0]) as e:
+        e.set_tuning(split=1, rows_band=8, sweep_band=16, cols_panel=16, cols_p=1, threads=128, stream=0)
+        t = e.tuning()
+        assert t["split"] == 1 and t["rows_band"] == 8 and t["sweep_band"] == 16 and t["cols_panel"] == 16
+        assert t["stream"] == 0 and t["threads"] == 128
+        with pytest.raises(ch.ChError):
+            e.set_tuning(cols_panel=64, cols_p=16, threads=128)
+        with pytest.raises(ch.ChError):
+            e.set_tuning(threads=100)
+        assert e.tuning()["rows_band"] == 8  # a rejected request keeps the shape in effect
+        ch.ch_set_tuning(e.h)  # defaults
+        e.step(3)
