@@ -274,6 +274,68 @@ int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, 
 int ch_step_field_noalloc(double* C, int nx, int ny, double L, double gamma, double dt, int64_t nsteps,
                           void* stream);
 
+/* ------------------------------------------------------------------------------------ */
+/* Serving: a stream of single-run requests with continuous batching.                    */
+/*                                                                                        */
+/* The paper (Sec. 4.1) ran its ensembles as M separate processes sharing the GPUs        */
+/* through CUDA MPS.  A server instead keeps every admitted run on the device and steps   */
+/* all of them together (the kernels of ch_create_batch): requests that arrive while      */
+/* others run are admitted as soon as a member slot and room for their fields in the HBM  */
+/* budget free up (FIFO), and each run retires the step its horizon ends.  A run's result */
+/* depends only on its own request (same result alone and in any mix).  A worker thread  */
+/* inside the library drives the GPU; the calls below never block on GPU work except     */
+/* ch_server_wait.                                                                        */
+/* ------------------------------------------------------------------------------------ */
+typedef struct ch_server_s* ch_server;
+
+typedef struct {
+  int nx, ny;          /* grid, each >= 5 */
+  double L, gamma, dt; /* > 0 */
+  double C0;           /* mean of the initial field (C0 + 0.1(2u-1), SplitMix64 stream `seed`) */
+  uint64_t seed;
+  int64_t nsteps;      /* horizon, >= 1 */
+  int every;           /* sampling period for the beta average (0: 100) */
+  double t1;           /* beta window start (< 0: 0.2 * nsteps * dt) */
+  double* field_out;   /* optional host buffer, ny*nx doubles, for the final field; caller-
+                          owned, must stay valid until the request is polled */
+} ch_request;
+
+typedef struct {
+  int64_t steps;       /* steps run (= nsteps) */
+  double F, dFdt, beta;/* observables of the final field (Eqs. (4), (6)) at t = nsteps dt */
+  double beta_avg;     /* time average of the sampled beta over t >= t1 (Eq. (42)) */
+  int64_t beta_count;
+  int nonfinite;       /* the run diverged */
+  double t_queued_s;   /* submit -> admitted */
+  double t_run_s;      /* admitted -> result ready */
+  double t_total_s;    /* submit -> result ready (time-to-result) */
+} ch_result;
+
+typedef struct {
+  int64_t submitted, completed, running, queued, max_running;
+  int64_t member_steps, grid_point_steps, chunks;
+  double busy_s, wall_s;           /* worker time with runs present; time since creation */
+  size_t arena_bytes, arena_peak_bytes;
+} ch_server_stats_t;
+
+/*
+ * Create a server of one precision whose runs' fields fit in hbm_budget_bytes of device
+ * memory (two arenas: fields and row-solve scratch, allocated now) with at most
+ * max_members runs in flight.  Errors: CH_EINVAL, CH_ENOMEM, CH_ECUDA.
+ */
+int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch_server* out);
+/* Queue a request (non-blocking); *id identifies it.  Errors: CH_EINVAL (bad request),
+ * CH_ENOMEM (larger than the whole budget), CH_EBUSY (queue full), or the server's error. */
+int ch_submit(ch_server s, const ch_request* r, uint64_t* id);
+/* CH_PENDING while queued or running; CH_OK with *out filled once finished (the request is
+ * then forgotten); CH_ENONFINITE if the run diverged; CH_ENOTFOUND for unknown ids. */
+int ch_poll(ch_server s, uint64_t id, ch_result* out);
+/* ch_poll after waiting up to timeout_s seconds for the result; CH_ETIMEOUT if not ready. */
+int ch_server_wait(ch_server s, uint64_t id, double timeout_s, ch_result* out);
+int ch_server_stats(ch_server s, ch_server_stats_t* out);
+/* Stop the worker (runs in flight are abandoned) and release everything. */
+void ch_server_destroy(ch_server s);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char* ch_last_error(void);
 

@@ -19,7 +19,8 @@ __all__ = [
     "ch_set_field", "ch_set_fields", "ch_get_fields", "ch_launch_phase", "ch_set_tuning", "ch_get_tuning", "Tuning",
     "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
     "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_step_field_noalloc", "ch_last_error", "ch_version",
-    "Ensemble",
+    "Ensemble", "Server", "Request", "Result", "ServerStats", "ch_server_create", "ch_submit", "ch_poll",
+    "ch_server_wait", "ch_server_stats", "ch_server_destroy",
 ]
 
 CH_OK, CH_PENDING = 0, 1
@@ -41,6 +42,35 @@ class MemberDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("L", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("dt", ctypes.c_double), ("C0", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("counter_base", ctypes.c_uint64)]
+
+
+class Request(ctypes.Structure):
+    """ch_request: one single-run request to a server."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("L", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("dt", ctypes.c_double), ("C0", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("nsteps", ctypes.c_int64), ("every", ctypes.c_int), ("t1", ctypes.c_double),
+                ("field_out", ctypes.POINTER(ctypes.c_double))]
+
+
+class Result(ctypes.Structure):
+    """ch_result: outcome of a served run."""
+    _fields_ = [("steps", ctypes.c_int64), ("F", ctypes.c_double), ("dFdt", ctypes.c_double),
+                ("beta", ctypes.c_double), ("beta_avg", ctypes.c_double), ("beta_count", ctypes.c_int64),
+                ("nonfinite", ctypes.c_int), ("t_queued_s", ctypes.c_double), ("t_run_s", ctypes.c_double),
+                ("t_total_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("max_running", ctypes.c_int64), ("member_steps", ctypes.c_int64),
+                ("grid_point_steps", ctypes.c_int64), ("chunks", ctypes.c_int64), ("busy_s", ctypes.c_double),
+                ("wall_s", ctypes.c_double), ("arena_bytes", ctypes.c_size_t), ("arena_peak_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Tuning(ctypes.Structure):
@@ -86,6 +116,12 @@ _SIGS = {
     "ch_load": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_penta_factor": (_c_int, [_c_dbl, _c_int, _dp, _dp, _dp, _ip]),
     "ch_step_field_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
+    "ch_server_create": (_c_int, [ctypes.c_size_t, _c_int, _c_int, ctypes.POINTER(_vp)]),
+    "ch_submit": (_c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ch_poll": (_c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "ch_server_wait": (_c_int, [_vp, ctypes.c_uint64, _c_dbl, ctypes.POINTER(Result)]),
+    "ch_server_stats": (_c_int, [_vp, ctypes.POINTER(ServerStats)]),
+    "ch_server_destroy": (None, [_vp]),
     "ch_last_error": (ctypes.c_char_p, []),
     "ch_version": (ctypes.c_char_p, []),
 }
@@ -278,6 +314,86 @@ def ch_save(h, path):
 
 def ch_load(h, path):
     _check(lib().ch_load(h, os.fsencode(path)))
+
+
+def ch_server_create(hbm_budget_bytes, precision=CH_FP32, max_members=4096):
+    s = _vp()
+    _check(lib().ch_server_create(hbm_budget_bytes, precision, max_members, ctypes.byref(s)))
+    return s.value
+
+
+def ch_submit(s, nx, ny, L, gamma, dt, C0, seed, nsteps, every=0, t1=-1.0, field_out=None):
+    """Queue a run; field_out (optional float64 numpy array of ny*nx) receives the final field."""
+    fo = None
+    if field_out is not None:
+        assert field_out.dtype == np.float64 and field_out.flags["C_CONTIGUOUS"] and field_out.size == nx * ny
+        fo = _ptr(field_out)
+    r = Request(nx, ny, L, gamma, dt, C0, seed, nsteps, every, t1, fo)
+    rid = ctypes.c_uint64()
+    _check(lib().ch_submit(s, ctypes.byref(r), ctypes.byref(rid)))
+    return rid.value
+
+
+def ch_poll(s, rid):
+    """None while pending, else the result dict (raises on a failed run)."""
+    res = Result()
+    rc = lib().ch_poll(s, rid, ctypes.byref(res))
+    if rc == CH_PENDING:
+        return None
+    _check(rc)
+    return res.as_dict()
+
+
+def ch_server_wait(s, rid, timeout_s):
+    res = Result()
+    _check(lib().ch_server_wait(s, rid, timeout_s, ctypes.byref(res)))
+    return res.as_dict()
+
+
+def ch_server_stats(s):
+    st = ServerStats()
+    _check(lib().ch_server_stats(s, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def ch_server_destroy(s):
+    lib().ch_server_destroy(s)
+
+
+class Server:
+    """Owns one libch server; methods forward to the ch_server_* functions."""
+
+    def __init__(self, hbm_budget_bytes, precision=CH_FP32, max_members=4096):
+        self.s = ch_server_create(hbm_budget_bytes, precision, max_members)
+
+    def submit(self, **req):
+        return ch_submit(self.s, **req)
+
+    def poll(self, rid):
+        return ch_poll(self.s, rid)
+
+    def wait(self, rid, timeout_s=600.0):
+        return ch_server_wait(self.s, rid, timeout_s)
+
+    def stats(self):
+        return ch_server_stats(self.s)
+
+    def close(self):
+        if self.s:
+            ch_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Ensemble:

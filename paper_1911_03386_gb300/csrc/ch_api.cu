@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "ch.h"
+#include "ch_handle.h"
 #include "ch_internal.h"
 
 namespace chk {
@@ -19,13 +20,11 @@ namespace chk {
 void record_error(const char* msg);
 }
 
-using chk::MemberParams;
-using chk::MemberState;
-using chk::Tile;
-
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace chh {
 
 int fail(int code, const std::string& msg) {
   g_last_error = msg;
@@ -120,61 +119,12 @@ int preroll_length(double p1, double p2, double tol) {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
-}  // namespace
+}  // namespace chh
 
 void chk::record_error(const char* msg) { g_last_error = msg; }
 
-struct ch_ensemble {
-  int precision = CH_FP64;
-  int m = 0;
-  size_t elt = 8;
-  int device = 0;
-  std::vector<MemberParams> hp;
-  std::vector<MemberState> hs0;  // initial state (for reset)
-  std::vector<Tile> rt, st, ct;   // stencil/fused bands, row-sweep bands, column panels
-  chk::LaunchShape shape{};
-  ch_tuning tuning{};             // as requested (0 / -1 = default)
-  int64_t total_points = 0, max_points = 0;
-  int64_t total_bands = 0;
-  int every = 1;
-  double t1 = 0.0;
-  int64_t series_cap = 0;
-  // device
-  void* C = nullptr;
-  void* W = nullptr;
-  MemberParams* dmp = nullptr;
-  MemberState* dms = nullptr;
-  Tile* drt = nullptr;
-  Tile* dst = nullptr;
-  Tile* dct = nullptr;
-  size_t cap_rt = 0, cap_st = 0, cap_ct = 0, cap_part = 0;  // device array capacities
-  double2* dpart = nullptr;
-  double* dseries = nullptr;
-  double* dobs = nullptr;
-  cudaStream_t own = nullptr;
-  cudaStream_t stream = nullptr;
-  bool external_stream = false;
-  cudaGraphExec_t graph = nullptr;
-  int graph_steps = 0;
 
-  chk::DevView view() const {
-    chk::DevView v;
-    v.C = C;
-    v.W = W;
-    v.mp = dmp;
-    v.ms = dms;
-    v.row_tiles = drt;
-    v.sweep_tiles = dst;
-    v.col_tiles = dct;
-    v.partials = dpart;
-    v.series = dseries;
-    v.obs_now = dobs;
-    v.m = m;
-    return v;
-  }
-};
-
-namespace {
+namespace chh {
 
 void drop_graph(ch_ensemble* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
@@ -298,6 +248,11 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   int64_t part = 0;
   for (int k = 0; k < h->m; ++k) {
     MemberParams& p = h->hp[k];
+    if (!h->has(k)) {
+      p.nbands = 0;
+      p.partial_base = part;
+      continue;
+    }
     int br = std::min(p.ny, want_br);
     while (br > 1 && rows_smem_bytes(br, p.nx, h->elt, threads) > kSmemMax) br = (br + 1) / 2;
     if (rows_smem_bytes(br, p.nx, h->elt, threads) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
@@ -418,12 +373,7 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
     h->max_points = std::max(h->max_points, np);
   }
   h->total_points = off;
-  ch_tuning defaults;
-  defaults.split = -1;
-  defaults.rows_band = defaults.rows_p = defaults.sweep_band = defaults.cols_panel = defaults.cols_p = 0;
-  defaults.threads = 0;
-  defaults.stream = -1;
-  int rc = build_tiles(h, defaults);
+  int rc = build_tiles(h, default_tuning());
   if (rc) {
     delete h;
     return rc;
@@ -521,7 +471,17 @@ int read_states(ch_ensemble* h, std::vector<MemberState>& s) {
   return copy_out(h, s.data(), h->dms, sizeof(MemberState) * h->m, "read member state");
 }
 
-}  // namespace
+ch_tuning default_tuning() {
+  ch_tuning t;
+  t.split = -1;
+  t.rows_band = t.rows_p = t.sweep_band = t.cols_panel = t.cols_p = t.threads = 0;
+  t.stream = -1;
+  return t;
+}
+
+}  // namespace chh
+
+using namespace chh;
 
 extern "C" {
 
@@ -772,14 +732,7 @@ int ch_launch_phase(ch_handle h, int phase) {
 
 int ch_set_tuning(ch_handle h, const ch_tuning* t) {
   if (int rc = check_handle(h)) return rc;
-  ch_tuning req;
-  if (t) {
-    req = *t;
-  } else {
-    req.split = -1;
-    req.rows_band = req.rows_p = req.sweep_band = req.cols_panel = req.cols_p = req.threads = 0;
-    req.stream = -1;
-  }
+  const ch_tuning req = t ? *t : default_tuning();
   if (req.rows_band < 0 || req.rows_p < 0 || req.sweep_band < 0 || req.cols_panel < 0 || req.cols_p < 0 ||
       req.threads < 0 || req.split < -1 || req.split > 1 || req.stream < -1 || req.stream > 1)
     return fail(CH_EINVAL, "tuning fields must be >= 0 (split, stream: -1, 0 or 1)");

@@ -93,6 +93,9 @@ struct LaunchShape {
 
 // Kernel launchers (ch_kernels.cu).  Each returns the launch status.
 cudaError_t launch_init_fields(const DevView& v, int precision, int64_t max_points, cudaStream_t st);
+// Initial fields of the members listed in `list` (device array of count member indices).
+cudaError_t launch_init_members(const DevView& v, int precision, const int* list, int count, int64_t max_points,
+                                cudaStream_t st);
 // One step = phases 0 (stencil or fused rows), 1 (row sweep, split form only), 2 (columns).
 cudaError_t launch_step(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st);
 cudaError_t launch_phase(const DevView& v, int precision, int phase, const LaunchShape& sh, cudaStream_t st);

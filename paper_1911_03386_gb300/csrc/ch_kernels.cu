@@ -58,8 +58,9 @@ __device__ __forceinline__ uint64_t sm64_draw(uint64_t seed, uint64_t k) {
 }
 
 template <typename T>
-__global__ void init_fields_kernel(DevView v) {
-  for (int m = blockIdx.y; m < v.m; m += gridDim.y) {
+__global__ void init_fields_kernel(DevView v, const int* list, int count) {
+  for (int q = blockIdx.y; q < count; q += gridDim.y) {
+    const int m = list ? list[q] : q;
     const MemberParams& P = v.mp[m];
     const int64_t npts = (int64_t)P.nx * P.ny;
     T* C = static_cast<T*>(v.C) + P.offset;
@@ -671,6 +672,7 @@ __global__ void obs_finalize_kernel(DevView v) {
 
 template <typename T>
 cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaStream_t st) {
+  if (sh.n_row_tiles == 0) return cudaSuccess;  // no member present
   switch (phase) {
     case 0:
       if (sh.split)
@@ -709,7 +711,7 @@ cudaError_t step_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) 
 
 template <typename T>
 cudaError_t observe_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
-  rows_kernel<T, true><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
+  if (sh.n_row_tiles > 0) rows_kernel<T, true><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   obs_finalize_kernel<<<(v.m + 127) / 128, 128, 0, st>>>(v);
@@ -741,15 +743,21 @@ cudaError_t set_kernel_smem_limits(int precision) {
   return precision == 0 ? smem_limits_impl<double>() : smem_limits_impl<float>();
 }
 
-cudaError_t launch_init_fields(const DevView& v, int precision, int64_t max_points, cudaStream_t st) {
+cudaError_t launch_init_members(const DevView& v, int precision, const int* list, int count, int64_t max_points,
+                                cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
   int64_t blocks = (max_points + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  dim3 grid((unsigned)blocks, (unsigned)(v.m < 65535 ? v.m : 65535));
+  dim3 grid((unsigned)blocks, (unsigned)(count < 65535 ? count : 65535));
   if (precision == 0)
-    init_fields_kernel<double><<<grid, 256, 0, st>>>(v);
+    init_fields_kernel<double><<<grid, 256, 0, st>>>(v, list, count);
   else
-    init_fields_kernel<float><<<grid, 256, 0, st>>>(v);
+    init_fields_kernel<float><<<grid, 256, 0, st>>>(v, list, count);
   return cudaGetLastError();
+}
+
+cudaError_t launch_init_fields(const DevView& v, int precision, int64_t max_points, cudaStream_t st) {
+  return launch_init_members(v, precision, nullptr, v.m, max_points, st);
 }
 
 cudaError_t launch_step(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st) {
