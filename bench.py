@@ -145,6 +145,18 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
 
 
+def finite_or_none(x):
+    """Strict JSON: non-finite floats (e.g. the beta average of a run that ends before its
+    window opens) become null."""
+    if isinstance(x, float):
+        return x if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: finite_or_none(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [finite_or_none(v) for v in x]
+    return x
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in sorted(os.listdir(os.path.join(ROOT, "paper_1911_03386_gb300", "csrc"))):
@@ -264,6 +276,36 @@ def run_e2e_leg(ch, torch, p, prec, K, rank, dist):
     return {"s": t1 - t0, "pts": npts * K * STEPS_PER_BENCH_STEP, "h2d": npts * 8 / K, "d2h": 3 * m * 8}
 
 
+def run_serving_leg(ch, torch, n_requests, rate, seed, precision, budget_bytes=8 << 30):
+    """Poisson stream of single-run requests through one server; latencies are the
+    library's submit-to-result times."""
+    import numpy as np
+    from paper_1911_03386_gb300 import workloads as wl
+    reqs = wl.request_stream(count=n_requests, rate=rate, seed=seed)
+    lat, ids = [], []
+    with ch.Server(budget_bytes, precision, max_members=4096) as srv:
+        t0 = time.perf_counter()
+        for r in reqs:
+            delay = r["arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(nx=r["nx"], ny=r["ny"], L=r["L"], gamma=r["gamma"], dt=r["dt"], C0=r["C0"],
+                                  seed=r["seed"], nsteps=r["steps"]))
+        t_sub = time.perf_counter() - t0
+        for i in ids:
+            lat.append(srv.wait(i, 3600.0)["t_total_s"])
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    work = sum(r["nx"] * r["ny"] * r["steps"] for r in reqs)
+    span = max(reqs[-1]["arrival"], 1e-9)
+    cap = st["grid_point_steps"] / max(st["busy_s"], 1e-9)
+    lat = np.array(lat)
+    return {"requests": n_requests, "rate_per_s": rate, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "max_s": float(lat.max()),
+            "throughput": work / wall, "capacity": cap, "offered": work / span, "rho": (work / span) / cap,
+            "max_running": st["max_running"], "submit_span_s": t_sub, "wall_s": wall, "unit": UNIT}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +315,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=120)
     args = ap.parse_args()
     K, W = args.steps, args.warmup
     if W < 3:
@@ -308,7 +352,7 @@ def main():
                                  "sample": "per step: %d members x %d time steps of %dx%d, one member per process"
                                            % (cores, ref_steps, p["nx"], p["ny"])},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
+        print(json.dumps(finite_or_none(line), allow_nan=False), flush=True)
         return
 
     pool = make_pool(cores) if (rank == 0 and world == 1 and not args.no_cpu) else None
@@ -326,6 +370,17 @@ def main():
     r64 = run_gpu_leg(ch, torch, p, ch.CH_FP64, K, W, rank, world, dist)
     r32 = None if args.no_fp32 else run_gpu_leg(ch, torch, p, ch.CH_FP32, K, W, rank, world, dist)
     e2e = None if args.no_e2e else run_e2e_leg(ch, torch, p, ch.CH_FP64, K, rank, dist)
+    serving = None
+    if not args.no_serving and rank == 0:
+        # the serving workload's own rate, then a rate the measured capacity sustains
+        nreq = args.serving_requests
+        at_rate = run_serving_leg(ch, torch, nreq, wl.SERVING["rate"], wl.BASE_SEED, ch.CH_FP32)
+        mean_work = at_rate["offered"] / wl.SERVING["rate"]
+        steady_rate = 0.7 * at_rate["capacity"] / mean_work
+        steady = run_serving_leg(ch, torch, nreq, steady_rate, wl.BASE_SEED + 1, ch.CH_FP32)
+        serving = {"workload": wl.SERVING["name"], "precision": "fp32",
+                   "sample": "%d requests per leg (n in {64..1024}^2, horizons U[1000, 50000], C0 ~ U[0, 0.5])"
+                             % nreq, "at_workload_rate": at_rate, "at_0.7_capacity": steady}
 
     def max_over_ranks(x):
         if not dist:
@@ -417,8 +472,8 @@ def main():
             "dtype": "f64", "data": "synthetic", "config": workload_config(p, "fp64"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_line,
             "gpu_launches": r64["launches"], "clocks": r64["clocks"], "fp32": fp32,
-            "beta_avg": beta_stats(avg64), "kernel_source": kernel_source_hash()}
-    print(json.dumps(line), flush=True)
+            "beta_avg": beta_stats(avg64), "serving": serving, "kernel_source": kernel_source_hash()}
+    print(json.dumps(finite_or_none(line), allow_nan=False), flush=True)
     if dist:
         torch.distributed.destroy_process_group()
 

@@ -181,8 +181,8 @@ int ch_launch_phase(ch_handle h, int phase);
  *   rows_band   rows per stencil / fused CTA (default 16 FP64, 32 FP32).
  *   rows_p      fused form: threads per row in the row sweep (chunks pre-rolled alone).
  *   sweep_band  split form: rows (one thread each) per row-sweep CTA (default 32).
- *   cols_panel  columns per column CTA (default 32 FP64, 16 FP32).
- *   cols_p      threads per column; 1 = in-place sweep with half the shared memory.
+ *   cols_panel  columns per column CTA (default 32).
+ *   cols_p      threads per column (default 1 FP64; FP32 chosen from ny).
  *   threads     threads per stencil / fused / column CTA, multiple of 32, <= 512
  *               (default 512 FP64, 256 FP32).
  *   stream      split form only: 1 = streaming sweeps (a warp streams 32 lines through
@@ -190,6 +190,9 @@ int ch_launch_phase(ch_handle h, int phase);
  *               intermediate kept in the scratch field), so recurrences in flight are not
  *               limited by shared memory; 0 = whole lines resident in shared memory
  *               (sweep_band, cols_panel, cols_p apply).  Default: 1 for CH_FP64.
+ *   persist     1 = the column kernel runs one CTA per resident slot and walks its panels
+ *               with double-buffered copies (the next panel loads while the current one
+ *               is swept); 0 = one CTA per panel (default).
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
  * size, lines too long for shared memory).
@@ -203,6 +206,7 @@ typedef struct {
   int cols_p;
   int threads;
   int stream;
+  int persist;
 } ch_tuning;
 int ch_set_tuning(ch_handle h, const ch_tuning* t); /* NULL restores the defaults */
 int ch_get_tuning(ch_handle h, ch_tuning* t);       /* shape in effect (member 0's values) */

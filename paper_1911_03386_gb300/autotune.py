@@ -32,8 +32,9 @@ def _candidates(precision):
     for threads in (128, 256, 512):
         for cb in (8, 16, 32, 64):
             for cp in (1, 2, 4, 8):
-                if cb * cp <= threads:
-                    out.append((-1, 2, dict(cols_panel=cb, cols_p=cp, threads=threads, stream=0)))
+                for persist in (0, 1):
+                    if cb * cp <= threads:
+                        out.append((-1, 2, dict(cols_panel=cb, cols_p=cp, threads=threads, stream=0, persist=persist)))
     return out
 
 
@@ -108,7 +109,7 @@ def tune(nx, ny, precision, points=1 << 24, reps=20, verbose=False):
             s_panel = min([t for t in table if t["phase"] == 1 and not t.get("stream")], key=lambda t: t["ms"])
             sel.update(stream=0, sweep_band=s_panel["sweep_band"])
             tot += s_panel["ms"] - min(t["ms"] for t in table if t["phase"] == 1)
-        sel.update(cols_panel=c2["cols_panel"], cols_p=c2["cols_p"])
+        sel.update(cols_panel=c2["cols_panel"], cols_p=c2["cols_p"], persist=c2.get("persist", 0))
     return sel, dict(table=table, step_ms=tot + cms, members=m)
 
 

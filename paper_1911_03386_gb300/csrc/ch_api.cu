@@ -215,8 +215,10 @@ size_t rows_smem_bytes(int nr, int nx, size_t elt, int threads) {
 
 size_t sweep_smem_bytes(int nr, int nx, size_t elt) { return (size_t)nr * (nx + 1) * elt; }
 
-size_t cols_smem_bytes(int nc, int ny, size_t elt, bool inplace) {
-  return (size_t)(inplace ? 1 : 2) * ny * (nc + 1) * elt;
+// W panel swept in place + C panel, twice when double-buffered
+size_t cols_panel_elems(int nc, int ny) { return (size_t)ny * (nc + 1); }
+size_t cols_smem_bytes(int nc, int ny, size_t elt, bool persist) {
+  return (size_t)(persist ? 4 : 2) * cols_panel_elems(nc, ny) * elt;
 }
 
 int round_warps(int t) { return ((t + 31) / 32) * 32; }
@@ -232,16 +234,15 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   if (threads % 32 || threads > 512) return fail(CH_EINVAL, "threads must be a multiple of 32, at most 512");
   const int want_br = t.rows_band > 0 ? t.rows_band : (f64 ? 16 : 32);
   const int want_bs = t.sweep_band > 0 ? t.sweep_band : 32;
-  const int want_bc = t.cols_panel > 0 ? t.cols_panel : (f64 ? 32 : 16);
+  const int want_bc = t.cols_panel > 0 ? t.cols_panel : 32;
   if (t.sweep_band > 512 || want_bc * std::max(1, t.cols_p) > threads || want_br * std::max(1, t.rows_p) > threads)
     return fail(CH_EINVAL, "band/panel times threads per line exceeds the CTA size");
-  const bool inplace = t.cols_p > 0 ? t.cols_p == 1 : f64;
   const int stream = split ? (t.stream >= 0 ? (t.stream ? 1 : 0) : (f64 ? 1 : 0)) : 0;
+  const bool persist = t.persist == 1;
   std::vector<Tile> rt, st, ct;
   chk::LaunchShape sh{};
   sh.split = split;
   sh.stream = stream;
-  sh.cols_inplace = inplace ? 1 : 0;
   sh.rows_threads = threads;
   sh.cols_threads = threads;
   sh.sweep_threads = 0;
@@ -256,15 +257,15 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     int br = std::min(p.ny, want_br);
     while (br > 1 && rows_smem_bytes(br, p.nx, h->elt, threads) > kSmemMax) br = (br + 1) / 2;
     if (rows_smem_bytes(br, p.nx, h->elt, threads) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
-    p.rows_p = t.rows_p > 0 ? t.rows_p : (f64 ? 1 : std::max(1, std::min(threads / br, p.nx / 32)));
+    p.rows_p = t.rows_p > 0 ? t.rows_p : (f64 ? 1 : std::max(1, std::min(threads / br, p.nx / 64)));
     if (br * p.rows_p > threads) p.rows_p = std::max(1, threads / br);
     int bs = stream ? std::min(p.ny, 32) : std::min(p.ny, want_bs);
     while (bs > 1 && !stream && sweep_smem_bytes(bs, p.nx, h->elt) > kSmemMax) bs = (bs + 1) / 2;
     int bc = stream ? std::min(p.nx, 32) : std::min(p.nx, want_bc);
-    while (bc > 1 && !stream && cols_smem_bytes(bc, p.ny, h->elt, inplace) > kSmemMax) bc = (bc + 1) / 2;
-    if (!stream && cols_smem_bytes(bc, p.ny, h->elt, inplace) > kSmemMax)
+    while (bc > 1 && !stream && cols_smem_bytes(bc, p.ny, h->elt, persist) > kSmemMax) bc = (bc + 1) / 2;
+    if (!stream && cols_smem_bytes(bc, p.ny, h->elt, persist) > kSmemMax)
       return fail(CH_EINVAL, "column too long for shared memory");
-    p.cols_p = inplace ? 1 : (t.cols_p > 0 ? t.cols_p : std::max(1, std::min(threads / bc, p.ny / 32)));
+    p.cols_p = t.cols_p > 0 ? t.cols_p : (f64 ? 1 : std::max(1, std::min(threads / bc, p.ny / 64)));
     if (bc * p.cols_p > threads) p.cols_p = std::max(1, threads / bc);
     int b = 0;
     for (int j0 = 0; j0 < p.ny; j0 += br, ++b) rt.push_back(Tile{k, j0, std::min(br, p.ny - j0), b});
@@ -282,7 +283,18 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     int q = 0;
     for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
     sh.rows_smem = std::max(sh.rows_smem, rows_smem_bytes(br, p.nx, h->elt, threads));
-    if (!stream) sh.cols_smem = std::max(sh.cols_smem, cols_smem_bytes(bc, p.ny, h->elt, inplace));
+    if (!stream) {
+      sh.cols_smem = std::max(sh.cols_smem, cols_smem_bytes(bc, p.ny, h->elt, persist));
+      sh.cols_panel_cap = std::max(sh.cols_panel_cap, (int)cols_panel_elems(bc, p.ny));
+    }
+  }
+  sh.cols_persist = persist ? 1 : 0;
+  if (!stream && !rt.empty()) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = chk::cols_blocks_per_sm(h->precision, sh.cols_persist, threads, sh.cols_smem);
+    sh.cols_grid = std::max(1, sms * std::max(1, per_sm));
   }
   if (sh.sweep_threads > 512) return fail(CH_EINVAL, "row-sweep band above 512 rows");
   sh.n_row_tiles = (int)rt.size();
@@ -476,6 +488,7 @@ ch_tuning default_tuning() {
   t.split = -1;
   t.rows_band = t.rows_p = t.sweep_band = t.cols_panel = t.cols_p = t.threads = 0;
   t.stream = -1;
+  t.persist = -1;
   return t;
 }
 
@@ -734,8 +747,9 @@ int ch_set_tuning(ch_handle h, const ch_tuning* t) {
   if (int rc = check_handle(h)) return rc;
   const ch_tuning req = t ? *t : default_tuning();
   if (req.rows_band < 0 || req.rows_p < 0 || req.sweep_band < 0 || req.cols_panel < 0 || req.cols_p < 0 ||
-      req.threads < 0 || req.split < -1 || req.split > 1 || req.stream < -1 || req.stream > 1)
-    return fail(CH_EINVAL, "tuning fields must be >= 0 (split, stream: -1, 0 or 1)");
+      req.threads < 0 || req.split < -1 || req.split > 1 || req.stream < -1 || req.stream > 1 || req.persist < -1 ||
+      req.persist > 1)
+    return fail(CH_EINVAL, "tuning fields must be >= 0 (split, stream, persist: -1, 0 or 1)");
   CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
   const std::vector<MemberParams> saved = h->hp;
   const ch_tuning old = h->tuning;
@@ -760,6 +774,7 @@ int ch_get_tuning(ch_handle h, ch_tuning* t) {
   t->cols_p = h->hp[0].cols_p;
   t->threads = h->shape.rows_threads;
   t->stream = h->shape.stream;
+  t->persist = h->shape.cols_persist;
   return CH_OK;
 }
 

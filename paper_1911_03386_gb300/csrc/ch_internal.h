@@ -81,7 +81,6 @@ struct DevView {
 struct LaunchShape {
   int split;             // 1: stencil_kernel + rowsweep_kernel, 0: fused rows_kernel
   int stream;            // 1 (split only): rowstream_kernel + colstream_kernel, 32-line tiles
-  int cols_inplace;      // 1: cols_kernel<T, true> (one thread per column)
   int n_row_tiles, n_sweep_tiles, n_col_tiles;
   int rows_threads;      // threads per stencil / fused CTA
   size_t rows_smem;      // dynamic shared memory (max over tiles)
@@ -89,6 +88,9 @@ struct LaunchShape {
   size_t sweep_smem;
   int cols_threads;
   size_t cols_smem;
+  int cols_persist;      // 1: cols_kernel walks panels with double-buffered copies
+  int cols_grid;         // CTAs of the persistent column kernel (SMs x resident CTAs)
+  int cols_panel_cap;    // elements of one panel buffer
 };
 
 // Kernel launchers (ch_kernels.cu).  Each returns the launch status.
@@ -101,5 +103,7 @@ cudaError_t launch_step(const DevView& v, int precision, const LaunchShape& sh, 
 cudaError_t launch_phase(const DevView& v, int precision, int phase, const LaunchShape& sh, cudaStream_t st);
 cudaError_t launch_observe(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st);
 cudaError_t set_kernel_smem_limits(int precision);
+// Resident CTAs per SM of the column kernel for a launch shape (0 on error).
+int cols_blocks_per_sm(int precision, int persist, int threads, size_t smem);
 
 }  // namespace chk

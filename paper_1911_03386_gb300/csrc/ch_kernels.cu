@@ -151,47 +151,185 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-// Forward recurrence y_i = r_i + p1 y_{i-1} + p2 y_{i-2} on the chunk [c0, c1) of a
-// periodic line of n points stored with element stride `es`; the state is pre-rolled
-// from zero over the K points before c0 (cyclically).  `in` and `out` may be the same
-// line when [c0, c1) is the whole line.
+// Whole-line sweep in place by one thread, written for instruction economy: the pre-roll
+// walks contiguous segments (no per-point wrap test) and every pass runs in batches of 8
+// whose loads are issued before the batch's dependent FMAs.  The recurrences are the ones
+// stated at the top of this file (forward over the K points before the line start, then
+// the line; backward over the K points after its end, then the line).
 template <typename T>
-__device__ __forceinline__ void sweep_forward(const T* in, T* out, int es, int n, int c0, int c1, int K, T p1,
-                                              T p2) {
-  T y1 = T(0), y2 = T(0);
-  int k = wrap_index(c0 - K, n);
-  for (int q = 0; q < K; ++q) {
-    const T y = fma(p1, y1, fma(p2, y2, in[k * es]));
-    y2 = y1;
-    y1 = y;
-    if (++k == n) k = 0;
+__device__ __forceinline__ void seg_forward(const T* line, int es, int begin, int end, T p1, T p2, T& a, T& b) {
+  int i = begin;
+  for (; i + 8 <= end; i += 8) {
+    T r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = line[(i + u) * es];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T y = fma(p1, a, fma(p2, b, r[u]));
+      b = a;
+      a = y;
+    }
   }
-  for (int i = c0; i < c1; ++i) {
-    const T y = fma(p1, y1, fma(p2, y2, in[i * es]));
-    out[i * es] = y;
-    y2 = y1;
-    y1 = y;
+  for (; i < end; ++i) {
+    const T y = fma(p1, a, fma(p2, b, line[i * es]));
+    b = a;
+    a = y;
   }
 }
 
-// Backward recurrence x_i = y_i + p1 x_{i+1} + p2 x_{i+2} on [c0, c1), pre-rolled over the
-// K points after c1 (cyclically).  In place allowed for a whole line, as above.
 template <typename T>
-__device__ __forceinline__ void sweep_backward(const T* in, T* out, int es, int n, int c0, int c1, int K, T p1,
-                                               T p2) {
-  T x1 = T(0), x2 = T(0);
-  int k = wrap_index(c1 - 1 + K, n);
-  for (int q = 0; q < K; ++q) {
-    const T x = fma(p1, x1, fma(p2, x2, in[k * es]));
-    x2 = x1;
-    x1 = x;
-    if (--k < 0) k = n - 1;
+__device__ __forceinline__ void seg_backward(const T* line, int es, int hi, int lo, T p1, T p2, T& a, T& b) {
+  int i = hi;  // walks hi, hi-1, ..., lo
+  for (; i - 8 >= lo - 1; i -= 8) {
+    T r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = line[(i - u) * es];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T y = fma(p1, a, fma(p2, b, r[u]));
+      b = a;
+      a = y;
+    }
   }
-  for (int i = c1 - 1; i >= c0; --i) {
-    const T x = fma(p1, x1, fma(p2, x2, in[i * es]));
-    out[i * es] = x;
-    x2 = x1;
-    x1 = x;
+  for (; i >= lo; --i) {
+    const T y = fma(p1, a, fma(p2, b, line[i * es]));
+    b = a;
+    a = y;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void line_sweep_inplace(T* line, int es, int n, int K, T p1, T p2) {
+  // forward pre-roll over indices -K .. -1 (mod n), in increasing order
+  T a = T(0), b = T(0);
+  for (int rem = K, idx = wrap_index(-K, n); rem > 0;) {
+    const int seg = min(rem, n - idx);
+    seg_forward<T>(line, es, idx, idx + seg, p1, p2, a, b);
+    rem -= seg;
+    idx = 0;
+  }
+  // forward pass in place
+  int i = 0;
+  for (; i + 8 <= n; i += 8) {
+    T r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = line[(i + u) * es];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T y = fma(p1, a, fma(p2, b, r[u]));
+      line[(i + u) * es] = y;
+      b = a;
+      a = y;
+    }
+  }
+  for (; i < n; ++i) {
+    const T y = fma(p1, a, fma(p2, b, line[i * es]));
+    line[i * es] = y;
+    b = a;
+    a = y;
+  }
+  // backward pre-roll over indices n-1+K .. n (mod n), in decreasing order
+  a = T(0);
+  b = T(0);
+  for (int rem = K, idx = wrap_index(n - 1 + K, n); rem > 0;) {
+    const int seg = min(rem, idx + 1);
+    seg_backward<T>(line, es, idx, idx - seg + 1, p1, p2, a, b);
+    rem -= seg;
+    idx = n - 1;
+  }
+  // backward pass in place
+  i = n - 1;
+  for (; i - 8 >= -1; i -= 8) {
+    T r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = line[(i - u) * es];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T x = fma(p1, a, fma(p2, b, r[u]));
+      line[(i - u) * es] = x;
+      b = a;
+      a = x;
+    }
+  }
+  for (; i >= 0; --i) {
+    const T x = fma(p1, a, fma(p2, b, line[i * es]));
+    line[i * es] = x;
+    b = a;
+    a = x;
+  }
+}
+
+// Chunked in-place sweep of a line shared by several threads, lean form: thread owns
+// [c0, c1) (active = it owns a non-empty chunk).  Each pass pre-rolls first (contiguous
+// segments, reads only), then after a CTA barrier runs its chunk in place in batches of
+// 8 with the loads issued ahead.  Every thread of the CTA must call it (it contains
+// __syncthreads).
+template <typename T>
+__device__ __forceinline__ void chunk_sweep_inplace(T* line, int es, int n, int c0, int c1, int K, T p1, T p2,
+                                                    bool active) {
+  T a = T(0), b = T(0);
+  if (active) {
+    for (int rem = K, idx = wrap_index(c0 - K, n); rem > 0;) {
+      const int seg = min(rem, n - idx);
+      seg_forward<T>(line, es, idx, idx + seg, p1, p2, a, b);
+      rem -= seg;
+      idx = 0;
+    }
+  }
+  __syncthreads();
+  if (active) {
+    int i = c0;
+    for (; i + 8 <= c1; i += 8) {
+      T r[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) r[u] = line[(i + u) * es];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T y = fma(p1, a, fma(p2, b, r[u]));
+        line[(i + u) * es] = y;
+        b = a;
+        a = y;
+      }
+    }
+    for (; i < c1; ++i) {
+      const T y = fma(p1, a, fma(p2, b, line[i * es]));
+      line[i * es] = y;
+      b = a;
+      a = y;
+    }
+  }
+  __syncthreads();
+  a = T(0);
+  b = T(0);
+  if (active) {
+    for (int rem = K, idx = wrap_index(c1 - 1 + K, n); rem > 0;) {
+      const int seg = min(rem, idx + 1);
+      seg_backward<T>(line, es, idx, idx - seg + 1, p1, p2, a, b);
+      rem -= seg;
+      idx = n - 1;
+    }
+  }
+  __syncthreads();
+  if (active) {
+    int i = c1 - 1;
+    for (; i - 8 >= c0 - 1; i -= 8) {
+      T r[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) r[u] = line[(i - u) * es];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T x = fma(p1, a, fma(p2, b, r[u]));
+        line[(i - u) * es] = x;
+        b = a;
+        a = x;
+      }
+    }
+    for (; i >= c0; --i) {
+      const T x = fma(p1, a, fma(p2, b, line[i * es]));
+      line[i * es] = x;
+      b = a;
+      a = x;
+    }
   }
 }
 
@@ -362,9 +500,11 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
   const int c1 = min(nx, c0 + chunk);
   const bool sweeper = threadIdx.x < nsweep && c0 < c1;
   const T p1 = (T)P.p1x, p2 = (T)P.p2x;
-  if (sweeper) sweep_forward<T>(Cs + (size_t)row * ld, Ms + (size_t)row * ld, 1, nx, c0, c1, P.kx, p1, p2);
-  __syncthreads();
-  if (sweeper) sweep_backward<T>(Ms + (size_t)row * ld, Cs + (size_t)row * ld, 1, nx, c0, c1, P.kx, p1, p2);
+  if (sweep_p == 1) {
+    if (sweeper) line_sweep_inplace<T>(Cs + (size_t)row * ld, 1, nx, P.kx, p1, p2);
+  } else {
+    chunk_sweep_inplace<T>(Cs + (size_t)row * ld, 1, nx, c0, c1, P.kx, p1, p2, sweeper);
+  }
   __syncthreads();
 
   {
@@ -428,12 +568,7 @@ __global__ void __launch_bounds__(512) rowsweep_kernel(DevView v) {
   load_rows_async<T>(Bs, ld, W, nx, P.ny, j0, nr);
   cp_async_wait_all();
   __syncthreads();
-  if (threadIdx.x < nr) {
-    T* line = Bs + (size_t)threadIdx.x * ld;
-    const T p1 = (T)P.p1x, p2 = (T)P.p2x;
-    sweep_forward<T>(line, line, 1, nx, 0, nx, P.kx, p1, p2);
-    sweep_backward<T>(line, line, 1, nx, 0, nx, P.kx, p1, p2);
-  }
+  if (threadIdx.x < nr) line_sweep_inplace<T>(Bs + (size_t)threadIdx.x * ld, 1, nx, P.kx, (T)P.p1x, (T)P.p2x);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int r = warp; r < nr; r += nwarps) {
@@ -444,59 +579,85 @@ __global__ void __launch_bounds__(512) rowsweep_kernel(DevView v) {
 }
 
 // -------------------------------------------------------------------------------------
-// Column kernel: column sweep and update for a panel of columns of one member.
-// Shared memory: Ws (and Ys unless INPLACE), ny rows of nc+1 elements each.  INPLACE
-// needs one thread per column (cols_p == 1).
+// Column kernel: column sweep and update for panels of columns.
+// Shared memory per buffer: Ws (the W panel, swept in place) and Cs (the C panel), ny rows
+// of nc+1 elements each; cols_p threads per column.  With PERSIST, a CTA walks the panels
+// blockIdx.x, blockIdx.x + gridDim.x, ... with two buffers: the next panel's W and C are
+// copied in (cp.async) while the current one is swept and written back, so every CTA keeps
+// memory traffic in flight through its compute phases.  Without PERSIST each CTA takes one
+// panel.  panel_cap: elements of one panel buffer (max over members of ny * (nc + 1)).
 // -------------------------------------------------------------------------------------
-template <typename T, bool INPLACE>
-__global__ void __launch_bounds__(512) cols_kernel(DevView v) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Tile tl = v.col_tiles[blockIdx.x];
-  MemberState* st = v.ms + tl.member;
-  if (!st->active) return;
+template <typename T>
+__device__ __forceinline__ void cols_issue(const DevView& v, int tile, T* Ws, T* Cs) {
+  const Tile tl = v.col_tiles[tile];
+  if (!v.ms[tl.member].active) return;
   const MemberParams& P = v.mp[tl.member];
-  const int nx = P.nx, ny = P.ny, i0 = tl.start, nc = tl.count;
-  const int ldc = nc + 1;
-  T* Ws = reinterpret_cast<T*>(smem);
-  T* Ys = INPLACE ? Ws : Ws + (size_t)ny * ldc;
-
-  {
-    const T* __restrict__ W = static_cast<const T*>(v.W) + P.offset;
-    for (int idx = threadIdx.x; idx < ny * nc; idx += blockDim.x) {
-      const int j = idx / nc, c = idx - j * nc;
-      cp_async_elem(Ws + (size_t)j * ldc + c, W + (int64_t)j * nx + i0 + c);
-    }
-    cp_async_wait_all();
+  const int nx = P.nx, ny = P.ny, i0 = tl.start, nc = tl.count, ldc = nc + 1;
+  const int tx = threadIdx.x % nc, ty = threadIdx.x / nc, ry = blockDim.x / nc;
+  if (ty >= ry) return;
+  const T* W = static_cast<const T*>(v.W) + P.offset + i0 + tx;
+  const T* C = static_cast<const T*>(v.C) + P.offset + i0 + tx;
+  for (int j = ty; j < ny; j += ry) {
+    cp_async_elem(Ws + (size_t)j * ldc + tx, W + (int64_t)j * nx);
+    cp_async_elem(Cs + (size_t)j * ldc + tx, C + (int64_t)j * nx);
   }
-  __syncthreads();
+}
 
-  const int sweep_p = INPLACE ? 1 : P.cols_p;
-  const int nsweep = nc * sweep_p;
-  const int chunk = (ny + sweep_p - 1) / sweep_p;
-  const int col = threadIdx.x % nc;
-  const int c0 = (threadIdx.x / nc) * chunk;
-  const int c1 = min(ny, c0 + chunk);
-  const bool sweeper = threadIdx.x < nsweep && c0 < c1;
-  const T p1 = (T)P.p1y, p2 = (T)P.p2y;
-  if (sweeper) sweep_forward<T>(Ws + col, Ys + col, ldc, ny, c0, c1, P.ky, p1, p2);
-  if (!INPLACE) __syncthreads();
-  if (sweeper) sweep_backward<T>(Ys + col, Ws + col, ldc, ny, c0, c1, P.ky, p1, p2);
-  __syncthreads();
-
-  {
-    T* __restrict__ C = static_cast<T*>(v.C) + P.offset;
-    const T kap = (T)P.kappa;
-    for (int idx = threadIdx.x; idx < ny * nc; idx += blockDim.x) {
-      const int j = idx / nc, c = idx - j * nc;
-      const int64_t g = (int64_t)j * nx + i0 + c;
-      C[g] = fma(kap, Ws[(size_t)j * ldc + c], C[g]);
+template <typename T, bool PERSIST>
+__global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int panel_cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* buf[2];
+  buf[0] = reinterpret_cast<T*>(smem);
+  buf[1] = buf[0] + 2 * (size_t)panel_cap;
+  int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  cols_issue<T>(v, tile, buf[0], buf[0] + panel_cap);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int it = 0; tile < ntiles; ++it) {
+    const int next = tile + gridDim.x;
+    T* Ws = buf[PERSIST ? (it & 1) : 0];
+    T* Cs = Ws + panel_cap;
+    if (PERSIST && next < ntiles) {
+      T* Wn = buf[(it + 1) & 1];
+      cols_issue<T>(v, next, Wn, Wn + panel_cap);
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    const Tile tl = v.col_tiles[tile];
+    MemberState* st = v.ms + tl.member;
+    if (st->active) {
+      const MemberParams& P = v.mp[tl.member];
+      const int nx = P.nx, ny = P.ny, i0 = tl.start, nc = tl.count, ldc = nc + 1;
+      const int sweep_p = P.cols_p;
+      const int nsweep = nc * sweep_p;
+      const int chunk = (ny + sweep_p - 1) / sweep_p;
+      const int col = threadIdx.x % nc;
+      const int c0 = (threadIdx.x / nc) * chunk;
+      const int c1 = min(ny, c0 + chunk);
+      const bool sweeper = threadIdx.x < nsweep && c0 < c1;
+      const T p1 = (T)P.p1y, p2 = (T)P.p2y;
+      if (sweep_p == 1) {
+        if (sweeper) line_sweep_inplace<T>(Ws + col, ldc, ny, P.ky, p1, p2);
+      } else {
+        chunk_sweep_inplace<T>(Ws + col, ldc, ny, c0, c1, P.ky, p1, p2, sweeper);
+      }
+      __syncthreads();
+      T* __restrict__ C = static_cast<T*>(v.C) + P.offset;
+      const T kap = (T)P.kappa;
+      const int tx = threadIdx.x % nc, ty = threadIdx.x / nc, ry = blockDim.x / nc;
+      if (ty < ry)
+        for (int j = ty; j < ny; j += ry)
+          C[(int64_t)j * nx + i0 + tx] = fma(kap, Ws[(size_t)j * ldc + tx], Cs[(size_t)j * ldc + tx]);
+      // Panel 0 finalises the member's sample of this step (partials written by the
+      // stencil phase of the same step) and advances the member's step counter.  No other
+      // CTA of this launch reads or writes the member's state.
+      if (tl.index == 0 && threadIdx.x == 0) finalize_sample(v, tl.member, st, P);
+    }
+    __syncthreads();  // the buffer is refilled two panels later
+    if (!PERSIST) break;
+    tile = next;
   }
-
-  // Panel 0 finalises the member's sample of this step (partials written by the stencil
-  // phase of the same step) and advances the member's step counter.  No other CTA of
-  // this launch reads or writes the member's state.
-  if (tl.index == 0 && threadIdx.x == 0) finalize_sample(v, tl.member, st, P);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // -------------------------------------------------------------------------------------
@@ -509,7 +670,7 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v) {
 // backward pass pre-rolls over the line's start and writes back to front.
 // -------------------------------------------------------------------------------------
 constexpr int kStreamWarps = 4;  // warps per CTA of the streaming sweeps
-constexpr int kUnroll = 8;       // loads issued ahead of the recurrence in the column sweep
+
 
 constexpr size_t rowstream_smem_bytes(size_t elt) { return (size_t)kStreamWarps * 2 * 32 * 33 * elt; }
 
@@ -538,6 +699,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
     T* Wc = static_cast<T*>(v.W) + P.offset + tl.start + lane;
     T* Cc = static_cast<T*>(v.C) + P.offset + tl.start + lane;
     const T p1 = (T)P.p1y, p2 = (T)P.p2y, kap = (T)P.kappa;
+    constexpr int kUnroll = 8;  // loads issued ahead of the recurrence
     const int len = K + ny;
     // forward: y_j = W'_j + p1 y_{j-1} + p2 y_{j-2}; y written over W'
     T y1 = T(0), y2 = T(0);
@@ -631,11 +793,24 @@ __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v,
       const int cnt = min(32, len - qbase);
       if (lane < nr) {
         T* row = buf[b][lane];
-        for (int u = 0; u < cnt; ++u) {
-          const T val = fma(p1, s1, fma(p2, s2, row[u]));
-          s2 = s1;
-          s1 = val;
-          row[u] = val;
+        if (cnt == 32) {
+          T vals[32];
+#pragma unroll
+          for (int u = 0; u < 32; ++u) vals[u] = row[u];
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            const T val = fma(p1, s1, fma(p2, s2, vals[u]));
+            s2 = s1;
+            s1 = val;
+            row[u] = val;
+          }
+        } else {
+          for (int u = 0; u < cnt; ++u) {
+            const T val = fma(p1, s1, fma(p2, s2, row[u]));
+            s2 = s1;
+            s1 = val;
+            row[u] = val;
+          }
         }
       }
       __syncwarp();
@@ -692,10 +867,12 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
       if (sh.stream)
         colstream_kernel<T><<<(sh.n_col_tiles + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps, 0, st>>>(
             v, sh.n_col_tiles);
-      else if (sh.cols_inplace)
-        cols_kernel<T, true><<<sh.n_col_tiles, sh.cols_threads, sh.cols_smem, st>>>(v);
+      else if (sh.cols_persist)
+        cols_kernel<T, true><<<min(sh.n_col_tiles, sh.cols_grid), sh.cols_threads, sh.cols_smem, st>>>(
+            v, sh.n_col_tiles, sh.cols_panel_cap);
       else
-        cols_kernel<T, false><<<sh.n_col_tiles, sh.cols_threads, sh.cols_smem, st>>>(v);
+        cols_kernel<T, false><<<sh.n_col_tiles, sh.cols_threads, sh.cols_smem, st>>>(v, sh.n_col_tiles,
+                                                                                      sh.cols_panel_cap);
   }
   return cudaGetLastError();
 }
@@ -730,9 +907,10 @@ cudaError_t smem_limits_impl() {
     return e;
   if ((e = cudaFuncSetAttribute(rowsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(cols_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
-    return e;
+
   if ((e = cudaFuncSetAttribute(rowstream_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(cols_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(cols_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
 }
@@ -770,6 +948,18 @@ cudaError_t launch_phase(const DevView& v, int precision, int phase, const Launc
 
 cudaError_t launch_observe(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st) {
   return precision == 0 ? observe_impl<double>(v, sh, st) : observe_impl<float>(v, sh, st);
+}
+
+int cols_blocks_per_sm(int precision, int persist, int threads, size_t smem) {
+  int n = 0;
+  cudaError_t e;
+  if (precision == 0)
+    e = persist ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cols_kernel<double, true>, threads, smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cols_kernel<double, false>, threads, smem);
+  else
+    e = persist ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cols_kernel<float, true>, threads, smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cols_kernel<float, false>, threads, smem);
+  return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace chk

@@ -320,6 +320,8 @@ TUNINGS = [
     dict(split=0, rows_band=2, rows_p=1, cols_panel=8, cols_p=8, threads=64),
     dict(split=1, stream=1), dict(split=1, stream=1, rows_band=4, threads=128),
     dict(split=1, stream=0, sweep_band=32, cols_panel=32, cols_p=1),
+    dict(split=0, persist=1, cols_panel=8, cols_p=2, threads=128), dict(split=0, persist=0, rows_p=1, cols_p=1),
+    dict(split=1, stream=0, persist=1, cols_panel=16, cols_p=1, threads=256),
 ]
 
 
