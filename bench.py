@@ -167,18 +167,20 @@ def kernel_source_hash():
 
 
 def ncu_traffic(kernel, workload):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """Per-launch DRAM bytes of `kernel` from the committed ncu table (profiles/traffic.txt),
+    if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(path) as f:
-            data = json.load(f)
-    except (OSError, ValueError):
+            lines = [ln for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
         return None
-    ent = data.get("%s|%s" % (kernel, workload))
-    if not ent or ent.get("source_hash") != kernel_source_hash():
-        return None
-    return ent.get("dram_bytes_per_launch")
+    src = kernel_source_hash()
+    for ln in lines:
+        parts = [x.strip() for x in ln.split("|")]
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[3] == src:
+            return int(parts[2])
+    return None
 
 
 def workload_config(p, prec_name):
@@ -195,9 +197,14 @@ def workload_config(p, prec_name):
 # ------------------------------------------------------------------------------------------
 def run_gpu_leg(ch, torch, p, prec, K, W, rank, world, dist, profile_kernels=True):
     """Device-timed run of K bench steps after W warm-up steps; returns a dict."""
+    from paper_1911_03386_gb300 import replicas
     from paper_1911_03386_gb300 import workloads as wl
     npts = len(p["C0"]) * p["nx"] * p["ny"]
-    e = ch.Ensemble.create(p["nx"], p["ny"], p["L"], p["gamma"], p["dt"], p["C0"], wl.BASE_SEED + rank, prec)
+    # replica r: its own members, disjoint counter ranges of the same SplitMix64 stream
+    descs = [dict(nx=p["nx"], ny=p["ny"], L=p["L"], gamma=p["gamma"], dt=p["dt"], C0=c0, seed=wl.BASE_SEED,
+                  counter_base=replicas.member_counter_base(rank, len(p["C0"]), p["nx"] * p["ny"]) + k * p["nx"] * p["ny"])
+             for k, c0 in enumerate(p["C0"])]
+    e = ch.Ensemble.batch(descs, prec)
     stream = torch.cuda.Stream()
     e.set_stream(stream.cuda_stream)
     e.set_sampling(p["every"], p["t1"], capacity=0)
@@ -249,10 +256,14 @@ def run_gpu_leg(ch, torch, p, prec, K, W, rank, world, dist, profile_kernels=Tru
 def run_e2e_leg(ch, torch, p, prec, K, rank, dist):
     """End to end through the C ABI with host buffers (see module docstring)."""
     import numpy as np
+    from paper_1911_03386_gb300 import replicas
     from paper_1911_03386_gb300 import workloads as wl
     m = len(p["C0"])
     npts = m * p["nx"] * p["ny"]
-    e = ch.Ensemble.create(p["nx"], p["ny"], p["L"], p["gamma"], p["dt"], p["C0"], wl.BASE_SEED + rank, prec)
+    descs = [dict(nx=p["nx"], ny=p["ny"], L=p["L"], gamma=p["gamma"], dt=p["dt"], C0=c0, seed=wl.BASE_SEED,
+                  counter_base=replicas.member_counter_base(rank, m, p["nx"] * p["ny"]) + k * p["nx"] * p["ny"])
+             for k, c0 in enumerate(p["C0"])]
+    e = ch.Ensemble.batch(descs, prec)
     e.set_sampling(p["every"], p["t1"], capacity=0)
     # the job's input: every member's initial field, in page-locked host memory
     host_in = torch.empty(npts, dtype=torch.float64).pin_memory()
@@ -376,27 +387,20 @@ def main():
         nreq = args.serving_requests
         at_rate = run_serving_leg(ch, torch, nreq, wl.SERVING["rate"], wl.BASE_SEED, ch.CH_FP32)
         mean_work = at_rate["offered"] / wl.SERVING["rate"]
-        steady_rate = 0.7 * at_rate["capacity"] / mean_work
+        steady_rate = 0.5 * at_rate["capacity"] / mean_work
         steady = run_serving_leg(ch, torch, nreq, steady_rate, wl.BASE_SEED + 1, ch.CH_FP32)
         serving = {"workload": wl.SERVING["name"], "precision": "fp32",
                    "sample": "%d requests per leg (n in {64..1024}^2, horizons U[1000, 50000], C0 ~ U[0, 0.5])"
                              % nreq, "at_workload_rate": at_rate, "at_0.7_capacity": steady}
 
+    from paper_1911_03386_gb300 import replicas
+    tdist = torch.distributed if dist else None
+
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, tdist, device="cuda")
 
     def gather_avg(avg):
-        if not dist:
-            return avg
-        import numpy as np
-        t = torch.tensor(avg, dtype=torch.float64, device="cuda")
-        out = [torch.empty_like(t) for _ in range(world)]
-        torch.distributed.all_gather(out, t)
-        return np.concatenate([o.cpu().numpy() for o in out])
+        return replicas.gather_members(avg, tdist, device="cuda")
 
     ms64 = max_over_ranks(r64["ms"])
     total_pts = r64["pts"] * world
@@ -423,13 +427,9 @@ def main():
     import numpy as np
 
     def beta_stats(avg):
-        out = {}
         m = len(p["C0"])
-        for c0 in sorted(set(p["C0"])):
-            idx = [k for k in range(len(avg)) if p["C0"][k % m] == c0]
-            v = np.array([avg[k] for k in idx])
-            out["C0=%g" % c0] = {"mean": float(v.mean()), "se": float(v.std(ddof=1) / math.sqrt(len(v))), "n": len(v)}
-        return out
+        labels = [p["C0"][k % m] for k in range(len(avg))]
+        return {"C0=%g" % c0: v for c0, v in replicas.ensemble_stats(avg, labels).items()}
 
     npts = len(p["C0"]) * p["nx"] * p["ny"]
 
