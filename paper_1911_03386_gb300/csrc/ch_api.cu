@@ -207,8 +207,12 @@ int fill_params(const ch_member_desc& d, int precision, MemberParams* p) {
   return CH_OK;
 }
 
+// C tile (nr+4 rows, dense pitch when rows move in 16-byte pieces) + mu tile (nr+2 rows,
+// pitch nx+1) + the FP64 reduction buffer; R' and the row sweep reuse the C tile's memory.
 size_t rows_smem_bytes(int nr, int nx, size_t elt, int threads) {
-  size_t b = (size_t)(2 * nr + 6) * (nx + 1) * elt;
+  const int lc = (nx * (int)elt) % 16 == 0 ? nx : nx + 1;
+  const size_t c_region = std::max((size_t)(nr + 4) * lc, (size_t)nr * (nx + 1));
+  size_t b = (c_region + (size_t)(nr + 2) * (nx + 1)) * elt;
   b = (b + 15) & ~(size_t)15;
   return b + (size_t)2 * (threads / 32) * sizeof(double);
 }
@@ -262,8 +266,8 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     int bs = stream ? std::min(p.ny, 32) : std::min(p.ny, want_bs);
     while (bs > 1 && !stream && sweep_smem_bytes(bs, p.nx, h->elt) > kSmemMax) bs = (bs + 1) / 2;
     int bc = stream ? std::min(p.nx, 32) : std::min(p.nx, want_bc);
-    while (bc > 1 && !stream && cols_smem_bytes(bc, p.ny, h->elt, persist) > kSmemMax) bc = (bc + 1) / 2;
-    if (!stream && cols_smem_bytes(bc, p.ny, h->elt, persist) > kSmemMax)
+    while (bc > 1 && !stream && cols_smem_bytes(bc + 3, p.ny, h->elt, persist) > kSmemMax) bc = (bc + 1) / 2;
+    if (!stream && cols_smem_bytes(bc + 3, p.ny, h->elt, persist) > kSmemMax)
       return fail(CH_EINVAL, "column too long for shared memory");
     p.cols_p = t.cols_p > 0 ? t.cols_p : (f64 ? 1 : std::max(1, std::min(threads / bc, p.ny / 64)));
     if (bc * p.cols_p > threads) p.cols_p = std::max(1, threads / bc);
@@ -283,11 +287,12 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     int q = 0;
     for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
     sh.rows_smem = std::max(sh.rows_smem, rows_smem_bytes(br, p.nx, h->elt, threads));
-    if (!stream) {
-      sh.cols_smem = std::max(sh.cols_smem, cols_smem_bytes(bc, p.ny, h->elt, persist));
-      sh.cols_panel_cap = std::max(sh.cols_panel_cap, (int)cols_panel_elems(bc, p.ny));
-    }
+    if (!stream) sh.cols_panel_cap = std::max(sh.cols_panel_cap, (int)cols_panel_elems(bc, p.ny));
   }
+  // Panel buffers start on 16-byte boundaries (the 16-byte copies need it): round the
+  // panel capacity to 4 elements and size the shared memory from the rounded capacity.
+  sh.cols_panel_cap = (sh.cols_panel_cap + 3) / 4 * 4;
+  if (!stream) sh.cols_smem = (size_t)(persist ? 4 : 2) * sh.cols_panel_cap * h->elt;
   sh.cols_persist = persist ? 1 : 0;
   if (!stream && !rt.empty()) {
     int sms = 0, dev = 0;

@@ -94,8 +94,27 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+// Rows of a field can be moved in 16-byte pieces when a row is a whole number of them
+// (member bases are 16-byte aligned); tiles then use the dense pitch nx.
+template <typename T>
+__device__ __forceinline__ bool rows_vec_ok(int nx) {
+  return (nx * (int)sizeof(T)) % 16 == 0;
+}
+
+// Pitch of a C tile: dense when rows move in 16-byte pieces, else nx + 1.
+template <typename T>
+__device__ __forceinline__ int ctile_pitch(int nx) {
+  return rows_vec_ok<T>(nx) ? nx : nx + 1;
+}
+
 // Rows j_first .. j_first+nrows-1 (periodic in j) of an ny x nx field -> shared rows of
-// pitch ld, one warp per row.  The caller waits (cp_async_wait_all + __syncthreads).
+// pitch ld, one warp per row; 16-byte copies when rows_vec_ok (then ld must be nx).  The
+// caller waits (cp_async_wait_all + __syncthreads).
 template <typename T>
 __device__ __forceinline__ void load_rows_async(T* dst, int ld, const T* __restrict__ field, int nx, int ny,
                                                 int j_first, int nrows) {
@@ -106,7 +125,13 @@ __device__ __forceinline__ void load_rows_async(T* dst, int ld, const T* __restr
     if (j >= ny) j -= ny;
     const T* src = field + (int64_t)j * nx;
     T* d = dst + (size_t)r * ld;
-    for (int i = lane; i < nx; i += 32) cp_async_elem(d + i, src + i);
+    if (rows_vec_ok<T>(nx) && ld == nx) {
+      const int nv = nx * (int)sizeof(T) / 16;
+      for (int q = lane; q < nv; q += 32)
+        cp_async16(reinterpret_cast<char*>(d) + 16 * q, reinterpret_cast<const char*>(src) + 16 * q);
+    } else {
+      for (int i = lane; i < nx; i += 32) cp_async_elem(d + i, src + i);
+    }
   }
 }
 
@@ -138,7 +163,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
 // the FP32 form's observables so that dF/dt is the FP64 functional of the FP32 field.
 template <typename T>
 __device__ __forceinline__ double mu64_at(const T* Cs, int ld, int r, int i, int nx, double a, double bx,
-                                          double by) {
+                                          double by) {  // ld: C tile pitch
   const T* c0 = Cs + (size_t)r * ld;
   const int ie = (i + 1 == nx) ? 0 : i + 1;
   const int iw = (i == 0) ? nx - 1 : i - 1;
@@ -333,15 +358,15 @@ __device__ __forceinline__ void chunk_sweep_inplace(T* line, int es, int n, int 
   }
 }
 
-// mu on nrows rows: Ms row r <- C tile row r+1 (C tile rows r .. r+2 are read).
+// mu on nrows rows: Ms row r (pitch lm) <- C tile row r+1 (pitch lc; rows r .. r+2 read).
 template <typename T>
-__device__ __forceinline__ void compute_mu(const T* Cs, T* Ms, int ld, int nx, int nrows, T a, T bx, T by) {
+__device__ __forceinline__ void compute_mu(const T* Cs, int lc, T* Ms, int lm, int nx, int nrows, T a, T bx, T by) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int r = warp; r < nrows; r += nwarps) {
-    const T* c0 = Cs + (size_t)(r + 1) * ld;
-    const T* cm = c0 - ld;
-    const T* cp = c0 + ld;
-    T* mrow = Ms + (size_t)r * ld;
+    const T* c0 = Cs + (size_t)(r + 1) * lc;
+    const T* cm = c0 - lc;
+    const T* cp = c0 + lc;
+    T* mrow = Ms + (size_t)r * lm;
     for (int i = lane; i < nx; i += 32) {
       const int ie = (i + 1 == nx) ? 0 : i + 1;
       const int iw = (i == 0) ? nx - 1 : i - 1;
@@ -355,16 +380,16 @@ __device__ __forceinline__ void compute_mu(const T* Cs, T* Ms, int ld, int nx, i
 // FP64 partial sums of the F and dF/dt densities over the band's nr rows (C tile rows
 // 2..nr+1, mu rows 1..nr), reduced in fixed order; thread 0 stores them.
 template <typename T>
-__device__ __forceinline__ void band_partials(const T* Cs, const T* Ms, int ld, int nx, int nr, const MemberParams& P,
-                                              double2* slot, double* red) {
+__device__ __forceinline__ void band_partials(const T* Cs, int lc, const T* Ms, int lm, int nx, int nr,
+                                              const MemberParams& P, double2* slot, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   double sF = 0.0, sD = 0.0;
   const double hxi = 1.0 / P.hx, hyi = 1.0 / P.hy, hg = 0.5 * P.gamma;
   for (int r = warp; r < nr; r += nwarps) {
-    const T* c0 = Cs + (size_t)(r + 2) * ld;
-    const T* cp = c0 + ld;
-    const T* m0 = Ms + (size_t)(r + 1) * ld;
-    const T* mp = m0 + ld;
+    const T* c0 = Cs + (size_t)(r + 2) * lc;
+    const T* cp = c0 + lc;
+    const T* m0 = Ms + (size_t)(r + 1) * lm;
+    const T* mp = m0 + lm;
     for (int i = lane; i < nx; i += 32) {
       const int ie = (i + 1 == nx) ? 0 : i + 1;
       const double c = (double)c0[i];
@@ -378,9 +403,9 @@ __device__ __forceinline__ void band_partials(const T* Cs, const T* Ms, int ld, 
         mue = (double)m0[ie];
         mun = (double)mp[i];
       } else {
-        mu = mu64_at(Cs, ld, r + 2, i, nx, P.a, P.bx, P.by);
-        mue = mu64_at(Cs, ld, r + 2, ie, nx, P.a, P.bx, P.by);
-        mun = mu64_at(Cs, ld, r + 3, i, nx, P.a, P.bx, P.by);
+        mu = mu64_at(Cs, lc, r + 2, i, nx, P.a, P.bx, P.by);
+        mue = mu64_at(Cs, lc, r + 2, ie, nx, P.a, P.bx, P.by);
+        mun = mu64_at(Cs, lc, r + 3, i, nx, P.a, P.bx, P.by);
       }
       const double mx = (mue - mu) * hxi;
       const double my = (mun - mu) * hyi;
@@ -464,19 +489,22 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
   bool sample = true;
   if (!OBS_ONLY && !stencil_prologue(tl, st, P, sample)) return;
   const int nx = P.nx, ny = P.ny, j0 = tl.start, nr = tl.count;
-  const int ld = nx + 1;
+  const int lc = ctile_pitch<T>(nx), lm = nx + 1, lr = nx + 1;
+  // R' and the row sweep reuse the C tile's memory (pitch lr) once mu is known
+  const size_t c_region = max((size_t)(nr + 4) * lc, (size_t)nr * lr);
   T* Cs = reinterpret_cast<T*>(smem);
-  T* Ms = Cs + (size_t)(nr + 4) * ld;
-  double* red = red_buffer(smem, (size_t)(2 * nr + 6) * ld * sizeof(T));
+  T* Ms = Cs + c_region;
+  T* Rs = Cs;
+  double* red = red_buffer(smem, (c_region + (size_t)(nr + 2) * lm) * sizeof(T));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-  load_rows_async<T>(Cs, ld, static_cast<const T*>(v.C) + P.offset, nx, ny, j0 - 2, nr + 4);
+  load_rows_async<T>(Cs, lc, static_cast<const T*>(v.C) + P.offset, nx, ny, j0 - 2, nr + 4);
   cp_async_wait_all();
   __syncthreads();
-  compute_mu<T>(Cs, Ms, ld, nx, nr + 2, (T)P.a, (T)P.bx, (T)P.by);
+  compute_mu<T>(Cs, lc, Ms, lm, nx, nr + 2, (T)P.a, (T)P.bx, (T)P.by);
   __syncthreads();
   if (sample) {
-    band_partials<T>(Cs, Ms, ld, nx, nr, P, v.partials + P.partial_base + tl.index, red);
+    band_partials<T>(Cs, lc, Ms, lm, nx, nr, P, v.partials + P.partial_base + tl.index, red);
     __syncthreads();
   }
   if (OBS_ONLY) return;
@@ -484,9 +512,9 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
   {
     const T rho = (T)P.rho, w0 = (T)P.w0;
     for (int r = warp; r < nr; r += nwarps) {
-      const T* m0 = Ms + (size_t)(r + 1) * ld;
-      T* out = Cs + (size_t)r * ld;
-      for (int i = lane; i < nx; i += 32) out[i] = rprime_at<T>(m0, ld, i, nx, rho, w0);
+      const T* m0 = Ms + (size_t)(r + 1) * lm;
+      T* out = Rs + (size_t)r * lr;
+      for (int i = lane; i < nx; i += 32) out[i] = rprime_at<T>(m0, lm, i, nx, rho, w0);
     }
   }
   __syncthreads();
@@ -501,16 +529,16 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
   const bool sweeper = threadIdx.x < nsweep && c0 < c1;
   const T p1 = (T)P.p1x, p2 = (T)P.p2x;
   if (sweep_p == 1) {
-    if (sweeper) line_sweep_inplace<T>(Cs + (size_t)row * ld, 1, nx, P.kx, p1, p2);
+    if (sweeper) line_sweep_inplace<T>(Rs + (size_t)row * lr, 1, nx, P.kx, p1, p2);
   } else {
-    chunk_sweep_inplace<T>(Cs + (size_t)row * ld, 1, nx, c0, c1, P.kx, p1, p2, sweeper);
+    chunk_sweep_inplace<T>(Rs + (size_t)row * lr, 1, nx, c0, c1, P.kx, p1, p2, sweeper);
   }
   __syncthreads();
 
   {
     T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
     for (int r = warp; r < nr; r += nwarps) {
-      const T* src = Cs + (size_t)r * ld;
+      const T* src = Rs + (size_t)r * lr;
       T* dst = W + (int64_t)(j0 + r) * nx;
       for (int i = lane; i < nx; i += 32) dst[i] = src[i];
     }
@@ -529,25 +557,25 @@ __global__ void __launch_bounds__(512) stencil_kernel(DevView v) {
   bool sample = true;
   if (!stencil_prologue(tl, st, P, sample)) return;
   const int nx = P.nx, ny = P.ny, j0 = tl.start, nr = tl.count;
-  const int ld = nx + 1;
+  const int lc = ctile_pitch<T>(nx), lm = nx + 1;
   T* Cs = reinterpret_cast<T*>(smem);
-  T* Ms = Cs + (size_t)(nr + 4) * ld;
-  double* red = red_buffer(smem, (size_t)(2 * nr + 6) * ld * sizeof(T));
+  T* Ms = Cs + (size_t)(nr + 4) * lc;
+  double* red = red_buffer(smem, ((size_t)(nr + 4) * lc + (size_t)(nr + 2) * lm) * sizeof(T));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-  load_rows_async<T>(Cs, ld, static_cast<const T*>(v.C) + P.offset, nx, ny, j0 - 2, nr + 4);
+  load_rows_async<T>(Cs, lc, static_cast<const T*>(v.C) + P.offset, nx, ny, j0 - 2, nr + 4);
   cp_async_wait_all();
   __syncthreads();
-  compute_mu<T>(Cs, Ms, ld, nx, nr + 2, (T)P.a, (T)P.bx, (T)P.by);
+  compute_mu<T>(Cs, lc, Ms, lm, nx, nr + 2, (T)P.a, (T)P.bx, (T)P.by);
   __syncthreads();
-  if (sample) band_partials<T>(Cs, Ms, ld, nx, nr, P, v.partials + P.partial_base + tl.index, red);
+  if (sample) band_partials<T>(Cs, lc, Ms, lm, nx, nr, P, v.partials + P.partial_base + tl.index, red);
 
   T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
   const T rho = (T)P.rho, w0 = (T)P.w0;
   for (int r = warp; r < nr; r += nwarps) {
-    const T* m0 = Ms + (size_t)(r + 1) * ld;
+    const T* m0 = Ms + (size_t)(r + 1) * lm;
     T* dst = W + (int64_t)(j0 + r) * nx;
-    for (int i = lane; i < nx; i += 32) dst[i] = rprime_at<T>(m0, ld, i, nx, rho, w0);
+    for (int i = lane; i < nx; i += 32) dst[i] = rprime_at<T>(m0, lm, i, nx, rho, w0);
   }
 }
 
@@ -587,19 +615,39 @@ __global__ void __launch_bounds__(512) rowsweep_kernel(DevView v) {
 // memory traffic in flight through its compute phases.  Without PERSIST each CTA takes one
 // panel.  panel_cap: elements of one panel buffer (max over members of ny * (nc + 1)).
 // -------------------------------------------------------------------------------------
+// Panels move in 16-byte pieces (dense pitch nc) when the panel's rows are 16-byte aligned
+// whole pieces; otherwise element by element with pitch nc + 1.
+template <typename T>
+__device__ __forceinline__ bool panel_vec_ok(int nx, int i0, int nc) {
+  return (nx * (int)sizeof(T)) % 16 == 0 && (i0 * (int)sizeof(T)) % 16 == 0 && (nc * (int)sizeof(T)) % 16 == 0;
+}
+
 template <typename T>
 __device__ __forceinline__ void cols_issue(const DevView& v, int tile, T* Ws, T* Cs) {
   const Tile tl = v.col_tiles[tile];
   if (!v.ms[tl.member].active) return;
   const MemberParams& P = v.mp[tl.member];
-  const int nx = P.nx, ny = P.ny, i0 = tl.start, nc = tl.count, ldc = nc + 1;
+  const int nx = P.nx, ny = P.ny, i0 = tl.start, nc = tl.count;
+  const T* W = static_cast<const T*>(v.W) + P.offset + i0;
+  const T* C = static_cast<const T*>(v.C) + P.offset + i0;
+  if (panel_vec_ok<T>(nx, i0, nc)) {
+    const int nv = nc * (int)sizeof(T) / 16;  // 16-byte pieces per panel row
+    const int tv = threadIdx.x % nv, ty = threadIdx.x / nv, ry = blockDim.x / nv;
+    if (ty >= ry) return;
+    for (int j = ty; j < ny; j += ry) {
+      cp_async16(reinterpret_cast<char*>(Ws + (size_t)j * nc) + 16 * tv,
+                 reinterpret_cast<const char*>(W + (int64_t)j * nx) + 16 * tv);
+      cp_async16(reinterpret_cast<char*>(Cs + (size_t)j * nc) + 16 * tv,
+                 reinterpret_cast<const char*>(C + (int64_t)j * nx) + 16 * tv);
+    }
+    return;
+  }
+  const int ldc = nc + 1;
   const int tx = threadIdx.x % nc, ty = threadIdx.x / nc, ry = blockDim.x / nc;
   if (ty >= ry) return;
-  const T* W = static_cast<const T*>(v.W) + P.offset + i0 + tx;
-  const T* C = static_cast<const T*>(v.C) + P.offset + i0 + tx;
   for (int j = ty; j < ny; j += ry) {
-    cp_async_elem(Ws + (size_t)j * ldc + tx, W + (int64_t)j * nx);
-    cp_async_elem(Cs + (size_t)j * ldc + tx, C + (int64_t)j * nx);
+    cp_async_elem(Ws + (size_t)j * ldc + tx, W + (int64_t)j * nx + tx);
+    cp_async_elem(Cs + (size_t)j * ldc + tx, C + (int64_t)j * nx + tx);
   }
 }
 
@@ -627,7 +675,9 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
     MemberState* st = v.ms + tl.member;
     if (st->active) {
       const MemberParams& P = v.mp[tl.member];
-      const int nx = P.nx, ny = P.ny, i0 = tl.start, nc = tl.count, ldc = nc + 1;
+      const int nx = P.nx, ny = P.ny, i0 = tl.start, nc = tl.count;
+      const bool vec = panel_vec_ok<T>(nx, i0, nc);
+      const int ldc = vec ? nc : nc + 1;
       const int sweep_p = P.cols_p;
       const int nsweep = nc * sweep_p;
       const int chunk = (ny + sweep_p - 1) / sweep_p;
@@ -644,10 +694,36 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
       __syncthreads();
       T* __restrict__ C = static_cast<T*>(v.C) + P.offset;
       const T kap = (T)P.kappa;
-      const int tx = threadIdx.x % nc, ty = threadIdx.x / nc, ry = blockDim.x / nc;
-      if (ty < ry)
-        for (int j = ty; j < ny; j += ry)
-          C[(int64_t)j * nx + i0 + tx] = fma(kap, Ws[(size_t)j * ldc + tx], Cs[(size_t)j * ldc + tx]);
+      if (vec) {
+        // 16-byte pieces: 4 floats or 2 doubles per thread and row
+        constexpr int E = 16 / sizeof(T);
+        const int nv = nc / E;
+        const int tv = threadIdx.x % nv, ty = threadIdx.x / nv, ry = blockDim.x / nv;
+        if (ty < ry)
+          for (int j = ty; j < ny; j += ry) {
+            const T* w = Ws + (size_t)j * nc + E * tv;
+            const T* c = Cs + (size_t)j * nc + E * tv;
+            T* g = C + (int64_t)j * nx + i0 + E * tv;
+            if (E == 4) {
+              float4 o;
+              o.x = (float)fma(kap, w[0], c[0]);
+              o.y = (float)fma(kap, w[1], c[1]);
+              o.z = (float)fma(kap, w[2], c[2]);
+              o.w = (float)fma(kap, w[3], c[3]);
+              *reinterpret_cast<float4*>(g) = o;
+            } else {
+              double2 o;
+              o.x = (double)fma(kap, w[0], c[0]);
+              o.y = (double)fma(kap, w[1], c[1]);
+              *reinterpret_cast<double2*>(g) = o;
+            }
+          }
+      } else {
+        const int tx = threadIdx.x % nc, ty = threadIdx.x / nc, ry = blockDim.x / nc;
+        if (ty < ry)
+          for (int j = ty; j < ny; j += ry)
+            C[(int64_t)j * nx + i0 + tx] = fma(kap, Ws[(size_t)j * ldc + tx], Cs[(size_t)j * ldc + tx]);
+      }
       // Panel 0 finalises the member's sample of this step (partials written by the
       // stencil phase of the same step) and advances the member's step counter.  No other
       // CTA of this launch reads or writes the member's state.

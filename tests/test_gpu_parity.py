@@ -322,6 +322,7 @@ TUNINGS = [
     dict(split=1, stream=0, sweep_band=32, cols_panel=32, cols_p=1),
     dict(split=0, persist=1, cols_panel=8, cols_p=2, threads=128), dict(split=0, persist=0, rows_p=1, cols_p=1),
     dict(split=1, stream=0, persist=1, cols_panel=16, cols_p=1, threads=256),
+    dict(split=0, rows_band=64, rows_p=2, cols_panel=32, cols_p=4, threads=128),
 ]
 
 
@@ -330,7 +331,10 @@ TUNINGS = [
 def test_every_tuning_matches_oracle(orc, prec, tuning):
     descs = []
     base = 0
-    for k, d in enumerate(UNEVEN_SMALL[:4] + [dict(nx=96, ny=80, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.2)]):
+    extra = [dict(nx=96, ny=80, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.2),
+             dict(nx=8, ny=100, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.1),
+             dict(nx=100, ny=12, L=TWO_PI, gamma=0.005, dt=1e-3, C0=-0.1)]
+    for k, d in enumerate(UNEVEN_SMALL[:4] + extra):
         descs.append(dict(d, seed=SEED + 7 * k, counter_base=base))
         base += d["nx"] * d["ny"]
     nsteps = 40
