@@ -748,7 +748,10 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
 constexpr int kStreamWarps = 4;  // warps per CTA of the streaming sweeps
 
 
-constexpr size_t rowstream_smem_bytes(size_t elt) { return (size_t)kStreamWarps * 2 * 32 * 33 * elt; }
+// shared memory of rowstream_kernel: per warp two 32 x (CW+1) tiles, CW = 32 floats / 16 doubles
+constexpr size_t rowstream_smem_bytes(size_t elt) {
+  return (size_t)kStreamWarps * 2 * 32 * ((elt == 8 ? 16 : 32) + 1) * elt;
+}
 
 // Sequence position q of a pass -> column/row index: positions 0..K-1 are the pre-roll,
 // K..K+n-1 the line itself.  Forward: pre-roll over indices -K..-1 (mod n), then 0..n-1.
@@ -820,11 +823,20 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
   if (tl.index == 0 && lane == 0) finalize_sample(v, tl.member, st, P);
 }
 
-// Row sweep, one thread per row, streaming 32-column chunks of the warp's 32 rows
-// through a double-buffered shared tile (pitch 33, conflict-free for both the row-wise
-// cp.async fill and the per-thread column walk).  Tiles: 32-row groups.
+// Row sweep, one thread per row, streaming CW-column chunks of the warp's 32 rows through
+// a double-buffered shared tile (pitch CW+1, conflict-free for the cp.async fill and for
+// the per-thread walk).  CW = 32 floats or 16 doubles, so the tiles of a 4-warp CTA take
+// about 34 KB in both precisions and the whole launch fits the SMs in one wave.
+// Tiles: 32-row groups.
+template <typename T>
+struct StreamChunk {
+  static constexpr int CW = sizeof(T) == 8 ? 16 : 32;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v, int ntiles) {
+  constexpr int CW = StreamChunk<T>::CW;
+  constexpr int RPI = 32 / CW;  // rows covered by one warp-wide copy instruction
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kStreamWarps + w;
@@ -836,21 +848,22 @@ __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v,
   T* Wb = static_cast<T*>(v.W) + P.offset + (int64_t)tl.start * nx;
   const T p1 = (T)P.p1x, p2 = (T)P.p2x;
   const int len = K + nx;
-  const int nchunks = (len + 31) / 32;
-  // this warp's two 32 x 33 buffers
-  T (*buf)[32][33] = reinterpret_cast<T (*)[32][33]>(reinterpret_cast<T*>(smem) + (size_t)w * 2 * 32 * 33);
+  const int nchunks = (len + CW - 1) / CW;
+  // this warp's two 32 x (CW+1) buffers
+  T (*buf)[32][CW + 1] =
+      reinterpret_cast<T (*)[32][CW + 1]>(reinterpret_cast<T*>(smem) + (size_t)w * 2 * 32 * (CW + 1));
+  const int cl = lane % CW, rsub = lane / CW;  // copy geometry: column cl of rows rsub, rsub + RPI, ...
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) {
       // the backward pass reads (through cp.async) what other lanes stored in the forward pass
       __threadfence_block();
       __syncwarp();
     }
-    // prefetch chunk 0
     auto issue = [&](int ch, int b) {
-      const int q = ch * 32 + lane;
+      const int q = ch * CW + cl;
       if (q < len) {
         const int col = pass == 0 ? fwd_index(q, K, nx) : bwd_index(q, K, nx);
-        for (int r = 0; r < nr; ++r) cp_async_elem(&buf[b][r][lane], Wb + (int64_t)r * nx + col);
+        for (int r = rsub; r < nr; r += RPI) cp_async_elem(&buf[b][r][cl], Wb + (int64_t)r * nx + col);
       }
       asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -865,16 +878,16 @@ __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v,
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       }
       __syncwarp();
-      const int qbase = ch * 32;
-      const int cnt = min(32, len - qbase);
+      const int qbase = ch * CW;
+      const int cnt = min(CW, len - qbase);
       if (lane < nr) {
         T* row = buf[b][lane];
-        if (cnt == 32) {
-          T vals[32];
+        if (cnt == CW) {
+          T vals[CW];
 #pragma unroll
-          for (int u = 0; u < 32; ++u) vals[u] = row[u];
+          for (int u = 0; u < CW; ++u) vals[u] = row[u];
 #pragma unroll
-          for (int u = 0; u < 32; ++u) {
+          for (int u = 0; u < CW; ++u) {
             const T val = fma(p1, s1, fma(p2, s2, vals[u]));
             s2 = s1;
             s1 = val;
@@ -891,10 +904,10 @@ __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v,
       }
       __syncwarp();
       // write back the positions that belong to the line itself (not the pre-roll)
-      const int q = qbase + lane;
+      const int q = qbase + cl;
       if (q < len && q >= K) {
         const int col = pass == 0 ? q - K : nx - 1 - (q - K);
-        for (int r = 0; r < nr; ++r) Wb[(int64_t)r * nx + col] = buf[b][r][lane];
+        for (int r = rsub; r < nr; r += RPI) Wb[(int64_t)r * nx + col] = buf[b][r][cl];
       }
       __syncwarp();
     }
