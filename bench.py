@@ -287,13 +287,13 @@ def run_e2e_leg(ch, torch, p, prec, K, rank, dist):
     return {"s": t1 - t0, "pts": npts * K * STEPS_PER_BENCH_STEP, "h2d": npts * 8 / K, "d2h": 3 * m * 8}
 
 
-def run_serving_leg(ch, torch, n_requests, rate, seed, precision, budget_bytes=8 << 30):
+def run_serving_leg(ch, torch, n_requests, rate, seed, precision, budget_bytes=8 << 30, keep=False):
     """Poisson stream of single-run requests through one server; latencies are the
-    library's submit-to-result times."""
+    library's submit-to-result times (keep=True also returns each request's result)."""
     import numpy as np
     from paper_1911_03386_gb300 import workloads as wl
     reqs = wl.request_stream(count=n_requests, rate=rate, seed=seed)
-    lat, ids = [], []
+    lat, ids, results = [], [], []
     with ch.Server(budget_bytes, precision, max_members=4096) as srv:
         t0 = time.perf_counter()
         for r in reqs:
@@ -304,17 +304,27 @@ def run_serving_leg(ch, torch, n_requests, rate, seed, precision, budget_bytes=8
                                   seed=r["seed"], nsteps=r["steps"]))
         t_sub = time.perf_counter() - t0
         for i in ids:
-            lat.append(srv.wait(i, 3600.0)["t_total_s"])
+            res = srv.wait(i, 3600.0)
+            lat.append(res["t_total_s"])
+            results.append(res)
         wall = time.perf_counter() - t0
         st = srv.stats()
     work = sum(r["nx"] * r["ny"] * r["steps"] for r in reqs)
     span = max(reqs[-1]["arrival"], 1e-9)
     cap = st["grid_point_steps"] / max(st["busy_s"], 1e-9)
     lat = np.array(lat)
-    return {"requests": n_requests, "rate_per_s": rate, "p50_s": float(np.percentile(lat, 50)),
+    out = {"requests": n_requests, "rate_per_s": rate, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "max_s": float(lat.max()),
             "throughput": work / wall, "capacity": cap, "offered": work / span, "rho": (work / span) / cap,
             "max_running": st["max_running"], "submit_span_s": t_sub, "wall_s": wall, "unit": UNIT}
+    if keep:
+        out["results"] = results
+    return out
+
+
+def value_estimate(res):
+    """Grid-point-steps/s of one device-timed leg."""
+    return res["pts"] / (res["ms"] * 1e-3)
 
 
 def main():
@@ -389,9 +399,23 @@ def main():
         mean_work = at_rate["offered"] / wl.SERVING["rate"]
         steady_rate = 0.5 * at_rate["capacity"] / mean_work
         steady = run_serving_leg(ch, torch, nreq, steady_rate, wl.BASE_SEED + 1, ch.CH_FP32)
+        # the served FP32 form against the plain FP64 GPU path: the same requests at a rate
+        # the FP64 ensemble throughput sustains, with paired <beta> differences
+        ncmp = max(10, nreq // 3)
+        cmp_rate = 0.5 * value_estimate(r64) / mean_work
+        c32 = run_serving_leg(ch, torch, ncmp, cmp_rate, wl.BASE_SEED + 2, ch.CH_FP32, keep=True)
+        c64 = run_serving_leg(ch, torch, ncmp, cmp_rate, wl.BASE_SEED + 2, ch.CH_FP64, keep=True)
+        import numpy as np
+        d = np.array([a["beta_avg"] - b["beta_avg"] for a, b in zip(c32.pop("results"), c64.pop("results"))])
+        d = d[np.isfinite(d)]
         serving = {"workload": wl.SERVING["name"], "precision": "fp32",
                    "sample": "%d requests per leg (n in {64..1024}^2, horizons U[1000, 50000], C0 ~ U[0, 0.5])"
-                             % nreq, "at_workload_rate": at_rate, "at_0.7_capacity": steady}
+                             % nreq, "at_workload_rate": at_rate, "at_0.5_capacity": steady,
+                   "fp32_vs_fp64_same_requests": {
+                       "requests": ncmp, "rate_per_s": cmp_rate, "fp32": c32, "fp64": c64,
+                       "p99_ratio_fp64_over_fp32": c64["p99_s"] / c32["p99_s"],
+                       "beta_avg_diff_mean": float(d.mean()) if d.size else None,
+                       "beta_avg_diff_max_abs": float(np.abs(d).max()) if d.size else None}}
 
     from paper_1911_03386_gb300 import replicas
     tdist = torch.distributed if dist else None

@@ -221,13 +221,18 @@ void worker_main(ch_server_s* S) {
       server_fail_all(S, rc, "step launch failed");
       return;
     }
-    if (chh::read_states(h, states) != CH_OK) {
+    // states of the occupied slots only (slots are taken lowest-first)
+    int hi = 0;
+    for (int k = 0; k < h->m; ++k)
+      if (h->has(k)) hi = k + 1;
+    states.resize(h->m);
+    if (hi > 0 && chh::copy_out(h, states.data(), h->dms, sizeof(MemberState) * hi, "read member state") != CH_OK) {
       server_fail_all(S, CH_ECUDA, "state read failed");
       return;
     }
     // finished runs: final observables of their fields, then results out
     std::vector<int> done;
-    for (int k = 0; k < h->m; ++k)
+    for (int k = 0; k < hi; ++k)
       if (h->has(k) && states[k].remaining == 0) done.push_back(k);
     if (!done.empty()) {
       cudaError_t e = chk::launch_observe(h->view(), h->precision, h->shape, h->stream);
