@@ -406,16 +406,24 @@ def main():
         c32 = run_serving_leg(ch, torch, ncmp, cmp_rate, wl.BASE_SEED + 2, ch.CH_FP32, keep=True)
         c64 = run_serving_leg(ch, torch, ncmp, cmp_rate, wl.BASE_SEED + 2, ch.CH_FP64, keep=True)
         import numpy as np
-        d = np.array([a["beta_avg"] - b["beta_avg"] for a, b in zip(c32.pop("results"), c64.pop("results"))])
-        d = d[np.isfinite(d)]
+        creqs = wl.request_stream(count=ncmp, rate=cmp_rate, seed=wl.BASE_SEED + 2)
+        pairs = [(a["beta_avg"], b["beta_avg"], r["nx"]) for a, b, r in zip(c32.pop("results"), c64.pop("results"), creqs)
+                 if math.isfinite(a["beta_avg"]) and math.isfinite(b["beta_avg"])]
+        # relative difference for every request; absolute difference for the well-resolved
+        # sizes (n <= 256): at finer grids the factorised scheme damps the grid-scale modes of
+        # the initial noise by only ~1/(4s) per step, and they dominate dF/dt and beta
+        rel = np.array([abs(x - y) / max(abs(y), 1e-300) for x, y, _ in pairs])
+        d = np.array([x - y for x, y, n in pairs if n <= 256])
         serving = {"workload": wl.SERVING["name"], "precision": "fp32",
                    "sample": "%d requests per leg (n in {64..1024}^2, horizons U[1000, 50000], C0 ~ U[0, 0.5])"
                              % nreq, "at_workload_rate": at_rate, "at_0.5_capacity": steady,
                    "fp32_vs_fp64_same_requests": {
                        "requests": ncmp, "rate_per_s": cmp_rate, "fp32": c32, "fp64": c64,
                        "p99_ratio_fp64_over_fp32": c64["p99_s"] / c32["p99_s"],
-                       "beta_avg_diff_mean": float(d.mean()) if d.size else None,
-                       "beta_avg_diff_max_abs": float(np.abs(d).max()) if d.size else None}}
+                       "beta_avg_rel_diff_max": float(rel.max()) if rel.size else None,
+                       "beta_avg_rel_diff_median": float(np.median(rel)) if rel.size else None,
+                       "beta_avg_diff_mean_n_le_256": float(d.mean()) if d.size else None,
+                       "beta_avg_diff_max_abs_n_le_256": float(np.abs(d).max()) if d.size else None}}
 
     from paper_1911_03386_gb300 import replicas
     tdist = torch.distributed if dist else None

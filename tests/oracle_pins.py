@@ -181,6 +181,30 @@ def pin_mode_amplification(orc):
         assert abs(amp - want) <= 1e-7 * abs(want), (kx, ky, amp, want)
 
 
+def pin_nyquist_mode_exact(orc):
+    # The checkerboard (-1)^(i+j) is closed under the step, nonlinear term included:
+    # phi^2 = 1 is constant (the Laplacian removes it) and phi^3 = phi.  So its amplitude
+    # follows a scalar recursion exactly, here at s = gamma dt / h^4 of order 10^3, where the
+    # factorised operator damps the mode by only about 1 / (4 s) per step.
+    nx, ny, L, gamma, dt, C0, eps, nsteps = 96, 80, 0.6, 0.005, 1e-3, 0.3, 0.05, 12
+    hx, hy = L / nx, L / ny
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    phi = np.where((i + j) % 2 == 0, 1.0, -1.0)
+    C = C0 + eps * phi
+    for _ in range(nsteps):
+        orc.step(C, L, gamma, dt)
+    amp = np.sum((C - C0) * phi) / phi.size
+    sigma, ax, ay = gamma * dt, 4 / hx ** 2, 4 / hy ** 2
+    A, d = ax + ay, 3 * C0 * C0 - 1
+    assert sigma * ax * ax / 16 > 1e3  # s_x
+    x = eps
+    for _ in range(nsteps):
+        x -= dt * (A * (d * x + x ** 3) + gamma * A * A * x) / ((1 + sigma * ax * ax) * (1 + sigma * ay * ay))
+    assert 0 < 1 - x / eps < 1e-2
+    assert abs(amp - x) <= 1e-12 * abs(x), (amp, x)
+    assert np.max(np.abs(C - C0 - amp * phi)) <= 1e-12
+
+
 def pin_mass_conservation(orc):
     C = orc.initial_field(40, 24, 0.2, 99, 0)
     m0 = C.sum()
@@ -298,6 +322,7 @@ ALL_PINS = [
     pin_penta_eigenvectors,
     pin_penta_constant,
     pin_mode_amplification,
+    pin_nyquist_mode_exact,
     pin_mass_conservation,
     pin_energy_monotone,
     pin_dFdt_is_time_derivative,

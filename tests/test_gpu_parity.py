@@ -365,3 +365,33 @@ def test_tuning_round_trip_and_errors():
         assert e.tuning()["rows_band"] == 8  # a rejected request keeps the shape in effect
         ch.ch_set_tuning(e.h)  # defaults
         e.step(3)
+
+
+# ------------------------------------------------------------------------------------------
+# The factorised scheme at fine grids: grid-scale diagonal modes decay only by ~1/(4s)
+# per step (s = gamma dt / h^4), the closed-form amplification factor of the scheme
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+def test_fine_grid_nyquist_mode_decays_as_the_scheme_says(prec):
+    n, L, gamma, dt, C0, eps, nsteps = 1024, TWO_PI, 0.005, 1e-3, 0.3, 0.05, 20
+    h = L / n
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    phi = np.where((i + j) % 2 == 0, 1.0, -1.0)  # cos(pi i + pi j): the diagonal Nyquist mode
+    sigma, d = gamma * dt, 3 * C0 * C0 - 1
+    a = 4 / h ** 2
+    A = 2 * a
+    G = 1 - dt * (A * d + gamma * A * A) / (1 + sigma * a * a) ** 2
+    assert 1 - G < 1e-4  # s = 3520: the mode barely decays
+    with ens(n, n, [0.0], gamma, dt, L, prec=prec) as e:
+        e.set_field(0, C0 + eps * phi)
+        e.step(nsteps)
+        got = e.field(0)
+    amp = np.sum((got - C0) * phi) / phi.size
+    # phi^2 = 1 and phi^3 = phi: the mode's amplitude follows a scalar recursion exactly
+    want = eps
+    for _ in range(nsteps):
+        want -= dt * (A * (d * want + want ** 3) + gamma * A * A * want) / (1 + sigma * a * a) ** 2
+    tol = 1e-11 if prec == ch.CH_FP64 else 2e-5
+    assert abs(amp - want) <= tol * abs(want), (amp, want)
+    assert abs(eps - amp) > 0.5 * abs(eps - want)  # the decay itself, not only the amplitude
+    assert np.max(np.abs(got - C0 - amp * phi)) <= (1e-13 if prec == ch.CH_FP64 else 1e-6)
