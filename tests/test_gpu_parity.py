@@ -394,4 +394,7 @@ def test_fine_grid_nyquist_mode_decays_as_the_scheme_says(prec):
     tol = 1e-11 if prec == ch.CH_FP64 else 2e-5
     assert abs(amp - want) <= tol * abs(want), (amp, want)
     assert abs(eps - amp) > 0.5 * abs(eps - want)  # the decay itself, not only the amplitude
-    assert np.max(np.abs(got - C0 - amp * phi)) <= (1e-13 if prec == ch.CH_FP64 else 1e-6)
+    # away from the mode: rounding in R', which the operator passes to the smooth modes with
+    # gain up to (1 + 16 s)^2 ~ 3e9 relative to this one; the oracle's own deviation here
+    # is 7e-13 (FP64)
+    assert np.max(np.abs(got - C0 - amp * phi)) <= (2e-12 if prec == ch.CH_FP64 else 1e-6)
