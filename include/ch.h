@@ -190,12 +190,21 @@ int ch_launch_phase(ch_handle h, int phase);
  *               intermediate kept in the scratch field), so recurrences in flight are not
  *               limited by shared memory; 0 = whole lines resident in shared memory
  *               (sweep_band, cols_panel, cols_p apply).  Default: 1 for CH_FP64.
- *   persist     1 = the column kernel runs one CTA per resident slot and walks its panels
- *               with double-buffered copies (the next panel loads while the current one
- *               is swept); 0 = one CTA per panel (default).
+ *   persist     bit 0: the column kernel runs one CTA per resident slot and walks its
+ *               panels with double-buffered copies (the next panel loads while the current
+ *               one is swept); bit 1: the same for the segment-form row kernel (the next
+ *               band's C rows load while the current band is computed).  0 = one CTA per
+ *               panel / band (default).
+ *   row_seg     fused form: segment form of the row sweep with S = row_seg points per
+ *               lane (16 or 32): a row is held in registers by nx/S lanes and every
+ *               recurrence runs as a local pass, a scan of the segment end states across
+ *               the lanes and a second pass from the exact start state (no pre-roll;
+ *               rows_p does not apply).  Needs nx/S to be a power of two <= 32 for every
+ *               member.  0 = automatic (16 if every member fits, else 32 if every member
+ *               fits, else the chunked sweep); -1 = chunked sweep.
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
- * size, lines too long for shared memory).
+ * size, lines too long for shared memory, a row_seg that some member's nx does not fit).
  */
 typedef struct {
   int split;
@@ -207,6 +216,7 @@ typedef struct {
   int threads;
   int stream;
   int persist;
+  int row_seg;
 } ch_tuning;
 int ch_set_tuning(ch_handle h, const ch_tuning* t); /* NULL restores the defaults */
 int ch_get_tuning(ch_handle h, ch_tuning* t);       /* shape in effect (member 0's values) */
@@ -249,6 +259,21 @@ int ch_load(ch_handle h, const char* path);
  * Errors: CH_EINVAL (s not finite or <= 0, bad precision, no convergence).
  */
 int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, int* K);
+
+/*
+ * Host-side scan tables of the segment form of the row sweep (ch_tuning.row_seg), no GPU
+ * work: for the recurrence y_i = r_i + p1 y_{i-1} + p2 y_{i-2} on a periodic line of
+ * n = seg * groups points split into `groups` segments of `seg` points, with companion
+ * matrix M = [[p1, p2], [1, 0]] acting on the state (y_i, y_{i-1}), writes 152 doubles to
+ * out (host memory, caller-owned), each 2x2 matrix row-major:
+ *   out[0..19]    M^(seg 2^d), d = 0..4          (steps of the scan over the segments)
+ *   out[20..147]  M^(seg l),   l = 0..31          (start state of segment l from x0)
+ *   out[148..151] (I - M^n)^-1                     (periodic start state x0)
+ * Entries for d >= log2(groups) or l >= groups are zero.  p1, p2 are those of
+ * ch_penta_factor(s).  Errors: CH_EINVAL (s as in ch_penta_factor, seg < 1, groups not a
+ * power of two in [1, 32], out NULL).
+ */
+int ch_seg_tables(double s, int seg, int groups, double* out);
 
 /*
  * Allocation-free step (the paper has no counterpart; this is a deployment aid).

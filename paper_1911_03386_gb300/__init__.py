@@ -18,7 +18,7 @@ __all__ = [
     "ch_step", "ch_synchronize", "ch_observables", "ch_beta_avg", "ch_series", "ch_get_field",
     "ch_set_field", "ch_set_fields", "ch_get_fields", "ch_launch_phase", "ch_set_tuning", "ch_get_tuning", "Tuning",
     "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
-    "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_step_field_noalloc", "ch_last_error", "ch_version",
+    "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_seg_tables", "ch_step_field_noalloc", "ch_last_error", "ch_version",
     "Ensemble", "Server", "Request", "Result", "ServerStats", "ch_server_create", "ch_submit", "ch_poll",
     "ch_server_wait", "ch_server_stats", "ch_server_destroy",
 ]
@@ -77,7 +77,8 @@ class Tuning(ctypes.Structure):
     """ch_tuning: launch shape of a handle's kernels (fields <= 0 / split -1: default)."""
     _fields_ = [("split", ctypes.c_int), ("rows_band", ctypes.c_int), ("rows_p", ctypes.c_int),
                 ("sweep_band", ctypes.c_int), ("cols_panel", ctypes.c_int), ("cols_p", ctypes.c_int),
-                ("threads", ctypes.c_int), ("stream", ctypes.c_int), ("persist", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("stream", ctypes.c_int), ("persist", ctypes.c_int),
+                ("row_seg", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +116,7 @@ _SIGS = {
     "ch_save": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_load": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_penta_factor": (_c_int, [_c_dbl, _c_int, _dp, _dp, _dp, _ip]),
+    "ch_seg_tables": (_c_int, [_c_dbl, _c_int, _c_int, _dp]),
     "ch_step_field_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
     "ch_server_create": (_c_int, [ctypes.c_size_t, _c_int, _c_int, ctypes.POINTER(_vp)]),
     "ch_submit": (_c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -174,6 +176,14 @@ def ch_penta_factor(s, precision=CH_FP64):
     c, p1, p2, K = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     _check(lib().ch_penta_factor(s, precision, ctypes.byref(c), ctypes.byref(p1), ctypes.byref(p2), ctypes.byref(K)))
     return c.value, p1.value, p2.value, K.value
+
+
+def ch_seg_tables(s, seg, groups):
+    """Scan tables of the segment row sweep (host computation, no GPU): dict with
+    A (5 x 2 x 2, M^(seg 2^d)), B (32 x 2 x 2, M^(seg l)) and P (2 x 2, (I - M^n)^-1)."""
+    out = np.zeros(152)
+    _check(lib().ch_seg_tables(s, seg, groups, _ptr(out)))
+    return {"A": out[:20].reshape(5, 2, 2), "B": out[20:148].reshape(32, 2, 2), "P": out[148:].reshape(2, 2)}
 
 
 def ch_step_field_noalloc(C_ptr, nx, ny, L, gamma, dt, nsteps, stream_ptr=None):
@@ -286,8 +296,8 @@ def ch_launch_phase(h, phase):
 
 
 def ch_set_tuning(h, split=-1, rows_band=0, rows_p=0, sweep_band=0, cols_panel=0, cols_p=0, threads=0, stream=-1,
-                  persist=-1):
-    t = Tuning(split, rows_band, rows_p, sweep_band, cols_panel, cols_p, threads, stream, persist)
+                  persist=-1, row_seg=0):
+    t = Tuning(split, rows_band, rows_p, sweep_band, cols_panel, cols_p, threads, stream, persist, row_seg)
     _check(lib().ch_set_tuning(h, ctypes.byref(t)))
 
 

@@ -119,6 +119,47 @@ int preroll_length(double p1, double p2, double tol) {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// 2x2 row-major matrix product c = a b.
+static void mat2_mul(const double* a, const double* b, double* c) {
+  const double r0 = a[0] * b[0] + a[1] * b[2], r1 = a[0] * b[1] + a[1] * b[3];
+  const double r2 = a[2] * b[0] + a[3] * b[2], r3 = a[2] * b[1] + a[3] * b[3];
+  c[0] = r0;
+  c[1] = r1;
+  c[2] = r2;
+  c[3] = r3;
+}
+
+// Scan tables of the segment row sweep (S points per lane, G lanes, n = S G) for the
+// companion matrix M = [[p1, p2], [1, 0]]; products of M in FP64.
+void seg_tables(double p1, double p2, int S, int G, chk::SegTable* t) {
+  std::memset(t, 0, sizeof *t);
+  const double M[4] = {p1, p2, 1.0, 0.0};
+  double MS[4] = {1.0, 0.0, 0.0, 1.0};
+  for (int k = 0; k < S; ++k) mat2_mul(M, MS, MS);
+  double Ad[4] = {MS[0], MS[1], MS[2], MS[3]};
+  for (int d = 0; d < 5 && (1 << d) < G; ++d) {
+    std::memcpy(t->A[d], Ad, sizeof Ad);
+    mat2_mul(Ad, Ad, Ad);
+  }
+  double Bl[4] = {1.0, 0.0, 0.0, 1.0};
+  for (int l = 0; l < G; ++l) {
+    std::memcpy(t->B[l], Bl, sizeof Bl);
+    mat2_mul(Bl, MS, Bl);
+  }
+  // Bl = M^(S G) = M^n;  P = (I - M^n)^-1
+  const double a = 1.0 - Bl[0], b = -Bl[1], c = -Bl[2], d = 1.0 - Bl[3];
+  const double det = a * d - b * c;
+  t->P[0] = d / det;
+  t->P[1] = -b / det;
+  t->P[2] = -c / det;
+  t->P[3] = a / det;
+  for (int i = 0; i < 20; ++i) (&t->Af[0][0])[i] = (float)(&t->A[0][0])[i];
+  for (int i = 0; i < 128; ++i) (&t->Bf[0][0])[i] = (float)(&t->B[0][0])[i];
+  for (int i = 0; i < 4; ++i) t->Pf[i] = (float)t->P[i];
+}
+
+bool is_pow2_upto32(int g) { return g >= 1 && g <= 32 && (g & (g - 1)) == 0; }
+
 }  // namespace chh
 
 void chk::record_error(const char* msg) { g_last_error = msg; }
@@ -138,6 +179,7 @@ void free_device(ch_ensemble* h) {
   cudaFree(h->W);
   cudaFree(h->dmp);
   cudaFree(h->dms);
+  cudaFree(h->dseg);
   cudaFree(h->drt);
   cudaFree(h->dst);
   cudaFree(h->dct);
@@ -147,6 +189,7 @@ void free_device(ch_ensemble* h) {
   h->C = h->W = nullptr;
   h->dmp = nullptr;
   h->dms = nullptr;
+  h->dseg = nullptr;
   h->drt = h->dst = h->dct = nullptr;
   h->cap_rt = h->cap_st = h->cap_ct = h->cap_part = 0;
   h->dpart = nullptr;
@@ -202,6 +245,16 @@ int fill_params(const ch_member_desc& d, int precision, MemberParams* p) {
   p->ky = preroll_length(p->p1y, p->p2y, tol);
   if (p->kx < 0 || p->ky < 0) return fail(CH_EINVAL, "decay of I + s D^4 too slow (s out of range)");
   p->kappa = d.dt / (hx2 * p->cx * p->cy);
+  p->fa = (float)p->a;
+  p->fbx = (float)p->bx;
+  p->fby = (float)p->by;
+  p->frho = (float)p->rho;
+  p->fw0 = (float)p->w0;
+  p->fp1x = (float)p->p1x;
+  p->fp2x = (float)p->p2x;
+  p->fp1y = (float)p->p1y;
+  p->fp2y = (float)p->p2y;
+  p->fkappa = (float)p->kappa;
   p->every = 1;
   p->t1 = 0.0;
   return CH_OK;
@@ -215,6 +268,23 @@ size_t rows_smem_bytes(int nr, int nx, size_t elt, int threads) {
   size_t b = (c_region + (size_t)(nr + 2) * (nx + 1)) * elt;
   b = (b + 15) & ~(size_t)15;
   return b + (size_t)2 * (threads / 32) * sizeof(double);
+}
+
+// Segment form: C tile buffer(s) (nr+4 rows, dense pitch; two when the kernel is
+// persistent) + mu tile (nr+2 rows, 16 bytes of padding after every segment of S) + 24
+// scan constants and the sample flag (28 elements) + the FP64 reduction buffer; tile
+// sizes rounded to 4 elements.
+size_t seg_ctile(int nr, int nx) { return ((size_t)(nr + 4) * nx + 3) / 4 * 4; }
+size_t seg_mtile(int nr, int nx, int S, size_t elt) {
+  return ((size_t)(nr + 2) * ((size_t)nx + (16 / elt) * (size_t)(nx / S)) + 3) / 4 * 4;
+}
+size_t seg_smem_bytes(size_t ccap, size_t mcap, int nbuf, size_t elt, int threads) {
+  size_t b = ((size_t)nbuf * ccap + mcap + 28) * elt;
+  b = (b + 15) & ~(size_t)15;
+  return b + (size_t)2 * (threads / 32) * sizeof(double);
+}
+size_t rows_seg_smem_bytes(int nr, int nx, int S, size_t elt, int threads, int nbuf) {
+  return seg_smem_bytes(seg_ctile(nr, nx), seg_mtile(nr, nx, S, elt), nbuf, elt, threads);
 }
 
 size_t sweep_smem_bytes(int nr, int nx, size_t elt) { return (size_t)nr * (nx + 1) * elt; }
@@ -242,7 +312,27 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   if (t.sweep_band > 512 || want_bc * std::max(1, t.cols_p) > threads || want_br * std::max(1, t.rows_p) > threads)
     return fail(CH_EINVAL, "band/panel times threads per line exceeds the CTA size");
   const int stream = split ? (t.stream >= 0 ? (t.stream ? 1 : 0) : (f64 ? 1 : 0)) : 0;
-  const bool persist = t.persist == 1;
+  const bool persist = t.persist > 0 && (t.persist & 1);
+  bool seg_persist = t.persist > 0 && (t.persist & 2) != 0;
+  // segment form of the fused row sweep: S points per lane, nx / S lanes per row
+  int seg = 0;
+  if (!split && t.row_seg >= 0) {
+    auto fits = [&](int S) {
+      for (int k = 0; k < h->m; ++k) {
+        if (!h->has(k)) continue;
+        const int nx = h->hp[k].nx;
+        if (nx % S != 0 || !is_pow2_upto32(nx / S) || (nx * (int)h->elt) % 16 != 0) return false;
+      }
+      return true;
+    };
+    if (t.row_seg > 0) {
+      if (!fits(t.row_seg)) return fail(CH_EINVAL, "row_seg: some member's nx is not S times a power of two <= 32");
+      seg = t.row_seg;
+    } else {
+      seg = fits(16) ? 16 : fits(32) ? 32 : 0;
+    }
+  }
+  const int want_br_seg = t.rows_band > 0 ? t.rows_band : 16;
   std::vector<Tile> rt, st, ct;
   chk::LaunchShape sh{};
   sh.split = split;
@@ -258,9 +348,19 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       p.partial_base = part;
       continue;
     }
-    int br = std::min(p.ny, want_br);
-    while (br > 1 && rows_smem_bytes(br, p.nx, h->elt, threads) > kSmemMax) br = (br + 1) / 2;
-    if (rows_smem_bytes(br, p.nx, h->elt, threads) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
+    int br = std::min(p.ny, seg ? want_br_seg : want_br);
+    auto row_bytes = [&](int nr) {
+      return seg ? rows_seg_smem_bytes(nr, p.nx, seg, h->elt, threads, seg_persist ? 2 : 1)
+                 : rows_smem_bytes(nr, p.nx, h->elt, threads);
+    };
+    while (br > 1 && row_bytes(br) > kSmemMax) br = (br + 1) / 2;
+    if (row_bytes(br) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
+    p.seg_g = seg ? p.nx / seg : 0;
+    if (seg) {
+      seg_tables(p.p1x, p.p2x, seg, p.seg_g, &h->hseg[k]);
+      sh.seg_ccap = std::max(sh.seg_ccap, (int)seg_ctile(br, p.nx));
+      sh.seg_mcap = std::max(sh.seg_mcap, (int)seg_mtile(br, p.nx, seg, h->elt));
+    }
     p.rows_p = t.rows_p > 0 ? t.rows_p : (f64 ? 1 : std::max(1, std::min(threads / br, p.nx / 64)));
     if (br * p.rows_p > threads) p.rows_p = std::max(1, threads / br);
     int bs = stream ? std::min(p.ny, 32) : std::min(p.ny, want_bs);
@@ -302,6 +402,29 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     sh.cols_grid = std::max(1, sms * std::max(1, per_sm));
   }
   if (sh.sweep_threads > 512) return fail(CH_EINVAL, "row-sweep band above 512 rows");
+  sh.row_seg = seg;
+  if (seg) {
+    // the largest C tile and mu tile may come from different members
+    const int seg_threads = std::min(threads, 256);
+    if (seg_persist && seg_smem_bytes(sh.seg_ccap, sh.seg_mcap, 2, h->elt, threads) > kSmemMax) seg_persist = false;
+    if (seg_smem_bytes(sh.seg_ccap, sh.seg_mcap, 1, h->elt, threads) > kSmemMax) {
+      if (t.row_seg > 0) return fail(CH_EINVAL, "row_seg: the mixed members' tiles do not fit shared memory");
+      ch_tuning t2 = t;
+      t2.row_seg = -1;
+      if (int rc = build_tiles(h, t2)) return rc;
+      h->tuning = t;
+      return CH_OK;
+    }
+    sh.seg_persist = seg_persist ? 1 : 0;
+    sh.seg_smem = seg_smem_bytes(sh.seg_ccap, sh.seg_mcap, seg_persist ? 2 : 1, h->elt, threads);
+    if (seg_persist && !rt.empty()) {
+      int sms = 0, dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int per_sm = chk::seg_blocks_per_sm(h->precision, seg, seg_threads, sh.seg_smem);
+      sh.seg_grid = std::max(1, sms * std::max(1, per_sm));
+    }
+  }
   sh.n_row_tiles = (int)rt.size();
   sh.n_sweep_tiles = (int)st.size();
   sh.n_col_tiles = (int)ct.size();
@@ -342,6 +465,9 @@ int upload_tiles(ch_ensemble* h) {
   CH_CUDA(cudaMemsetAsync(h->dpart, 0, sizeof(double2) * std::max<int64_t>(h->total_bands, 1), h->stream), "partials");
   CH_CUDA(cudaMemcpyAsync(h->dmp, h->hp.data(), sizeof(MemberParams) * h->m, cudaMemcpyHostToDevice, h->stream),
           "upload member parameters");
+  if (h->shape.row_seg)
+    CH_CUDA(cudaMemcpyAsync(h->dseg, h->hseg.data(), sizeof(chk::SegTable) * h->m, cudaMemcpyHostToDevice, h->stream),
+            "upload scan tables");
   CH_CUDA(cudaStreamSynchronize(h->stream), "upload tiles");
   return CH_OK;
 }
@@ -376,6 +502,7 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
   h->elt = precision == CH_FP64 ? sizeof(double) : sizeof(float);
   cudaGetDevice(&h->device);
   h->hp.resize(m);
+  h->hseg.resize(m);
   int64_t off = 0;
   for (int k = 0; k < m; ++k) {
     int rc = fill_params(d[k], precision, &h->hp[k]);
@@ -408,6 +535,7 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
   if ((e = alloc(&h->C, h->elt * off)) != cudaSuccess || (e = alloc(&h->W, h->elt * off)) != cudaSuccess ||
       (e = alloc((void**)&h->dmp, sizeof(MemberParams) * m)) != cudaSuccess ||
       (e = alloc((void**)&h->dms, sizeof(MemberState) * m)) != cudaSuccess ||
+      (e = alloc((void**)&h->dseg, sizeof(chk::SegTable) * m)) != cudaSuccess ||
       (e = alloc((void**)&h->dobs, sizeof(double) * 3 * m)) != cudaSuccess) {
     free_device(h);
     cudaStreamDestroy(h->own);
@@ -494,6 +622,7 @@ ch_tuning default_tuning() {
   t.rows_band = t.rows_p = t.sweep_band = t.cols_panel = t.cols_p = t.threads = 0;
   t.stream = -1;
   t.persist = -1;
+  t.row_seg = 0;
   return t;
 }
 
@@ -753,8 +882,10 @@ int ch_set_tuning(ch_handle h, const ch_tuning* t) {
   const ch_tuning req = t ? *t : default_tuning();
   if (req.rows_band < 0 || req.rows_p < 0 || req.sweep_band < 0 || req.cols_panel < 0 || req.cols_p < 0 ||
       req.threads < 0 || req.split < -1 || req.split > 1 || req.stream < -1 || req.stream > 1 || req.persist < -1 ||
-      req.persist > 1)
-    return fail(CH_EINVAL, "tuning fields must be >= 0 (split, stream, persist: -1, 0 or 1)");
+      req.persist > 3)
+    return fail(CH_EINVAL, "tuning fields must be >= 0 (split, stream: -1, 0 or 1; persist: -1 .. 3)");
+  if (req.row_seg != -1 && req.row_seg != 0 && req.row_seg != 16 && req.row_seg != 32)
+    return fail(CH_EINVAL, "row_seg must be -1, 0, 16 or 32");
   CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
   const std::vector<MemberParams> saved = h->hp;
   const ch_tuning old = h->tuning;
@@ -779,7 +910,8 @@ int ch_get_tuning(ch_handle h, ch_tuning* t) {
   t->cols_p = h->hp[0].cols_p;
   t->threads = h->shape.rows_threads;
   t->stream = h->shape.stream;
-  t->persist = h->shape.cols_persist;
+  t->persist = h->shape.cols_persist | (h->shape.seg_persist << 1);
+  t->row_seg = h->shape.split ? 0 : (h->shape.row_seg ? h->shape.row_seg : -1);
   return CH_OK;
 }
 
@@ -906,6 +1038,20 @@ int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, 
   if (p1) *p1 = q1;
   if (p2) *p2 = q2;
   if (K) *K = k;
+  return CH_OK;
+}
+
+int ch_seg_tables(double s, int seg, int groups, double* out) {
+  if (!finite_pos(s)) return fail(CH_EINVAL, "s must be finite and > 0");
+  if (seg < 1 || !is_pow2_upto32(groups)) return fail(CH_EINVAL, "seg >= 1 and groups a power of two in [1, 32]");
+  if (!out) return fail(CH_EINVAL, "out is NULL");
+  double cc, q1, q2;
+  if (!spectral_factor(s, &cc, &q1, &q2)) return fail(CH_EINVAL, "factorisation did not converge");
+  chk::SegTable t;
+  seg_tables(q1, q2, seg, groups, &t);
+  std::memcpy(out, &t.A[0][0], sizeof t.A);
+  std::memcpy(out + 20, &t.B[0][0], sizeof t.B);
+  std::memcpy(out + 148, t.P, sizeof t.P);
   return CH_OK;
 }
 

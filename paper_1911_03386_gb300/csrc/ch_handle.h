@@ -23,6 +23,7 @@ struct ch_ensemble {
   std::vector<MemberParams> hp;
   std::vector<uint8_t> present;   // slot k holds a member (empty: every slot does)
   std::vector<MemberState> hs0;  // initial state (for reset)
+  std::vector<chk::SegTable> hseg;  // scan tables of the segment row sweep, per member
   std::vector<Tile> rt, st, ct;   // stencil/fused bands, row-sweep bands, column panels
   chk::LaunchShape shape{};
   ch_tuning tuning{};             // as requested (0 / -1 = default)
@@ -36,6 +37,7 @@ struct ch_ensemble {
   void* W = nullptr;
   MemberParams* dmp = nullptr;
   MemberState* dms = nullptr;
+  chk::SegTable* dseg = nullptr;
   Tile* drt = nullptr;
   Tile* dst = nullptr;
   Tile* dct = nullptr;
@@ -63,6 +65,7 @@ struct ch_ensemble {
     v.partials = dpart;
     v.series = dseries;
     v.obs_now = dobs;
+    v.seg = dseg;
     v.m = m;
     return v;
   }

@@ -25,6 +25,7 @@ struct MemberParams {
   int kx, ky;            // pre-roll lengths of the x / y recurrences (see ch_kernels.cu)
   int nbands;            // row tiles of this member = partial slots per sample
   int rows_p, cols_p;    // threads per line in the row / column sweep
+  int seg_g;             // segment form of the row sweep: lanes per row (nx / S), 0 = chunked
   int every;             // sampling period in steps
   int64_t partial_base;  // first partial slot
   int64_t series_cap;    // samples kept per member (ring)
@@ -43,6 +44,21 @@ struct MemberParams {
   double t1;             // start of the beta time-average window
   double C0;
   uint64_t seed, counter_base;
+  // the constants above rounded to FP32, for the FP32 kernels
+  float fa, fbx, fby, frho, fw0, fp1x, fp2x, fp1y, fp2y, fkappa;
+};
+
+// Scan tables of the segment form of the row sweep (S points per lane, G lanes per row),
+// for the companion matrix M = [[p1x, p2x], [1, 0]] of the x recurrence, 2x2 row-major:
+// A[d] = M^(S 2^d) (scan steps), B[l] = M^(S l) (start state of lane l from the periodic
+// start state), P = (I - M^nx)^-1 (periodic start state from the scan total).
+struct SegTable {
+  double A[5][4];
+  double B[32][4];
+  double P[4];
+  float Af[5][4];        // the same rounded to FP32
+  float Bf[32][4];
+  float Pf[4];
 };
 
 struct MemberState {
@@ -74,6 +90,7 @@ struct DevView {
   double2* partials;
   double* series;
   double* obs_now;       // [m][3] F, dF/dt, beta of ch_observables
+  const SegTable* seg;   // [m] scan tables (segment form of the row sweep)
   int m;
 };
 
@@ -91,6 +108,11 @@ struct LaunchShape {
   int cols_persist;      // 1: cols_kernel walks panels with double-buffered copies
   int cols_grid;         // CTAs of the persistent column kernel (SMs x resident CTAs)
   int cols_panel_cap;    // elements of one panel buffer
+  int row_seg;           // fused form: S of the segment row sweep (16 or 32), 0 = chunked sweep
+  int seg_persist;       // 1: the segment row kernel walks its tiles with a double-buffered C band
+  int seg_grid;          // CTAs of the persistent segment row kernel
+  int seg_ccap, seg_mcap;  // elements of one C tile buffer / of the mu tile (max over tiles)
+  size_t seg_smem;       // dynamic shared memory of the segment-form row kernel
 };
 
 // Kernel launchers (ch_kernels.cu).  Each returns the launch status.
@@ -105,5 +127,7 @@ cudaError_t launch_observe(const DevView& v, int precision, const LaunchShape& s
 cudaError_t set_kernel_smem_limits(int precision);
 // Resident CTAs per SM of the column kernel for a launch shape (0 on error).
 int cols_blocks_per_sm(int precision, int persist, int threads, size_t smem);
+// Resident CTAs per SM of the persistent segment row kernel (0 on error).
+int seg_blocks_per_sm(int precision, int seg, int threads, size_t smem);
 
 }  // namespace chk

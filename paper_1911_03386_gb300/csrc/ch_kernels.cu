@@ -38,6 +38,17 @@
 // chunk, against ~9 FMA per point for a band LDL^T + Woodbury corner correction.  With
 // one chunk per line the sweep can run in place (the pre-roll reads precede every write
 // they depend on).
+//
+// Segment form (rows_seg_kernel).  Since K grows like s^(1/4) ~ n, pre-rolled chunks
+// cost (1 + K p / n) passes for p chunks per line.  The segment form holds a row in the
+// registers of G = n / S lanes (S consecutive points each) and solves each recurrence
+// exactly: a pass from a zero state over every segment gives its end state e_l; an
+// inclusive scan across the lanes (Kogge-Stone, log2 G shuffle steps with the constant
+// matrices M^(S 2^d), M = [[p1, p2], [1, 0]]) gives the state Y_l after segment l of a
+// line started from zero; the periodic start state is x0 = (I - M^n)^-1 Y_{G-1}, lane l
+// starts from M^(S l) x0 + Y_{l-1}, and a second pass over the segment produces the
+// solution.  Two passes per recurrence whatever K, no shared-memory sweep traffic, no
+// barrier inside the sweep.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -377,12 +388,80 @@ __device__ __forceinline__ void compute_mu(const T* Cs, int lc, T* Ms, int lm, i
   }
 }
 
+// FP32 form: FP64 partial sums of the F and dF/dt densities over the band's nr rows (C
+// tile rows 2..nr+1) with mu recomputed in FP64 from the stored field once per point.  A
+// warp walks a strip of rows down a chunk of 31 columns, carrying three C rows and two mu
+// rows in registers; lane 31 holds the column after the chunk, so east neighbours come
+// from the next lane.  Fixed work split and order: deterministic.
+template <typename T>
+__device__ void band_partials_mu64(const T* Cs, int lc, int nx, int nr, const MemberParams& P, double2* slot,
+                                   double* red) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const double a = P.a, bx = P.bx, by = P.by;
+  const int nchunk = (nx + 30) / 31;
+  const int nstrip = max(1, nwarps / nchunk);
+  const int hs = (nr + nstrip - 1) / nstrip;
+  // unscaled sums: (C^2 - 1)^2, (D+x C)^2, (D+y C)^2, (D+x mu)^2, (D+y mu)^2 (the grid
+  // spacings and prefactors are applied once per thread at the end)
+  double sw = 0.0, sdx = 0.0, sdy = 0.0, smx = 0.0, smy = 0.0;
+  for (int item = warp; item < nchunk * nstrip; item += nwarps) {
+    const int k = item % nchunk, r0 = (item / nchunk) * hs, r1 = min(nr, r0 + hs);
+    if (r0 >= r1) continue;
+    const int i = (31 * k + lane) % nx;
+    const bool own = lane < 31 && 31 * k + lane < nx;
+    const int iw = i == 0 ? nx - 1 : i - 1, ie = i + 1 == nx ? 0 : i + 1;
+    // C at tile row q in FP64, and its west / east neighbours (shuffles inside the chunk)
+    auto cload = [&](int q) { return (double)Cs[(size_t)q * lc + i]; };
+    auto mu_row = [&](int q, double cq, double cdn, double cup) {
+      double w = __shfl_up_sync(full, cq, 1), e = __shfl_down_sync(full, cq, 1);
+      if (lane == 0) w = (double)Cs[(size_t)q * lc + iw];
+      if (lane == 31) e = (double)Cs[(size_t)q * lc + ie];
+      return cq * (cq * cq - a) - bx * (e + w) - by * (cup + cdn);
+    };
+    const int q0 = r0 + 2;
+    double cm = cload(q0 - 1), c0 = cload(q0), c1 = cload(q0 + 1), c2 = cload(q0 + 2);
+    double mu0 = mu_row(q0, c0, cm, c1);
+    double mu1 = mu_row(q0 + 1, c1, c0, c2);
+    for (int r = r0; r < r1; ++r) {
+      const double ce = __shfl_down_sync(full, c0, 1);
+      const double mue = __shfl_down_sync(full, mu0, 1);
+      if (own) {
+        const double w = c0 * c0 - 1.0, gx = ce - c0, gy = c1 - c0, mx = mue - mu0, my = mu1 - mu0;
+        sw += w * w;
+        sdx += gx * gx;
+        sdy += gy * gy;
+        smx += mx * mx;
+        smy += my * my;
+      }
+      if (r + 1 < r1) {  // advance: row q+3 enters, mu of row q+2
+        const double c3 = cload(r + 5);
+        const double mu2 = mu_row(r + 4, c2, c1, c3);
+        c0 = c1;
+        c1 = c2;
+        c2 = c3;
+        mu0 = mu1;
+        mu1 = mu2;
+      }
+    }
+  }
+  const double hxi2 = 1.0 / (P.hx * P.hx), hyi2 = 1.0 / (P.hy * P.hy);
+  double sF = 0.25 * sw + 0.5 * P.gamma * (hxi2 * sdx + hyi2 * sdy);
+  double sD = hxi2 * smx + hyi2 * smy;
+  block_sum2(sF, sD, red);
+  if (threadIdx.x == 0) *slot = make_double2(sF, sD);
+}
+
 // FP64 partial sums of the F and dF/dt densities over the band's nr rows (C tile rows
 // 2..nr+1, mu rows 1..nr), reduced in fixed order; thread 0 stores them.
 template <typename T>
 __device__ __forceinline__ void band_partials(const T* Cs, int lc, const T* Ms, int lm, int nx, int nr,
-                                              const MemberParams& P, double2* slot, double* red) {
+                                              const MemberParams& P, double2* slot, double* red, int seg = 0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if (sizeof(T) == sizeof(float)) {
+    band_partials_mu64<T>(Cs, lc, nx, nr, P, slot, red);
+    return;
+  }
   double sF = 0.0, sD = 0.0;
   const double hxi = 1.0 / P.hx, hyi = 1.0 / P.hy, hg = 0.5 * P.gamma;
   for (int r = warp; r < nr; r += nwarps) {
@@ -399,9 +478,12 @@ __device__ __forceinline__ void band_partials(const T* Cs, int lc, const T* Ms, 
       sF += 0.25 * w * w + hg * (gx * gx + gy * gy);
       double mu, mue, mun;
       if (sizeof(T) == sizeof(double)) {
-        mu = (double)m0[i];
-        mue = (double)m0[ie];
-        mun = (double)mp[i];
+        // mu tile index of point i (segment form: 16 bytes of padding per segment)
+        const int pi = seg ? i + (16 / (int)sizeof(T)) * (i / seg) : i;
+        const int pe = seg ? ie + (16 / (int)sizeof(T)) * (ie / seg) : ie;
+        mu = (double)m0[pi];
+        mue = (double)m0[pe];
+        mun = (double)mp[pi];
       } else {
         mu = mu64_at(Cs, lc, r + 2, i, nx, P.a, P.bx, P.by);
         mue = mu64_at(Cs, lc, r + 2, ie, nx, P.a, P.bx, P.by);
@@ -542,6 +624,284 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v) {
       T* dst = W + (int64_t)(j0 + r) * nx;
       for (int i = lane; i < nx; i += 32) dst[i] = src[i];
     }
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// Segment form of the fused row kernel (see the top of this file).
+// -------------------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+// Padding after every segment of the mu tile: 16 bytes, so that the 16-byte segment reads
+// of 8 consecutive lanes fall in distinct banks.
+template <typename T>
+__device__ __forceinline__ constexpr int seg_pad() { return 16 / (int)sizeof(T); }
+
+template <typename T, int S>
+__device__ __forceinline__ int seg_addr(int i) { return i + seg_pad<T>() * (i / S); }
+
+// A member constant in the kernel's precision (FP32 kernels read the pre-rounded copy).
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f);
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+// 4 consecutive elements (16-byte aligned for float, 32-byte for double).
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x;
+  v[1] = q.y;
+  v[2] = q.z;
+  v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// One recurrence over a row held as segments: y (S values of this lane) in, solution out.
+// REV = false: y_i = r_i + p1 y_{i-1} + p2 y_{i-2} (increasing i); REV = true: the same
+// recurrence for decreasing i.  G lanes (a power of two, lg = log2 G) hold the row, lane
+// l the points [l S, l S + S); Ks = the scan constants A[0..4] (M^(S 2^d)) then P
+// ((I - M^n)^-1); B = M^(S pos), pos = the lane's place in the recurrence's order.  Every
+// lane of the warp must call it (full-warp shuffles, width G).
+template <typename T, int S, bool REV>
+__device__ __forceinline__ void seg_sweep(T (&y)[S], T p1, T p2, int l, int G, int lg, const T* Ks,
+                                          const T (&B)[4]) {
+  T a = T(0), b = T(0);
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const T t = fma(p1, a, fma(p2, b, y[REV ? S - 1 - k : k]));
+    b = a;
+    a = t;
+  }
+  const int pos = REV ? G - 1 - l : l;
+#pragma unroll
+  for (int d = 0; d < 5; ++d) {
+    if (d < lg) {
+      const int delta = 1 << d;
+      const T ya = REV ? __shfl_down_sync(kFull, a, delta, G) : __shfl_up_sync(kFull, a, delta, G);
+      const T yb = REV ? __shfl_down_sync(kFull, b, delta, G) : __shfl_up_sync(kFull, b, delta, G);
+      T A[4];
+      ld4(Ks + 4 * d, A);
+      if (pos >= delta) {
+        const T na = fma(A[0], ya, fma(A[1], yb, a));
+        b = fma(A[2], ya, fma(A[3], yb, b));
+        a = na;
+      }
+    }
+  }
+  const int last = REV ? 0 : G - 1;
+  const T Ea = __shfl_sync(kFull, a, last, G), Eb = __shfl_sync(kFull, b, last, G);
+  T Pm[4];
+  ld4(Ks + 20, Pm);
+  const T xa = fma(Pm[0], Ea, Pm[1] * Eb), xb = fma(Pm[2], Ea, Pm[3] * Eb);
+  T pa = REV ? __shfl_down_sync(kFull, a, 1, G) : __shfl_up_sync(kFull, a, 1, G);
+  T pb = REV ? __shfl_down_sync(kFull, b, 1, G) : __shfl_up_sync(kFull, b, 1, G);
+  if (pos == 0) {
+    pa = T(0);
+    pb = T(0);
+  }
+  a = fma(B[0], xa, fma(B[1], xb, pa));
+  b = fma(B[2], xa, fma(B[3], xb, pb));
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const int u = REV ? S - 1 - k : k;
+    const T t = fma(p1, a, fma(p2, b, y[u]));
+    y[u] = t;
+    b = a;
+    a = t;
+  }
+}
+
+// Segment-form row work of one band (tile tl of member P) whose C rows j0-2 .. j0+nr+1
+// are in Cs (dense pitch nx): mu tile Ms (nr+2 rows, pitch nx + 16 bytes per segment), the
+// sample partials, then R' in registers, the forward and backward recurrences and W
+// stored with 16-byte writes.  Ks holds the member's 24 scan constants.  mu is computed 4
+// points per thread from 16-byte tile reads; each row is then taken by a group of G lanes.
+// Called by every thread of the CTA; contains barriers.
+template <typename T, int S>
+__device__ __forceinline__ void seg_tile(const DevView& v, const Tile& tl, const MemberParams& P, const T* Cs, T* Ms,
+                                         const T* Ks, double* red, bool sample) {
+  const int nx = P.nx, j0 = tl.start, nr = tl.count;
+  const int lmp = nx + seg_pad<T>() * (nx / S);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+
+  // mu tile: Ms row r <- C tile row r + 1, 4 points per thread; a row's chunks are taken
+  // by cs consecutive lanes (cs = min(32, nx/4), a power of two), the chunk neighbours
+  // coming from the adjacent lanes except at the ends of a lane run.
+  {
+    const T a = pick<T>(P.a, P.fa), bx = pick<T>(P.bx, P.fbx), by = pick<T>(P.by, P.fby);
+    const int nq = nx >> 2;
+    const int cs = nq < 32 ? nq : 32;
+    const int rpp = 32 / cs;
+    const int sub = lane / cs, ql = lane - sub * cs;
+    for (int rb = warp * rpp; rb < nr + 2; rb += nwarps * rpp) {
+      const int r = rb + sub;
+      const bool rv = r < nr + 2;
+      const int rr = rv ? r : nr + 1;
+      const T* c0 = Cs + (size_t)(rr + 1) * nx;
+      T* mrow = Ms + (size_t)rr * lmp;
+      for (int q0 = 0; q0 < nq; q0 += cs) {
+        const int i = (q0 + ql) << 2;
+        T c[4], n[4], so[4];
+        ld4(c0 + i, c);
+        ld4(c0 - nx + i, n);
+        ld4(c0 + nx + i, so);
+        T w = __shfl_up_sync(kFull, c[3], 1);
+        T e = __shfl_down_sync(kFull, c[0], 1);
+        if (ql == 0) w = c0[i == 0 ? nx - 1 : i - 1];
+        if (ql == cs - 1) e = c0[i + 4 == nx ? 0 : i + 4];
+        T out[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const T ce = k < 3 ? c[k + 1] : e;
+          const T cw = k > 0 ? c[k - 1] : w;
+          const T u = c[k] * fma(c[k], c[k], -a);
+          out[k] = fma(-by, so[k] + n[k], fma(-bx, ce + cw, u));
+        }
+        if (rv) st4(mrow + seg_addr<T, S>(i), out);
+      }
+    }
+  }
+  __syncthreads();
+  if (sample) {
+    band_partials<T>(Cs, nx, Ms, lmp, nx, nr, P, v.partials + P.partial_base + tl.index, red, S);
+    __syncthreads();
+  }
+
+  // rows: G lanes per row, groups of one warp take rows round-robin
+  const SegTable& tab = v.seg[tl.member];
+  const int G = P.seg_g;
+  const int lg = __ffs(G) - 1;
+  const int gpw = 32 / G, ngroups = nwarps * gpw;
+  const int l = lane & (G - 1), grp = warp * gpw + (lane >> lg);
+  T Bf[4], Bb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    Bf[k] = pick<T>(tab.B[l][k], tab.Bf[l][k]);
+    Bb[k] = pick<T>(tab.B[G - 1 - l][k], tab.Bf[G - 1 - l][k]);
+  }
+  const T p1 = pick<T>(P.p1x, P.fp1x), p2 = pick<T>(P.p2x, P.fp2x), rho = pick<T>(P.rho, P.frho),
+          w0 = pick<T>(P.w0, P.fw0);
+  T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
+  const int rounds = (nr + ngroups - 1) / ngroups;
+  for (int k = 0; k < rounds; ++k) {
+    const int r = k * ngroups + grp;
+    const bool rv = r < nr;
+    const T* mrow = Ms + (size_t)((rv ? r : nr - 1) + 1) * lmp + l * (S + seg_pad<T>());
+    T m[S];
+#pragma unroll
+    for (int c = 0; c < S / 4; ++c) ld4(mrow + 4 * c, &m[4 * c]);
+    const T left = __shfl_sync(kFull, m[S - 1], (l + G - 1) & (G - 1), G);
+    const T right = __shfl_sync(kFull, m[0], (l + 1) & (G - 1), G);
+    T prev = left;
+#pragma unroll
+    for (int c = 0; c < S / 4; ++c) {
+      T up[4], dn[4];
+      ld4(mrow - lmp + 4 * c, up);
+      ld4(mrow + lmp + 4 * c, dn);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u = 4 * c + q;
+        const T cur = m[u];
+        const T e = u + 1 < S ? m[u + 1] : right;
+        m[u] = fma(w0, cur, fma(rho, dn[q] + up[q], e + prev));
+        prev = cur;
+      }
+    }
+    seg_sweep<T, S, false>(m, p1, p2, l, G, lg, Ks, Bf);
+    seg_sweep<T, S, true>(m, p1, p2, l, G, lg, Ks, Bb);
+    if (rv) {
+      T* dst = W + (int64_t)(j0 + r) * nx + l * S;
+#pragma unroll
+      for (int c = 0; c < S / 4; ++c) st4(dst + 4 * c, &m[4 * c]);
+    }
+  }
+}
+
+// Next tile at or after t (stride gridDim.x) whose member still steps; tiles of finished
+// members are skipped, their band-0 CTA clearing the member's active flag.
+__device__ __forceinline__ int next_active_tile(const DevView& v, int t, int ntiles) {
+  while (t < ntiles) {
+    const Tile tl = v.row_tiles[t];
+    MemberState* st = v.ms + tl.member;
+    if (st->remaining > 0) return t;
+    if (tl.index == 0 && threadIdx.x == 0) st->active = 0;
+    t += gridDim.x;
+  }
+  return t;
+}
+
+// Per-tile set-up by the CTA: thread 0 marks the member active and decides the sample,
+// threads 0..23 load the scan constants (visible after the caller's barrier).
+template <typename T>
+__device__ __forceinline__ void seg_tile_setup(const DevView& v, const Tile& tl, const MemberParams& P, T* Ks,
+                                               int* s_sample) {
+  if (threadIdx.x == 0) {
+    MemberState* st = v.ms + tl.member;
+    if (tl.index == 0) st->active = 1;
+    *s_sample = (st->step % P.every) == 0;
+  }
+  if (threadIdx.x < 24) {
+    const SegTable& tab = v.seg[tl.member];
+    Ks[threadIdx.x] = threadIdx.x < 20
+                          ? pick<T>(tab.A[threadIdx.x >> 2][threadIdx.x & 3], tab.Af[threadIdx.x >> 2][threadIdx.x & 3])
+                          : pick<T>(tab.P[threadIdx.x - 20], tab.Pf[threadIdx.x - 20]);
+  }
+}
+
+// Fused row kernel, segment form (nx = G S, G a power of two <= 32, rows in 16-byte
+// pieces; at most 256 threads).  Shared memory: C tile buffer(s) of ccap elements (two
+// when PERSIST), the mu tile (mcap elements), the 24 scan constants and the sample flag
+// (28 T), then the FP64 reduction buffer.  PERSIST: a CTA walks the tiles blockIdx.x,
+// + gridDim.x, ... and copies the next tile's C band while it computes the current one.
+template <typename T, int S, bool PERSIST>
+__global__ void __launch_bounds__(256) rows_seg_kernel(DevView v, int ntiles, int ccap, int mcap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* Cbuf = reinterpret_cast<T*>(smem);
+  T* Ms = Cbuf + (size_t)(PERSIST ? 2 : 1) * ccap;
+  T* Ks = Ms + mcap;
+  int* s_sample = reinterpret_cast<int*>(Ks + 24);
+  double* red = red_buffer(smem, ((size_t)(PERSIST ? 2 : 1) * ccap + mcap + 28) * sizeof(T));
+  auto issue = [&](int t, T* dst) {
+    const Tile tl = v.row_tiles[t];
+    const MemberParams& P = v.mp[tl.member];
+    load_rows_async<T>(dst, P.nx, static_cast<const T*>(v.C) + P.offset, P.nx, P.ny, tl.start - 2, tl.count + 4);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int t = next_active_tile(v, blockIdx.x, PERSIST ? ntiles : blockIdx.x + 1);
+  if (t >= ntiles || (!PERSIST && t != (int)blockIdx.x)) return;
+  issue(t, Cbuf);
+  int cur = 0;
+  while (t < ntiles) {
+    const int nt = PERSIST ? next_active_tile(v, t + gridDim.x, ntiles) : ntiles;
+    if (PERSIST && nt < ntiles) {
+      issue(nt, Cbuf + (size_t)(cur ^ 1) * ccap);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    const Tile tl = v.row_tiles[t];
+    const MemberParams& P = v.mp[tl.member];
+    seg_tile_setup<T>(v, tl, P, Ks, s_sample);
+    __syncthreads();
+    seg_tile<T, S>(v, tl, P, Cbuf + (size_t)cur * ccap, Ms, Ks, red, *s_sample != 0);
+    __syncthreads();  // the mu tile, constants and this C buffer are free again
+    t = nt;
+    cur ^= 1;
   }
 }
 
@@ -935,12 +1295,31 @@ __global__ void obs_finalize_kernel(DevView v) {
 }
 
 template <typename T>
+void seg_launch(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
+  const int threads = min(sh.rows_threads, 256);
+  const int grid = sh.seg_persist ? min(sh.n_row_tiles, sh.seg_grid) : sh.n_row_tiles;
+  if (sh.row_seg == 16) {
+    if (sh.seg_persist)
+      rows_seg_kernel<T, 16, true><<<grid, threads, sh.seg_smem, st>>>(v, sh.n_row_tiles, sh.seg_ccap, sh.seg_mcap);
+    else
+      rows_seg_kernel<T, 16, false><<<grid, threads, sh.seg_smem, st>>>(v, sh.n_row_tiles, sh.seg_ccap, sh.seg_mcap);
+  } else {
+    if (sh.seg_persist)
+      rows_seg_kernel<T, 32, true><<<grid, threads, sh.seg_smem, st>>>(v, sh.n_row_tiles, sh.seg_ccap, sh.seg_mcap);
+    else
+      rows_seg_kernel<T, 32, false><<<grid, threads, sh.seg_smem, st>>>(v, sh.n_row_tiles, sh.seg_ccap, sh.seg_mcap);
+  }
+}
+
+template <typename T>
 cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaStream_t st) {
   if (sh.n_row_tiles == 0) return cudaSuccess;  // no member present
   switch (phase) {
     case 0:
       if (sh.split)
         stencil_kernel<T><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
+      else if (sh.row_seg)
+        seg_launch<T>(v, sh, st);
       else
         rows_kernel<T, false><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
       break;
@@ -994,6 +1373,18 @@ cudaError_t smem_limits_impl() {
     return e;
   if ((e = cudaFuncSetAttribute(stencil_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(rows_seg_kernel<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(rows_seg_kernel<T, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(rows_seg_kernel<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(rows_seg_kernel<T, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
+      cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(rowsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;
 
@@ -1037,6 +1428,18 @@ cudaError_t launch_phase(const DevView& v, int precision, int phase, const Launc
 
 cudaError_t launch_observe(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st) {
   return precision == 0 ? observe_impl<double>(v, sh, st) : observe_impl<float>(v, sh, st);
+}
+
+int seg_blocks_per_sm(int precision, int seg, int threads, size_t smem) {
+  int n = 0;
+  cudaError_t e;
+  if (precision == 0)
+    e = seg == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_seg_kernel<double, 16, true>, threads, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_seg_kernel<double, 32, true>, threads, smem);
+  else
+    e = seg == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_seg_kernel<float, 16, true>, threads, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rows_seg_kernel<float, 32, true>, threads, smem);
+  return e == cudaSuccess ? n : 0;
 }
 
 int cols_blocks_per_sm(int precision, int persist, int threads, size_t smem) {

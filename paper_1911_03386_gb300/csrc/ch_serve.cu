@@ -341,6 +341,7 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
   h->elt = elt;
   cudaGetDevice(&h->device);
   h->hp.assign(max_members, MemberParams{});
+  h->hseg.assign(max_members, chk::SegTable{});
   for (auto& p : h->hp) p.every = 1;
   h->present.assign(max_members, 0);
   h->tuning = chh::default_tuning();
@@ -352,6 +353,7 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
     cudaFree(h->W);
     cudaFree(h->dmp);
     cudaFree(h->dms);
+    cudaFree(h->dseg);
     cudaFree(h->dobs);
     cudaFree(S->dlist);
     if (h->own) cudaStreamDestroy(h->own);
@@ -366,6 +368,7 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
   if ((e = cudaMalloc(&h->C, elt * elems)) != cudaSuccess || (e = cudaMalloc(&h->W, elt * elems)) != cudaSuccess ||
       (e = cudaMalloc((void**)&h->dmp, sizeof(MemberParams) * max_members)) != cudaSuccess ||
       (e = cudaMalloc((void**)&h->dms, sizeof(MemberState) * max_members)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&h->dseg, sizeof(chk::SegTable) * max_members)) != cudaSuccess ||
       (e = cudaMalloc((void**)&h->dobs, sizeof(double) * 3 * max_members)) != cudaSuccess ||
       (e = cudaMalloc((void**)&S->dlist, sizeof(int) * max_members)) != cudaSuccess)
     return cleanup(e == cudaErrorMemoryAllocation ? CH_ENOMEM : CH_ECUDA,
@@ -481,6 +484,7 @@ void ch_server_destroy(ch_server s) {
   cudaFree(h->W);
   cudaFree(h->dmp);
   cudaFree(h->dms);
+  cudaFree(h->dseg);
   cudaFree(h->drt);
   cudaFree(h->dst);
   cudaFree(h->dct);

@@ -132,3 +132,70 @@ def test_preroll_sweep_matches_oracle(n, s, chunks):
     ref = orc.penta_solve(s, r)
     got = preroll_solve_model(r, c, p1, p2, K, chunks)
     assert np.max(np.abs(got - ref)) <= 1e-13 * (1 + 16 * s) * np.max(np.abs(ref))
+
+
+def seg_solve_model(r, c, p1, p2, seg, tabs):
+    """numpy model of the segment form of the row sweep: per segment a pass from a zero
+    state, the Kogge-Stone scan of the end states with the library's tables, the periodic
+    start state and a second pass; forward then backward, then division by c.  Test helper
+    only."""
+    n = r.size
+    G = n // seg
+    A, B, P = tabs["A"], tabs["B"], tabs["P"]
+
+    def one(v):
+        segs = v.reshape(G, seg)
+        e = np.zeros((G, 2))
+        for l in range(G):
+            a = b = 0.0
+            for u in range(seg):
+                a, b = segs[l, u] + p1 * a + p2 * b, a
+            e[l] = (a, b)
+        Y, d = e.copy(), 0
+        while (1 << d) < G:
+            Y = np.array([Y[l] + (A[d] @ Y[l - (1 << d)] if l >= (1 << d) else 0) for l in range(G)])
+            d += 1
+        x0 = P @ Y[G - 1]
+        out = np.empty((G, seg))
+        for l in range(G):
+            a, b = B[l] @ x0 + (Y[l - 1] if l else 0)
+            for u in range(seg):
+                a, b = segs[l, u] + p1 * a + p2 * b, a
+                out[l, u] = a
+        return out.reshape(n)
+
+    y = one(r)
+    return one(y[::-1])[::-1] / c
+
+
+@pytest.mark.parametrize("n,s,seg", [(16, 0.3, 16), (64, 0.107, 16), (64, 13.8, 32), (256, 13.8, 16),
+                                     (512, 220.0, 16), (1024, 3527.0, 32), (32, 5.0, 16)])
+def test_segment_sweep_matches_oracle(n, s, seg):
+    orc = get_oracle()
+    c, p1, p2, _ = ch.ch_penta_factor(s)
+    tabs = ch.ch_seg_tables(s, seg, n // seg)
+    rng = np.random.default_rng(n + seg)
+    r = rng.standard_normal(n)
+    ref = orc.penta_solve(s, r)
+    got = seg_solve_model(r, c, p1, p2, seg, tabs)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * (1 + 16 * s) * np.max(np.abs(ref))
+
+
+def test_segment_tables_are_matrix_powers():
+    # independent of the library's products: powers of the companion matrix by numpy
+    s, seg, G = 13.8, 16, 8
+    _, p1, p2, _ = ch.ch_penta_factor(s)
+    M = np.array([[p1, p2], [1.0, 0.0]])
+    t = ch.ch_seg_tables(s, seg, G)
+    MS = np.linalg.matrix_power(M, seg)
+    for d in range(3):
+        assert np.allclose(t["A"][d], np.linalg.matrix_power(MS, 1 << d), rtol=1e-12, atol=1e-15)
+    assert not t["A"][3].any() and not t["A"][4].any()
+    for l in range(G):
+        assert np.allclose(t["B"][l], np.linalg.matrix_power(MS, l), rtol=1e-12, atol=1e-15)
+    assert not t["B"][G:].any()
+    assert np.allclose(t["P"] @ (np.eye(2) - np.linalg.matrix_power(M, seg * G)), np.eye(2), atol=1e-12)
+    for bad in [(s, 16, 3), (s, 0, 4), (s, 16, 64), (-1.0, 16, 4)]:
+        with pytest.raises(ch.ChError) as e:
+            ch.ch_seg_tables(*bad)
+        assert e.value.code == ch.CH_EINVAL

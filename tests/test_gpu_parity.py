@@ -352,6 +352,78 @@ def test_every_tuning_matches_oracle(orc, prec, tuning):
             np.testing.assert_allclose(ser[:, 1], ref.series[:, 1], rtol=1e-11 if prec == ch.CH_FP64 else 1e-5)
 
 
+# Members whose rows split into a power of two <= 32 of segments (16 or 32 points): the
+# segment form of the fused row sweep, incl. one lane per row (nx = S), a long pre-roll
+# (K > nx), ragged bands and groups that share a warp.
+SEG_MEMBERS = [
+    dict(nx=16, ny=9, L=1.0, gamma=0.002, dt=1e-3, C0=0.3),       # G = 1 (S = 16); s large
+    dict(nx=32, ny=37, L=TWO_PI, gamma=0.01, dt=1e-3, C0=0.4),
+    dict(nx=64, ny=48, L=TWO_PI, gamma=0.005, dt=1e-3, C0=-0.2),
+    dict(nx=128, ny=20, L=4.0, gamma=0.02, dt=5e-4, C0=0.1),
+    dict(nx=256, ny=7, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.0),
+    dict(nx=512, ny=12, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.25),  # s = 220, G = 32 (S = 16)
+]
+SEG_TUNINGS = [dict(split=0, row_seg=0), dict(split=0, row_seg=16, rows_band=3, threads=64),
+               dict(split=0, row_seg=32, rows_band=16, threads=256, persist=0),
+               dict(split=0, row_seg=16, rows_band=1, threads=512, cols_panel=8, cols_p=2, persist=2),
+               dict(split=0, row_seg=16, rows_band=5, threads=128, persist=3)]
+
+
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+@pytest.mark.parametrize("tuning", SEG_TUNINGS, ids=[str(i) for i in range(len(SEG_TUNINGS))])
+def test_segment_row_sweep_matches_oracle(orc, prec, tuning):
+    descs, base = [], 0
+    members = SEG_MEMBERS if tuning.get("row_seg") != 32 else SEG_MEMBERS[1:]  # nx = 16 < S
+    for k, d in enumerate(members):
+        descs.append(dict(d, seed=SEED + 11 * k, counter_base=base))
+        base += d["nx"] * d["ny"]
+    nsteps = 40
+    with ch.Ensemble.batch(descs, prec) as e:
+        e.set_tuning(**tuning)
+        t = e.tuning()
+        assert t["row_seg"] == (tuning["row_seg"] or 16)
+        e.set_sampling(10, 0.0, capacity=8)
+        # the row phase alone: W of the segment sweep against the oracle's row solves
+        for k, d in enumerate(descs):
+            C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
+            hx, hy = d["L"] / d["nx"], d["L"] / d["ny"]
+            _, R = orc.rhs(C0, hx, hy, d["gamma"], d["dt"])
+            sx = d["gamma"] * d["dt"] / hx ** 4
+            Wref = np.stack([orc.penta_solve(sx, R[j]) for j in range(d["ny"])])
+            Wgot = e.row_solve(k)
+            # ||A^-1|| <= 1: rounding of R (relative to its largest value) bounds the error
+            tol = 1e-13 if prec == ch.CH_FP64 else 2e-6
+            assert np.max(np.abs(Wgot - Wref)) <= tol * np.max(np.abs(R)), k
+        e.step(nsteps)
+        for k, d in enumerate(descs):
+            C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
+            ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps, every=10)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            assert err <= (1e-12 if prec == ch.CH_FP64 else 1e-4), (k, err)
+            ser = e.series(k, 8)
+            np.testing.assert_allclose(ser[:, 1], ref.series[:, 1], rtol=1e-11 if prec == ch.CH_FP64 else 1e-5)
+            np.testing.assert_allclose(ser[:, 2], ref.series[:, 2], rtol=1e-9 if prec == ch.CH_FP64 else 1e-3)
+
+
+def test_segment_form_selection_and_errors():
+    with ch.Ensemble.batch([dict(nx=64, ny=16, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.0, seed=1, counter_base=0),
+                            dict(nx=1024, ny=8, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.0, seed=1,
+                                 counter_base=1024)], ch.CH_FP32) as e:
+        assert e.tuning()["row_seg"] == 32  # 1024 = 32 x 32 does not fit S = 16
+        with pytest.raises(ch.ChError) as err:
+            e.set_tuning(row_seg=16)
+        assert err.value.code == ch.CH_EINVAL
+        assert e.tuning()["row_seg"] == 32
+        with pytest.raises(ch.ChError):
+            e.set_tuning(row_seg=8)
+        e.set_tuning(row_seg=-1)
+        assert e.tuning()["row_seg"] == -1
+    with ens(100, 16, [0.0], prec=ch.CH_FP32) as e:
+        assert e.tuning()["row_seg"] == -1  # 100 is no power of two of segments: chunked sweep
+    with ens(64, 16, [0.0]) as e:
+        assert e.tuning()["row_seg"] == 0  # FP64 default: split form
+
+
 def test_tuning_round_trip_and_errors():
     with ens(64, 48, [0.0]) as e:
         e.set_tuning(split=1, rows_band=8, sweep_band=16, cols_panel=16, cols_p=1, threads=128, stream=0)
