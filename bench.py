@@ -183,6 +183,24 @@ def ncu_traffic(kernel, workload):
     return None
 
 
+def kernel_name(phase, t, elt):
+    """Kernel that runs a phase under tuning t (member 0's kernel classes)."""
+    ty = "double" if elt == 8 else "float"
+    if phase == "stencil":
+        return "stencil_kernel<%s>" % ty
+    if phase == "rowsweep":
+        return ("rowstream_kernel<%s>" if t["stream"] else "rowsweep_kernel<%s>") % ty
+    if phase == "rows":
+        if t["row_seg"] in (16, 32):
+            return "rows_seg_kernel<%s, %d, %s>" % (ty, t["row_seg"], "true" if t["persist"] & 2 else "false")
+        return "rowsT_kernel<%s>" % ty if t["row_seg"] == 1 else "rows_kernel<%s, false>" % ty
+    if t["col_seg"] in (16, 32):
+        return "colseg_kernel<%s, %d>" % (ty, t["col_seg"])
+    if t["split"] and t["stream"]:
+        return "colstream_kernel<%s>" % ty
+    return "cols_kernel<%s, %s>" % (ty, "true" if t["persist"] & 1 else "false")
+
+
 def workload_config(p, prec_name):
     return {"workload": p["name"], "members": len(p["C0"]), "nx": p["nx"], "ny": p["ny"], "L": "2*pi",
             "gamma": p["gamma"], "dt": p["dt"], "time_steps": p["steps"], "C0": "half 0.0, half 0.4",
@@ -249,6 +267,32 @@ def run_gpu_leg(ch, torch, p, prec, K, W, rank, world, dist, profile_kernels=Tru
             if name is None:
                 continue
             out["kernels"][name] = sum(evs[4 * r + ph].elapsed_time(evs[4 * r + ph + 1]) for r in range(reps)) / reps
+    e.close()
+    return out
+
+
+def run_descs_leg(ch, torch, descs, prec, nsteps, every, t1, warm=300):
+    """Device-timed run of an uneven batch (member descriptors) for nsteps time steps after
+    `warm` untimed ones (then reset): grid-point-steps/s, per-member window averages."""
+    e = ch.Ensemble.batch(descs, prec)
+    stream = torch.cuda.Stream()
+    e.set_stream(stream.cuda_stream)
+    e.set_sampling(every, t1, capacity=0)
+    e.step(warm)
+    e.synchronize()
+    e.reset()
+    e.set_sampling(every, t1, capacity=0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    e.step(nsteps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    avg, cnt = e.beta_avg()
+    pts = sum(d["nx"] * d["ny"] for d in descs) * nsteps
+    out = {"value": pts / (ms * 1e-3), "unit": UNIT, "ms_per_time_step": ms / nsteps, "time_steps": nsteps,
+           "tuning": e.tuning(), "beta_avg": avg}
     e.close()
     return out
 
@@ -322,6 +366,12 @@ def run_serving_leg(ch, torch, n_requests, rate, seed, precision, budget_bytes=8
     return out
 
 
+def replicas_stats(values, labels):
+    """Mean, standard error and count of the window-averaged beta per initial mean C0."""
+    from paper_1911_03386_gb300 import replicas
+    return {"C0=%g" % k: v for k, v in replicas.ensemble_stats(values, labels).items()}
+
+
 def value_estimate(res):
     """Grid-point-steps/s of one device-timed leg."""
     return res["pts"] / (res["ms"] * 1e-3)
@@ -338,6 +388,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--no-batches", action="store_true", help="skip the uneven-batch and 1024^2 legs")
+    ap.add_argument("--long-beta", action="store_true",
+                    help="also run the 32 x 1024^2 coarsening ensemble over its whole horizon in both precisions "
+                         "and compare <beta> (minutes of GPU time)")
     args = ap.parse_args()
     K, W = args.steps, args.warmup
     if W < 3:
@@ -425,6 +479,38 @@ def main():
                        "beta_avg_diff_mean_n_le_256": float(d.mean()) if d.size else None,
                        "beta_avg_diff_max_abs_n_le_256": float(np.abs(d).max()) if d.size else None}}
 
+    batches = None
+    if not args.no_batches and rank == 0:
+        # the uneven batch (its whole 2000-step horizon) and the 32 x 1024^2 ensemble (the
+        # first 1000 of its 200 000 steps), both precisions, default kernel classes
+        import numpy as np
+        ub = wl.UNEVEN
+        udescs = wl.uneven_members()
+        lb = wl.LONG_1024
+        ldescs = [dict(nx=lb["nx"], ny=lb["ny"], L=lb["L"], gamma=lb["gamma"], dt=lb["dt"], C0=c0, seed=wl.BASE_SEED,
+                       counter_base=k * lb["nx"] * lb["ny"]) for k, c0 in enumerate(lb["C0"])]
+        batches = {}
+        for name, descs, nsteps, every, t1 in [(ub["name"], udescs, ub["steps"], 100, 0.4),
+                                               (lb["name"], ldescs, 1000, 100, 0.1)]:
+            legs = {}
+            for prec, pname in ((ch.CH_FP32, "fp32"), (ch.CH_FP64, "fp64")):
+                r = run_descs_leg(ch, torch, descs, prec, nsteps, every, t1)
+                r.pop("beta_avg")
+                legs[pname] = r
+            legs["fp32_speedup"] = legs["fp32"]["value"] / legs["fp64"]["value"]
+            batches[name] = legs
+        if args.long_beta:
+            # <beta> over the whole horizon, t in [20, 100] (the paper's window), FP32 vs FP64
+            long = {}
+            for prec, pname in ((ch.CH_FP32, "fp32"), (ch.CH_FP64, "fp64")):
+                r = run_descs_leg(ch, torch, ldescs, prec, lb["steps"], 100, 20.0, warm=100)
+                labels = [d["C0"] for d in ldescs]
+                st = replicas_stats(r.pop("beta_avg"), labels)
+                long[pname] = dict(r, beta_avg=st)
+            long["within_one_se"] = {k: abs(long["fp32"]["beta_avg"][k]["mean"] - long["fp64"]["beta_avg"][k]["mean"])
+                                     <= long["fp64"]["beta_avg"][k]["se"] for k in long["fp64"]["beta_avg"]}
+            batches[lb["name"] + "/whole-horizon"] = long
+
     from paper_1911_03386_gb300 import replicas
     tdist = torch.distributed if dist else None
 
@@ -469,7 +555,7 @@ def main():
         ks = res["kernels"]
         dom = max(ks, key=ks.get)
         flops, words = KERNEL_WORK[dom]
-        tname = "%s_kernel<%s>" % (dom, "double" if elt == 8 else "float")
+        tname = kernel_name(dom, res["tuning"], elt)
         per_launch = {k: {"ms": v, "achieved_tflops": KERNEL_WORK[k][0] * npts / (v * 1e-3) / 1e12,
                           "achieved_gbs": KERNEL_WORK[k][1] * elt * npts / (v * 1e-3) / 1e9} for k, v in ks.items()}
         step_ms = sum(ks.values())
@@ -504,7 +590,8 @@ def main():
             "dtype": "f64", "data": "synthetic", "config": workload_config(p, "fp64"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_line,
             "gpu_launches": r64["launches"], "clocks": r64["clocks"], "fp32": fp32,
-            "beta_avg": beta_stats(avg64), "serving": serving, "kernel_source": kernel_source_hash()}
+            "beta_avg": beta_stats(avg64), "serving": serving, "batches": batches,
+            "kernel_source": kernel_source_hash()}
     print(json.dumps(finite_or_none(line), allow_nan=False), flush=True)
     if dist:
         torch.distributed.destroy_process_group()

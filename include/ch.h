@@ -201,7 +201,23 @@ int ch_launch_phase(ch_handle h, int phase);
  *               the lanes and a second pass from the exact start state (no pre-roll;
  *               rows_p does not apply).  Needs nx/S to be a power of two <= 32 for every
  *               member.  0 = automatic (16 if every member fits, else 32 if every member
- *               fits, else the chunked sweep); -1 = chunked sweep.
+ *               fits, else the chunked sweep); -1 = chunked sweep.  1 = transposed-block
+ *               form (nx = 32 nw, nw <= 16): a warp takes 32 columns of a 32-row band, runs
+ *               the stencil with lane = column straight from HBM, transposes its 32 x 32
+ *               block of R' through shared memory and runs the row recurrences with lane =
+ *               row, joining the nw segments of a row through shared memory (explicit
+ *               only).  Kernel classes are chosen per member (automatic: segment S = 16,
+ *               else S = 32, else chunked), so a run's arithmetic does not depend on the
+ *               other members; an explicit value applies to every member.
+ *   col_seg     segment form of the column kernel with S = col_seg rows per warp (16 or
+ *               32): lanes take adjacent columns, a column's ny/S segments sit in ny/S
+ *               warps, W and C move as coalesced row pieces straight between registers
+ *               and HBM, and each recurrence is a local pass, a combination of the segment
+ *               end states through shared memory and a second pass (no pre-roll, no
+ *               panels in shared memory).  Needs ny/S to be a power of two <= 32 (<= 16 for
+ *               CH_FP64) for every member.  0 = automatic (CH_FP32: 32 if every member
+ *               fits, else 16 if every member fits, else panels; CH_FP64: panels or
+ *               streaming); -1 = panels or streaming.
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
  * size, lines too long for shared memory, a row_seg that some member's nx does not fit).
@@ -217,6 +233,7 @@ typedef struct {
   int stream;
   int persist;
   int row_seg;
+  int col_seg;
 } ch_tuning;
 int ch_set_tuning(ch_handle h, const ch_tuning* t); /* NULL restores the defaults */
 int ch_get_tuning(ch_handle h, ch_tuning* t);       /* shape in effect (member 0's values) */

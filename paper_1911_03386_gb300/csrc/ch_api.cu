@@ -180,6 +180,8 @@ void free_device(ch_ensemble* h) {
   cudaFree(h->dmp);
   cudaFree(h->dms);
   cudaFree(h->dseg);
+  cudaFree(h->dsegy);
+  cudaFree(h->dcst);
   cudaFree(h->drt);
   cudaFree(h->dst);
   cudaFree(h->dct);
@@ -189,7 +191,9 @@ void free_device(ch_ensemble* h) {
   h->C = h->W = nullptr;
   h->dmp = nullptr;
   h->dms = nullptr;
-  h->dseg = nullptr;
+  h->dseg = h->dsegy = nullptr;
+  h->dcst = nullptr;
+  h->cap_cst = 0;
   h->drt = h->dst = h->dct = nullptr;
   h->cap_rt = h->cap_st = h->cap_ct = h->cap_part = 0;
   h->dpart = nullptr;
@@ -307,33 +311,54 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   const int threads = t.threads > 0 ? t.threads : (f64 ? 512 : 256);
   if (threads % 32 || threads > 512) return fail(CH_EINVAL, "threads must be a multiple of 32, at most 512");
   const int want_br = t.rows_band > 0 ? t.rows_band : (f64 ? 16 : 32);
+  const int want_br_seg = t.rows_band > 0 ? t.rows_band : 16;
   const int want_bs = t.sweep_band > 0 ? t.sweep_band : 32;
   const int want_bc = t.cols_panel > 0 ? t.cols_panel : 32;
   if (t.sweep_band > 512 || want_bc * std::max(1, t.cols_p) > threads || want_br * std::max(1, t.rows_p) > threads)
     return fail(CH_EINVAL, "band/panel times threads per line exceeds the CTA size");
   const int stream = split ? (t.stream >= 0 ? (t.stream ? 1 : 0) : (f64 ? 1 : 0)) : 0;
   const bool persist = t.persist > 0 && (t.persist & 1);
-  bool seg_persist = t.persist > 0 && (t.persist & 2) != 0;
-  // segment form of the fused row sweep: S points per lane, nx / S lanes per row
-  int seg = 0;
-  if (!split && t.row_seg >= 0) {
-    auto fits = [&](int S) {
-      for (int k = 0; k < h->m; ++k) {
-        if (!h->has(k)) continue;
-        const int nx = h->hp[k].nx;
-        if (nx % S != 0 || !is_pow2_upto32(nx / S) || (nx * (int)h->elt) % 16 != 0) return false;
-      }
-      return true;
-    };
-    if (t.row_seg > 0) {
-      if (!fits(t.row_seg)) return fail(CH_EINVAL, "row_seg: some member's nx is not S times a power of two <= 32");
-      seg = t.row_seg;
-    } else {
-      seg = fits(16) ? 16 : fits(32) ? 32 : 0;
-    }
+  const bool seg_persist = t.persist > 0 && (t.persist & 2) != 0;
+  const int max_wp = f64 ? 16 : 32;
+
+  // Kernel class of each member, from its own size and the tuning only (a run's arithmetic
+  // must not depend on the other members): segment-form rows with S = 16 or 32 points per
+  // lane (nx / S lanes per row, a power of two <= 32) or chunked sweeps; segment-form
+  // columns with S = 32 or 16 rows per warp (ny / S warps) or panels / streaming.
+  auto row_fits = [&](const MemberParams& p, int S) {
+    return p.nx % S == 0 && is_pow2_upto32(p.nx / S) && (p.nx * (int)h->elt) % 16 == 0;
+  };
+  auto col_fits = [&](const MemberParams& p, int S) {
+    return p.ny % S == 0 && is_pow2_upto32(p.ny / S) && p.ny / S <= max_wp;
+  };
+  // transposed-block rows: nx = 32 nw, nw <= 16
+  auto rowT_fits = [&](const MemberParams& p) { return p.nx % 32 == 0 && p.nx / 32 <= 16; };
+  auto row_class = [&](const MemberParams& p) {  // 1: transposed-block, 16 / 32: segment, 0: chunked
+    if (split || t.row_seg < 0) return 0;
+    if (t.row_seg > 0) return t.row_seg;
+    return row_fits(p, 16) ? 16 : row_fits(p, 32) ? 32 : 0;
+  };
+  auto col_class = [&](const MemberParams& p) {
+    if (t.col_seg < 0 || (t.col_seg == 0 && f64)) return 0;
+    if (t.col_seg > 0) return t.col_seg;
+    return col_fits(p, 32) ? 32 : col_fits(p, 16) ? 16 : 0;
+  };
+  int cwarps[2] = {8, 8};  // warps per CTA of the segment column kernel, S = 16 / 32
+  for (int k = 0; k < h->m; ++k) {
+    if (!h->has(k)) continue;
+    const MemberParams& p = h->hp[k];
+    if (t.row_seg == 1 && !split && !rowT_fits(p))
+      return fail(CH_EINVAL, "row_seg 1: some member's nx is not 32 times at most 16");
+    if (t.row_seg > 1 && !split && !row_fits(p, t.row_seg))
+      return fail(CH_EINVAL, "row_seg: some member's nx is not S times a power of two <= 32");
+    if (t.col_seg > 0 && !col_fits(p, t.col_seg))
+      return fail(CH_EINVAL, "col_seg: some member's ny is not S times a power of two <= 32 (<= 16 for FP64)");
+    const int cc = col_class(p);
+    if (cc) cwarps[cc == 32] = std::max(cwarps[cc == 32], p.ny / cc);
   }
-  const int want_br_seg = t.rows_band > 0 ? t.rows_band : 16;
-  std::vector<Tile> rt, st, ct;
+
+  std::vector<Tile> rts[3], csts[2], st, ct;  // rows: S = 16, S = 32, chunked; columns: S = 16, 32
+  std::vector<Tile> rtT[17];                   // rows, transposed-block form, by nw
   chk::LaunchShape sh{};
   sh.split = split;
   sh.stream = stream;
@@ -348,31 +373,42 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       p.partial_base = part;
       continue;
     }
-    int br = std::min(p.ny, seg ? want_br_seg : want_br);
+    const int rc = row_class(p), cc = col_class(p), ri = rc == 16 ? 0 : rc == 32 ? 1 : 2;
+    const bool seg = rc > 1;
+    int br = std::min(p.ny, rc == 1 ? 32 : seg ? want_br_seg : want_br);
     auto row_bytes = [&](int nr) {
-      return seg ? rows_seg_smem_bytes(nr, p.nx, seg, h->elt, threads, seg_persist ? 2 : 1)
+      return seg ? rows_seg_smem_bytes(nr, p.nx, rc, h->elt, threads, seg_persist ? 2 : 1)
                  : rows_smem_bytes(nr, p.nx, h->elt, threads);
     };
-    while (br > 1 && row_bytes(br) > kSmemMax) br = (br + 1) / 2;
-    if (row_bytes(br) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
-    p.seg_g = seg ? p.nx / seg : 0;
+    while (rc != 1 && br > 1 && row_bytes(br) > kSmemMax) br = (br + 1) / 2;
+    // segment form without an explicit band: at least two CTAs per SM (wide rows)
+    if (seg && t.rows_band <= 0)
+      while (br > 4 && row_bytes(br) > kSmemMax / 2) br = (br + 1) / 2;
+    if (rc != 1 && row_bytes(br) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
+    p.seg_g = seg ? p.nx / rc : 0;
+    p.row_t = rc == 1 ? p.nx / 32 : 0;
+    p.col_s = cc;
+    if (rc == 1) seg_tables(p.p1x, p.p2x, 32, p.nx / 32, &h->hseg[k]);
     if (seg) {
-      seg_tables(p.p1x, p.p2x, seg, p.seg_g, &h->hseg[k]);
-      sh.seg_ccap = std::max(sh.seg_ccap, (int)seg_ctile(br, p.nx));
-      sh.seg_mcap = std::max(sh.seg_mcap, (int)seg_mtile(br, p.nx, seg, h->elt));
+      seg_tables(p.p1x, p.p2x, rc, p.seg_g, &h->hseg[k]);
+      sh.seg_ccap[ri] = std::max(sh.seg_ccap[ri], (int)seg_ctile(br, p.nx));
+      sh.seg_mcap[ri] = std::max(sh.seg_mcap[ri], (int)seg_mtile(br, p.nx, rc, h->elt));
     }
     p.rows_p = t.rows_p > 0 ? t.rows_p : (f64 ? 1 : std::max(1, std::min(threads / br, p.nx / 64)));
     if (br * p.rows_p > threads) p.rows_p = std::max(1, threads / br);
     int bs = stream ? std::min(p.ny, 32) : std::min(p.ny, want_bs);
     while (bs > 1 && !stream && sweep_smem_bytes(bs, p.nx, h->elt) > kSmemMax) bs = (bs + 1) / 2;
     int bc = stream ? std::min(p.nx, 32) : std::min(p.nx, want_bc);
-    while (bc > 1 && !stream && cols_smem_bytes(bc + 3, p.ny, h->elt, persist) > kSmemMax) bc = (bc + 1) / 2;
-    if (!stream && cols_smem_bytes(bc + 3, p.ny, h->elt, persist) > kSmemMax)
-      return fail(CH_EINVAL, "column too long for shared memory");
+    if (!cc) {
+      while (bc > 1 && !stream && cols_smem_bytes(bc + 3, p.ny, h->elt, persist) > kSmemMax) bc = (bc + 1) / 2;
+      if (!stream && cols_smem_bytes(bc + 3, p.ny, h->elt, persist) > kSmemMax)
+        return fail(CH_EINVAL, "column too long for shared memory");
+    }
     p.cols_p = t.cols_p > 0 ? t.cols_p : (f64 ? 1 : std::max(1, std::min(threads / bc, p.ny / 64)));
     if (bc * p.cols_p > threads) p.cols_p = std::max(1, threads / bc);
     int b = 0;
-    for (int j0 = 0; j0 < p.ny; j0 += br, ++b) rt.push_back(Tile{k, j0, std::min(br, p.ny - j0), b});
+    std::vector<Tile>& rdst = rc == 1 ? rtT[p.nx / 32] : rts[ri];
+    for (int j0 = 0; j0 < p.ny; j0 += br, ++b) rdst.push_back(Tile{k, j0, std::min(br, p.ny - j0), b});
     p.nbands = b;
     p.partial_base = part;
     part += b;
@@ -384,53 +420,65 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
         sh.sweep_threads = std::max(sh.sweep_threads, std::max(128, round_warps(bs)));
       }
     }
-    int q = 0;
-    for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
+    if (cc) {
+      const int wp = p.ny / cc, width = 32 * (cwarps[cc == 32] / wp);
+      seg_tables(p.p1y, p.p2y, cc, wp, &h->hsegy[k]);
+      int q = 0;
+      for (int i0 = 0; i0 < p.nx; i0 += width, ++q)
+        csts[cc == 32].push_back(Tile{k, i0, std::min(width, p.nx - i0), q});
+    } else {
+      int q = 0;
+      for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
+      if (!stream) sh.cols_panel_cap = std::max(sh.cols_panel_cap, (int)cols_panel_elems(bc, p.ny));
+    }
     sh.rows_smem = std::max(sh.rows_smem, rows_smem_bytes(br, p.nx, h->elt, threads));
-    if (!stream) sh.cols_panel_cap = std::max(sh.cols_panel_cap, (int)cols_panel_elems(bc, p.ny));
   }
   // Panel buffers start on 16-byte boundaries (the 16-byte copies need it): round the
   // panel capacity to 4 elements and size the shared memory from the rounded capacity.
   sh.cols_panel_cap = (sh.cols_panel_cap + 3) / 4 * 4;
   if (!stream) sh.cols_smem = (size_t)(persist ? 4 : 2) * sh.cols_panel_cap * h->elt;
   sh.cols_persist = persist ? 1 : 0;
-  if (!stream && !rt.empty()) {
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!stream && !ct.empty()) {
     const int per_sm = chk::cols_blocks_per_sm(h->precision, sh.cols_persist, threads, sh.cols_smem);
     sh.cols_grid = std::max(1, sms * std::max(1, per_sm));
   }
   if (sh.sweep_threads > 512) return fail(CH_EINVAL, "row-sweep band above 512 rows");
-  sh.row_seg = seg;
-  if (seg) {
-    // the largest C tile and mu tile may come from different members
-    const int seg_threads = std::min(threads, 256);
-    if (seg_persist && seg_smem_bytes(sh.seg_ccap, sh.seg_mcap, 2, h->elt, threads) > kSmemMax) seg_persist = false;
-    if (seg_smem_bytes(sh.seg_ccap, sh.seg_mcap, 1, h->elt, threads) > kSmemMax) {
-      if (t.row_seg > 0) return fail(CH_EINVAL, "row_seg: the mixed members' tiles do not fit shared memory");
-      ch_tuning t2 = t;
-      t2.row_seg = -1;
-      if (int rc = build_tiles(h, t2)) return rc;
-      h->tuning = t;
-      return CH_OK;
-    }
-    sh.seg_persist = seg_persist ? 1 : 0;
-    sh.seg_smem = seg_smem_bytes(sh.seg_ccap, sh.seg_mcap, seg_persist ? 2 : 1, h->elt, threads);
-    if (seg_persist && !rt.empty()) {
-      int sms = 0, dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      const int per_sm = chk::seg_blocks_per_sm(h->precision, seg, seg_threads, sh.seg_smem);
-      sh.seg_grid = std::max(1, sms * std::max(1, per_sm));
+  // segment-form rows: shared memory and persistent grid per class (the largest C tile and
+  // mu tile of a class may come from different members)
+  sh.seg_persist = seg_persist ? 1 : 0;
+  for (int c = 0; c < 2; ++c) {
+    sh.rt_seg[c] = (int)rts[c].size();
+    if (rts[c].empty()) continue;
+    const int nbuf = seg_persist ? 2 : 1;
+    sh.seg_smem[c] = seg_smem_bytes(sh.seg_ccap[c], sh.seg_mcap[c], nbuf, h->elt, threads);
+    if (sh.seg_smem[c] > kSmemMax) return fail(CH_EINVAL, "segment row tiles of the mixed members exceed shared memory");
+    if (seg_persist) {
+      const int per_sm = chk::seg_blocks_per_sm(h->precision, c ? 32 : 16, std::min(threads, 256), sh.seg_smem[c]);
+      sh.seg_grid[c] = std::max(1, sms * std::max(1, per_sm));
     }
   }
+  for (int c = 0; c < 2; ++c) {
+    sh.cst_n[c] = (int)csts[c].size();
+    sh.colseg_threads[c] = 32 * cwarps[c];
+    sh.colseg_smem[c] = (size_t)2 * 2 * 32 * cwarps[c] * h->elt;
+  }
+  std::vector<Tile> rt, cst;
+  for (int nw = 1; nw <= 16; ++nw) {
+    sh.rtT_n[nw] = (int)rtT[nw].size();
+    rt.insert(rt.end(), rtT[nw].begin(), rtT[nw].end());
+  }
+  for (int c = 0; c < 3; ++c) rt.insert(rt.end(), rts[c].begin(), rts[c].end());
+  for (int c = 0; c < 2; ++c) cst.insert(cst.end(), csts[c].begin(), csts[c].end());
   sh.n_row_tiles = (int)rt.size();
   sh.n_sweep_tiles = (int)st.size();
   sh.n_col_tiles = (int)ct.size();
   h->rt.swap(rt);
   h->st.swap(st);
   h->ct.swap(ct);
+  h->cst.swap(cst);
   h->shape = sh;
   h->total_bands = part;
   h->tuning = t;
@@ -454,6 +502,7 @@ int upload_tiles(ch_ensemble* h) {
   if ((e = ensure((void**)&h->drt, h->cap_rt, h->rt.size(), sizeof(Tile))) != cudaSuccess ||
       (e = ensure((void**)&h->dst, h->cap_st, h->st.size(), sizeof(Tile))) != cudaSuccess ||
       (e = ensure((void**)&h->dct, h->cap_ct, h->ct.size(), sizeof(Tile))) != cudaSuccess ||
+      (e = ensure((void**)&h->dcst, h->cap_cst, h->cst.size(), sizeof(Tile))) != cudaSuccess ||
       (e = ensure((void**)&h->dpart, h->cap_part, (size_t)h->total_bands, sizeof(double2))) != cudaSuccess) {
     cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? CH_ENOMEM : CH_ECUDA, std::string("tile tables: ") + cudaGetErrorString(e));
@@ -465,9 +514,18 @@ int upload_tiles(ch_ensemble* h) {
   CH_CUDA(cudaMemsetAsync(h->dpart, 0, sizeof(double2) * std::max<int64_t>(h->total_bands, 1), h->stream), "partials");
   CH_CUDA(cudaMemcpyAsync(h->dmp, h->hp.data(), sizeof(MemberParams) * h->m, cudaMemcpyHostToDevice, h->stream),
           "upload member parameters");
-  if (h->shape.row_seg)
+  int n_rowT = 0;
+  for (int nw = 1; nw <= 16; ++nw) n_rowT += h->shape.rtT_n[nw];
+  if (h->shape.rt_seg[0] + h->shape.rt_seg[1] + n_rowT)
     CH_CUDA(cudaMemcpyAsync(h->dseg, h->hseg.data(), sizeof(chk::SegTable) * h->m, cudaMemcpyHostToDevice, h->stream),
             "upload scan tables");
+  if (!h->cst.empty()) {
+    CH_CUDA(cudaMemcpyAsync(h->dcst, h->cst.data(), sizeof(Tile) * h->cst.size(), cudaMemcpyHostToDevice, h->stream),
+            "tiles");
+    CH_CUDA(cudaMemcpyAsync(h->dsegy, h->hsegy.data(), sizeof(chk::SegTable) * h->m, cudaMemcpyHostToDevice,
+                            h->stream),
+            "upload scan tables");
+  }
   CH_CUDA(cudaStreamSynchronize(h->stream), "upload tiles");
   return CH_OK;
 }
@@ -503,6 +561,7 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
   cudaGetDevice(&h->device);
   h->hp.resize(m);
   h->hseg.resize(m);
+  h->hsegy.resize(m);
   int64_t off = 0;
   for (int k = 0; k < m; ++k) {
     int rc = fill_params(d[k], precision, &h->hp[k]);
@@ -536,6 +595,7 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
       (e = alloc((void**)&h->dmp, sizeof(MemberParams) * m)) != cudaSuccess ||
       (e = alloc((void**)&h->dms, sizeof(MemberState) * m)) != cudaSuccess ||
       (e = alloc((void**)&h->dseg, sizeof(chk::SegTable) * m)) != cudaSuccess ||
+      (e = alloc((void**)&h->dsegy, sizeof(chk::SegTable) * m)) != cudaSuccess ||
       (e = alloc((void**)&h->dobs, sizeof(double) * 3 * m)) != cudaSuccess) {
     free_device(h);
     cudaStreamDestroy(h->own);
@@ -623,6 +683,7 @@ ch_tuning default_tuning() {
   t.stream = -1;
   t.persist = -1;
   t.row_seg = 0;
+  t.col_seg = 0;
   return t;
 }
 
@@ -884,8 +945,10 @@ int ch_set_tuning(ch_handle h, const ch_tuning* t) {
       req.threads < 0 || req.split < -1 || req.split > 1 || req.stream < -1 || req.stream > 1 || req.persist < -1 ||
       req.persist > 3)
     return fail(CH_EINVAL, "tuning fields must be >= 0 (split, stream: -1, 0 or 1; persist: -1 .. 3)");
-  if (req.row_seg != -1 && req.row_seg != 0 && req.row_seg != 16 && req.row_seg != 32)
-    return fail(CH_EINVAL, "row_seg must be -1, 0, 16 or 32");
+  if (req.row_seg != -1 && req.row_seg != 0 && req.row_seg != 1 && req.row_seg != 16 && req.row_seg != 32)
+    return fail(CH_EINVAL, "row_seg must be -1, 0, 1, 16 or 32");
+  if (req.col_seg != -1 && req.col_seg != 0 && req.col_seg != 16 && req.col_seg != 32)
+    return fail(CH_EINVAL, "col_seg must be -1, 0, 16 or 32");
   CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
   const std::vector<MemberParams> saved = h->hp;
   const ch_tuning old = h->tuning;
@@ -911,7 +974,9 @@ int ch_get_tuning(ch_handle h, ch_tuning* t) {
   t->threads = h->shape.rows_threads;
   t->stream = h->shape.stream;
   t->persist = h->shape.cols_persist | (h->shape.seg_persist << 1);
-  t->row_seg = h->shape.split ? 0 : (h->shape.row_seg ? h->shape.row_seg : -1);
+  // kernel classes of member 0
+  t->row_seg = h->shape.split ? 0 : h->hp[0].row_t ? 1 : (h->hp[0].seg_g ? h->hp[0].nx / h->hp[0].seg_g : -1);
+  t->col_seg = h->hp[0].col_s ? h->hp[0].col_s : -1;
   return CH_OK;
 }
 

@@ -24,6 +24,8 @@ struct ch_ensemble {
   std::vector<uint8_t> present;   // slot k holds a member (empty: every slot does)
   std::vector<MemberState> hs0;  // initial state (for reset)
   std::vector<chk::SegTable> hseg;  // scan tables of the segment row sweep, per member
+  std::vector<chk::SegTable> hsegy; // scan tables of the segment column kernel, per member
+  std::vector<Tile> cst;            // CTAs of the segment column kernel
   std::vector<Tile> rt, st, ct;   // stencil/fused bands, row-sweep bands, column panels
   chk::LaunchShape shape{};
   ch_tuning tuning{};             // as requested (0 / -1 = default)
@@ -38,6 +40,9 @@ struct ch_ensemble {
   MemberParams* dmp = nullptr;
   MemberState* dms = nullptr;
   chk::SegTable* dseg = nullptr;
+  chk::SegTable* dsegy = nullptr;
+  Tile* dcst = nullptr;
+  size_t cap_cst = 0;
   Tile* drt = nullptr;
   Tile* dst = nullptr;
   Tile* dct = nullptr;
@@ -66,6 +71,8 @@ struct ch_ensemble {
     v.series = dseries;
     v.obs_now = dobs;
     v.seg = dseg;
+    v.segy = dsegy;
+    v.colseg_tiles = dcst;
     v.m = m;
     return v;
   }

@@ -26,6 +26,8 @@ struct MemberParams {
   int nbands;            // row tiles of this member = partial slots per sample
   int rows_p, cols_p;    // threads per line in the row / column sweep
   int seg_g;             // segment form of the row sweep: lanes per row (nx / S), 0 = chunked
+  int col_s;             // segment form of the column kernel: rows per warp S, 0 = panels / streaming
+  int row_t;             // transposed-block form of the row kernel: nw = nx / 32 warps, 0 = other forms
   int every;             // sampling period in steps
   int64_t partial_base;  // first partial slot
   int64_t series_cap;    // samples kept per member (ring)
@@ -91,6 +93,8 @@ struct DevView {
   double* series;
   double* obs_now;       // [m][3] F, dF/dt, beta of ch_observables
   const SegTable* seg;   // [m] scan tables (segment form of the row sweep)
+  const SegTable* segy;  // [m] scan tables of the y recurrence (segment form of the column kernel)
+  const Tile* colseg_tiles;  // CTAs of the segment-form column kernel
   int m;
 };
 
@@ -108,11 +112,19 @@ struct LaunchShape {
   int cols_persist;      // 1: cols_kernel walks panels with double-buffered copies
   int cols_grid;         // CTAs of the persistent column kernel (SMs x resident CTAs)
   int cols_panel_cap;    // elements of one panel buffer
-  int row_seg;           // fused form: S of the segment row sweep (16 or 32), 0 = chunked sweep
+  // Row tiles are ordered by kernel class: first the transposed-block form (32-row bands),
+  // grouped by nw = nx / 32 (rtT_n[nw] tiles for nw = 1 .. 16), then the segment form
+  // with S = 16 (rt_seg[0] tiles) and S = 32 (rt_seg[1]), then the chunked form.
+  int rtT_n[17];
+  int rt_seg[2];
   int seg_persist;       // 1: the segment row kernel walks its tiles with a double-buffered C band
-  int seg_grid;          // CTAs of the persistent segment row kernel
-  int seg_ccap, seg_mcap;  // elements of one C tile buffer / of the mu tile (max over tiles)
-  size_t seg_smem;       // dynamic shared memory of the segment-form row kernel
+  int seg_grid[2];       // CTAs of the persistent segment row kernel
+  int seg_ccap[2], seg_mcap[2];  // elements of one C tile buffer / of the mu tile (max over the class)
+  size_t seg_smem[2];    // dynamic shared memory of the segment-form row kernel
+  // Column tiles of the segment form: cst_n[0] with S = 16, then cst_n[1] with S = 32.
+  int cst_n[2];
+  int colseg_threads[2];
+  size_t colseg_smem[2];
 };
 
 // Kernel launchers (ch_kernels.cu).  Each returns the launch status.

@@ -563,9 +563,9 @@ __device__ __forceinline__ void finalize_sample(const DevView& v, int member, Me
 // sweep output.
 // -------------------------------------------------------------------------------------
 template <typename T, bool OBS_ONLY>
-__global__ void __launch_bounds__(512) rows_kernel(DevView v) {
+__global__ void __launch_bounds__(512) rows_kernel(DevView v, int tile_base) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const Tile tl = v.row_tiles[blockIdx.x];
+  const Tile tl = v.row_tiles[tile_base + blockIdx.x];
   const MemberParams& P = v.mp[tl.member];
   MemberState* st = v.ms + tl.member;
   bool sample = true;
@@ -832,11 +832,212 @@ __device__ __forceinline__ void seg_tile(const DevView& v, const Tile& tl, const
   }
 }
 
+// -------------------------------------------------------------------------------------
+// Fused row kernel, transposed-block form: a band of up to 32 rows (j0 .. j0+31) of one
+// member with nx = 32 nw (nw <= 16); warp w owns the columns [32 w, 32 w + 32).  With
+// lane = column the stencil walks down the band (C as coalesced 128-byte row pieces
+// straight from HBM, x neighbours by shuffles, y neighbours in registers); the warp's
+// 32 x 32 block of R' is then transposed through shared memory so that lane = row, each
+// lane runs the row recurrences over its 32 columns, and the nw segments of a row are
+// joined through shared memory (local pass, sequential combination of the segment end
+// states, periodic start state, second pass).  W goes back through the transpose and out
+// as coalesced row pieces.  On sample steps the FP64 F and dF/dt densities are summed
+// with backward differences (the periodic sums are the same).
+// -------------------------------------------------------------------------------------
+template <typename T, bool REV>
+__device__ __forceinline__ void rowT_pass(T (&x)[32], T p1, T p2, const SegTable& tab, T* xs, int warp, int lane,
+                                          int nw) {
+  T a = T(0), b = T(0);
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const T t = fma(p1, a, fma(p2, b, x[REV ? 31 - k : k]));
+    b = a;
+    a = t;
+  }
+  xs[2 * (warp * 32 + lane)] = a;
+  xs[2 * (warp * 32 + lane) + 1] = b;
+  __syncthreads();
+  const T A0 = pick<T>(tab.A[0][0], tab.Af[0][0]), A1 = pick<T>(tab.A[0][1], tab.Af[0][1]);
+  const T A2 = pick<T>(tab.A[0][2], tab.Af[0][2]), A3 = pick<T>(tab.A[0][3], tab.Af[0][3]);
+  const int pos = REV ? nw - 1 - warp : warp;
+  T ya = T(0), yb = T(0), pa = T(0), pb = T(0);
+  for (int k = 0; k < nw; ++k) {
+    const int w = REV ? nw - 1 - k : k;
+    const T ea = xs[2 * (w * 32 + lane)], eb = xs[2 * (w * 32 + lane) + 1];
+    const T na = fma(A0, ya, fma(A1, yb, ea));
+    yb = fma(A2, ya, fma(A3, yb, eb));
+    ya = na;
+    if (k + 1 == pos) {
+      pa = ya;
+      pb = yb;
+    }
+  }
+  const T P0 = pick<T>(tab.P[0], tab.Pf[0]), P1 = pick<T>(tab.P[1], tab.Pf[1]);
+  const T P2 = pick<T>(tab.P[2], tab.Pf[2]), P3 = pick<T>(tab.P[3], tab.Pf[3]);
+  const T xa = fma(P0, ya, P1 * yb), xb = fma(P2, ya, P3 * yb);
+  const T B0 = pick<T>(tab.B[pos][0], tab.Bf[pos][0]), B1 = pick<T>(tab.B[pos][1], tab.Bf[pos][1]);
+  const T B2 = pick<T>(tab.B[pos][2], tab.Bf[pos][2]), B3 = pick<T>(tab.B[pos][3], tab.Bf[pos][3]);
+  a = fma(B0, xa, fma(B1, xb, pa));
+  b = fma(B2, xa, fma(B3, xb, pb));
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const int u = REV ? 31 - k : k;
+    const T t = fma(p1, a, fma(p2, b, x[u]));
+    x[u] = t;
+    b = a;
+    a = t;
+  }
+}
+
+// Sample step of rowsT_kernel: FP64 partial sums of the F and dF/dt densities of the band
+// rows at column i, mu recomputed in FP64 from the stored field, backward differences
+// (the periodic sums equal those of forward differences); a second walk down the band.
+template <typename T>
+__device__ __noinline__ void rowT_partials(const DevView& v, const Tile& tl, const MemberParams& P, const T* Cm,
+                                           double* red, int i, int iw, int ie, int lane) {
+  const unsigned full = 0xffffffffu;
+  const int nx = P.nx, ny = P.ny, nr = tl.count;
+  const double a = P.a, bx = P.bx, by = P.by;
+  const int iww = iw == 0 ? nx - 1 : iw - 1;
+  int jn = tl.start - 2;
+  if (jn < 0) jn += ny;
+  const T* r0 = Cm + (int64_t)jn * nx;
+  if (++jn == ny) jn = 0;
+  const T* r1 = Cm + (int64_t)jn * nx;
+  double sw = 0.0, sdx = 0.0, sdy = 0.0, smx = 0.0, smy = 0.0, mu_prev = 0.0;
+  for (int q = 0; q <= nr; ++q) {  // mu rows j0-1 .. j0+nr-1
+    if (++jn == ny) jn = 0;
+    const T* r2 = Cm + (int64_t)jn * nx;
+    const double cd = (double)r1[i], cs = (double)r0[i], cn = (double)r2[i];
+    double w = __shfl_up_sync(full, cd, 1), e = __shfl_down_sync(full, cd, 1);
+    if (lane == 0) w = (double)r1[iw];
+    if (lane == 31) e = (double)r1[ie];
+    const double mu = cd * (cd * cd - a) - bx * (e + w) - by * (cn + cs);
+    double muw = __shfl_up_sync(full, mu, 1);
+    if (lane == 0) muw = w * (w * w - a) - bx * (cd + (double)r1[iww]) - by * ((double)r2[iw] + (double)r0[iw]);
+    if (q >= 1) {
+      const double gx = cd - w, gy = cd - cs, wv = cd * cd - 1.0, mx = mu - muw, my = mu - mu_prev;
+      sw += wv * wv;
+      sdx += gx * gx;
+      sdy += gy * gy;
+      smx += mx * mx;
+      smy += my * my;
+    }
+    mu_prev = mu;
+    r0 = r1;
+    r1 = r2;
+  }
+  const double hxi2 = 1.0 / (P.hx * P.hx), hyi2 = 1.0 / (P.hy * P.hy);
+  double sF = 0.25 * sw + 0.5 * P.gamma * (hxi2 * sdx + hyi2 * sdy);
+  double sD = hxi2 * smx + hyi2 * smy;
+  block_sum2(sF, sD, red);
+  if (threadIdx.x == 0) v.partials[P.partial_base + tl.index] = make_double2(sF, sD);
+}
+
+// Shared memory (elements of T): nw transpose tiles of 32 x 33, the mu edge columns
+// (nw x 2 x 34), the segment end states (2 directions x nw x 64), then the FP64
+// reduction buffer.
+template <typename T>
+__global__ void __launch_bounds__(512) rowsT_kernel(DevView v, int tile_base) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned full = 0xffffffffu;
+  const Tile tl = v.row_tiles[tile_base + blockIdx.x];
+  const MemberParams& P = v.mp[tl.member];
+  MemberState* st = v.ms + tl.member;
+  if (st->remaining <= 0) {
+    if (tl.index == 0 && threadIdx.x == 0) st->active = 0;
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nx = P.nx, ny = P.ny, j0 = tl.start, nr = tl.count;
+  T* tile = reinterpret_cast<T*>(smem) + warp * 32 * 33;
+  T* edge = reinterpret_cast<T*>(smem) + nw * 32 * 33;  // [w][side][34]: C halo columns, then mu edges
+  T* xch = edge + nw * 68;                              // [dir][w][32][2]
+  double* red = red_buffer(smem, ((size_t)nw * 32 * 33 + nw * 68 + 2 * nw * 64) * sizeof(T));
+  int smp = 0;
+  if (lane == 0) smp = (st->step % P.every) == 0;
+  smp = __shfl_sync(full, smp, 0);
+  if (threadIdx.x == 0 && tl.index == 0) st->active = 1;
+
+  const int i = 32 * warp + lane;
+  const int iw = i == 0 ? nx - 1 : i - 1, ie = i + 1 == nx ? 0 : i + 1;
+  const T* __restrict__ Cm = static_cast<const T*>(v.C) + P.offset;
+  // the 36 rows j0-2 .. j0+33 (periodic in j) at column i, all loads issued before use;
+  // the halo columns of this warp's block (left of lane 0, right of lane 31) for rows
+  // j0-1 .. j0+32 go through shared memory, 68 loads spread over the lanes
+  int jb = j0 - 2;
+  if (jb < 0) jb += ny;
+  T m[36];
+  {
+    int jn = jb;
+#pragma unroll
+    for (int q = 0; q < 36; ++q) {
+      m[q] = Cm[(int64_t)jn * nx + i];
+      if (++jn == ny) jn = 0;
+    }
+    T* halo = edge + warp * 68;
+    const int hl = 32 * warp == 0 ? nx - 1 : 32 * warp - 1, hr = 32 * warp + 32 == nx ? 0 : 32 * warp + 32;
+    for (int k = lane; k < 68; k += 32) {
+      const int q = k < 34 ? k : k - 34;
+      const int j = (jb + 1 + q) % ny;
+      halo[k] = Cm[(int64_t)j * nx + (k < 34 ? hl : hr)];
+    }
+    __syncwarp();
+    const T a = pick<T>(P.a, P.fa), bx = pick<T>(P.bx, P.fbx), by = pick<T>(P.by, P.fby);
+    // mu of row j0-1+q into m[q] (in place: row q of C is not needed after it)
+#pragma unroll
+    for (int q = 0; q < 34; ++q) {
+      const T c1 = m[q + 1];
+      T w = __shfl_up_sync(full, c1, 1), e = __shfl_down_sync(full, c1, 1);
+      if (lane == 0) w = halo[q];
+      if (lane == 31) e = halo[34 + q];
+      m[q] = fma(-by, m[q + 2] + m[q], fma(-bx, e + w, c1 * fma(c1, c1, -a)));
+    }
+    __syncwarp();
+    if (lane == 0 || lane == 31) {
+#pragma unroll
+      for (int q = 0; q < 34; ++q) halo[(lane == 31) * 34 + q] = m[q];
+    }
+  }
+  __syncthreads();
+  // R' in place: m[q] <- R' of band row q (mu rows q, q+1, q+2)
+  {
+    const T rho = pick<T>(P.rho, P.frho), w0 = pick<T>(P.w0, P.fw0);
+    const T* eleft = edge + (((warp + nw - 1) % nw) * 2 + 1) * 34;  // lane 31 of the warp on the left
+    const T* eright = edge + (((warp + 1) % nw) * 2) * 34;          // lane 0 of the warp on the right
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      T w = __shfl_up_sync(full, m[q + 1], 1), e = __shfl_down_sync(full, m[q + 1], 1);
+      if (lane == 0) w = eleft[q + 1];
+      if (lane == 31) e = eright[q + 1];
+      m[q] = fma(w0, m[q + 1], fma(rho, m[q + 2] + m[q], e + w));
+    }
+  }
+  // transpose: lane r takes band row r's 32 columns of this warp
+#pragma unroll
+  for (int q = 0; q < 32; ++q) tile[q * 33 + lane] = m[q];
+  __syncwarp();
+  T x[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) x[c] = tile[lane * 33 + c];
+  const SegTable& tab = v.seg[tl.member];
+  const T p1 = pick<T>(P.p1x, P.fp1x), p2 = pick<T>(P.p2x, P.fp2x);
+  rowT_pass<T, false>(x, p1, p2, tab, xch, warp, lane, nw);
+  rowT_pass<T, true>(x, p1, p2, tab, xch + nw * 64, warp, lane, nw);
+  // transpose back and store W as row pieces
+#pragma unroll
+  for (int c = 0; c < 32; ++c) tile[lane * 33 + c] = x[c];
+  __syncwarp();
+  T* __restrict__ Wm = static_cast<T*>(v.W) + P.offset + i;
+  for (int q = 0; q < nr; ++q) Wm[(int64_t)(j0 + q) * nx] = tile[q * 33 + lane];
+  if (smp) rowT_partials<T>(v, tl, P, Cm, red, i, iw, ie, lane);
+}
+
 // Next tile at or after t (stride gridDim.x) whose member still steps; tiles of finished
 // members are skipped, their band-0 CTA clearing the member's active flag.
-__device__ __forceinline__ int next_active_tile(const DevView& v, int t, int ntiles) {
+__device__ __forceinline__ int next_active_tile(const DevView& v, int base, int t, int ntiles) {
   while (t < ntiles) {
-    const Tile tl = v.row_tiles[t];
+    const Tile tl = v.row_tiles[base + t];
     MemberState* st = v.ms + tl.member;
     if (st->remaining > 0) return t;
     if (tl.index == 0 && threadIdx.x == 0) st->active = 0;
@@ -869,7 +1070,7 @@ __device__ __forceinline__ void seg_tile_setup(const DevView& v, const Tile& tl,
 // (28 T), then the FP64 reduction buffer.  PERSIST: a CTA walks the tiles blockIdx.x,
 // + gridDim.x, ... and copies the next tile's C band while it computes the current one.
 template <typename T, int S, bool PERSIST>
-__global__ void __launch_bounds__(256) rows_seg_kernel(DevView v, int ntiles, int ccap, int mcap) {
+__global__ void __launch_bounds__(256) rows_seg_kernel(DevView v, int base, int ntiles, int ccap, int mcap) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* Cbuf = reinterpret_cast<T*>(smem);
   T* Ms = Cbuf + (size_t)(PERSIST ? 2 : 1) * ccap;
@@ -877,24 +1078,24 @@ __global__ void __launch_bounds__(256) rows_seg_kernel(DevView v, int ntiles, in
   int* s_sample = reinterpret_cast<int*>(Ks + 24);
   double* red = red_buffer(smem, ((size_t)(PERSIST ? 2 : 1) * ccap + mcap + 28) * sizeof(T));
   auto issue = [&](int t, T* dst) {
-    const Tile tl = v.row_tiles[t];
+    const Tile tl = v.row_tiles[base + t];
     const MemberParams& P = v.mp[tl.member];
     load_rows_async<T>(dst, P.nx, static_cast<const T*>(v.C) + P.offset, P.nx, P.ny, tl.start - 2, tl.count + 4);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  int t = next_active_tile(v, blockIdx.x, PERSIST ? ntiles : blockIdx.x + 1);
+  int t = next_active_tile(v, base, blockIdx.x, PERSIST ? ntiles : blockIdx.x + 1);
   if (t >= ntiles || (!PERSIST && t != (int)blockIdx.x)) return;
   issue(t, Cbuf);
   int cur = 0;
   while (t < ntiles) {
-    const int nt = PERSIST ? next_active_tile(v, t + gridDim.x, ntiles) : ntiles;
+    const int nt = PERSIST ? next_active_tile(v, base, t + gridDim.x, ntiles) : ntiles;
     if (PERSIST && nt < ntiles) {
       issue(nt, Cbuf + (size_t)(cur ^ 1) * ccap);
       asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     } else {
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
-    const Tile tl = v.row_tiles[t];
+    const Tile tl = v.row_tiles[base + t];
     const MemberParams& P = v.mp[tl.member];
     seg_tile_setup<T>(v, tl, P, Ks, s_sample);
     __syncthreads();
@@ -1097,6 +1298,103 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
 }
 
 // -------------------------------------------------------------------------------------
+// Column kernel, segment form (fused form).  A CTA takes up to 32 * ppc columns of one
+// member (ppc panels of 32); each panel's columns are split into wp = ny / S segments of S
+// rows, one warp per segment and one lane per column, so every access to W and C is a
+// coalesced row piece of the panel and the S values of a lane stay in registers.  Each
+// recurrence runs as a pass from a zero state over the segment, an exchange of the
+// segments' end states through shared memory, the sequential combination over the wp
+// segments (Y_w = M^S Y_{w-1} + e_w), the periodic start state x0 = (I - M^ny)^-1 Y_{wp-1},
+// and a second pass from M^(S w) x0 + Y_{w-1}.  Then C += kappa Z row piece by row piece.
+// -------------------------------------------------------------------------------------
+template <typename T, int S, bool REV>
+__device__ __forceinline__ void colseg_pass(T (&y)[S], T p1, T p2, const SegTable& tab, T* xs, int warp, int lane,
+                                            int wseg, int wp, int pbase) {
+  T a = T(0), b = T(0);
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const T t = fma(p1, a, fma(p2, b, y[REV ? S - 1 - k : k]));
+    b = a;
+    a = t;
+  }
+  xs[2 * (warp * 32 + lane)] = a;
+  xs[2 * (warp * 32 + lane) + 1] = b;
+  __syncthreads();
+  // sequential combination over the panel's segments in the recurrence's order
+  const T A0 = pick<T>(tab.A[0][0], tab.Af[0][0]), A1 = pick<T>(tab.A[0][1], tab.Af[0][1]);
+  const T A2 = pick<T>(tab.A[0][2], tab.Af[0][2]), A3 = pick<T>(tab.A[0][3], tab.Af[0][3]);
+  const int pos = REV ? wp - 1 - wseg : wseg;
+  T ya = T(0), yb = T(0), pa = T(0), pb = T(0);
+  for (int k = 0; k < wp; ++k) {
+    const int w = pbase + (REV ? wp - 1 - k : k);
+    const T ea = xs[2 * (w * 32 + lane)], eb = xs[2 * (w * 32 + lane) + 1];
+    const T na = fma(A0, ya, fma(A1, yb, ea));
+    yb = fma(A2, ya, fma(A3, yb, eb));
+    ya = na;
+    if (k + 1 == pos) {
+      pa = ya;
+      pb = yb;
+    }
+  }
+  const T P0 = pick<T>(tab.P[0], tab.Pf[0]), P1 = pick<T>(tab.P[1], tab.Pf[1]);
+  const T P2 = pick<T>(tab.P[2], tab.Pf[2]), P3 = pick<T>(tab.P[3], tab.Pf[3]);
+  const T xa = fma(P0, ya, P1 * yb), xb = fma(P2, ya, P3 * yb);
+  const T B0 = pick<T>(tab.B[pos][0], tab.Bf[pos][0]), B1 = pick<T>(tab.B[pos][1], tab.Bf[pos][1]);
+  const T B2 = pick<T>(tab.B[pos][2], tab.Bf[pos][2]), B3 = pick<T>(tab.B[pos][3], tab.Bf[pos][3]);
+  a = fma(B0, xa, fma(B1, xb, pa));
+  b = fma(B2, xa, fma(B3, xb, pb));
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const int u = REV ? S - 1 - k : k;
+    const T t = fma(p1, a, fma(p2, b, y[u]));
+    y[u] = t;
+    b = a;
+    a = t;
+  }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) colseg_kernel(DevView v, int tile_base) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tile tl = v.colseg_tiles[tile_base + blockIdx.x];
+  MemberState* st = v.ms + tl.member;
+  if (!st->active) return;
+  const MemberParams& P = v.mp[tl.member];
+  const SegTable& tab = v.segy[tl.member];
+  const int nx = P.nx, ny = P.ny;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int wp = ny / S;
+  const int sg = warp / wp, wseg = warp - sg * wp, pbase = sg * wp;
+  const int cl = 32 * sg + lane;                      // column within the tile
+  const bool cv = sg < nwarps / wp && cl < tl.count;  // this lane owns a column
+  const int col = tl.start + (cv ? cl : 0);
+  T* xf = reinterpret_cast<T*>(smem);
+  T* xb = xf + 2 * 32 * nwarps;
+  const T* __restrict__ Wg = static_cast<const T*>(v.W) + P.offset + (int64_t)wseg * S * nx + col;
+  T y[S];
+#pragma unroll
+  for (int u = 0; u < S; ++u) y[u] = cv ? Wg[(int64_t)u * nx] : T(0);
+  const T p1 = pick<T>(P.p1y, P.fp1y), p2 = pick<T>(P.p2y, P.fp2y);
+  colseg_pass<T, S, false>(y, p1, p2, tab, xf, warp, lane, wseg, wp, pbase);
+  colseg_pass<T, S, true>(y, p1, p2, tab, xb, warp, lane, wseg, wp, pbase);
+  if (cv) {
+    const T kap = pick<T>(P.kappa, P.fkappa);
+    T* __restrict__ Cg = static_cast<T*>(v.C) + P.offset + (int64_t)wseg * S * nx + col;
+#pragma unroll
+    for (int u0 = 0; u0 < S; u0 += 8) {  // 8 loads in flight, few extra registers
+      T c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) c[u] = Cg[(int64_t)(u0 + u) * nx];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) Cg[(int64_t)(u0 + u) * nx] = fma(kap, y[u0 + u], c[u]);
+    }
+  }
+  // The first tile of the member finalises its sample of this step and advances its step
+  // counter (no other CTA of this launch touches the member's state).
+  if (tl.index == 0 && threadIdx.x == 0) finalize_sample(v, tl.member, st, P);
+}
+
+// -------------------------------------------------------------------------------------
 // Streaming sweeps (split form).  Lines are not held on chip: each warp owns 32 lines (one
 // per lane) and streams them, so the number of recurrences in flight per SM is bounded by
 // registers rather than by shared memory.  The intermediate y of the two-pass solve lives
@@ -1294,21 +1592,52 @@ __global__ void obs_finalize_kernel(DevView v) {
   v.obs_now[3 * m + 2] = -(t / F) * dFdt;
 }
 
+// Dynamic shared memory of rowsT_kernel with nw warps.
+template <typename T>
+size_t rowT_smem_bytes(int nw) {
+  size_t b = ((size_t)nw * 32 * 33 + (size_t)nw * 68 + (size_t)2 * nw * 64) * sizeof(T);
+  b = (b + 15) & ~(size_t)15;
+  return b + (size_t)2 * nw * sizeof(double);
+}
+
 template <typename T>
 void seg_launch(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
   const int threads = min(sh.rows_threads, 256);
-  const int grid = sh.seg_persist ? min(sh.n_row_tiles, sh.seg_grid) : sh.n_row_tiles;
-  if (sh.row_seg == 16) {
-    if (sh.seg_persist)
-      rows_seg_kernel<T, 16, true><<<grid, threads, sh.seg_smem, st>>>(v, sh.n_row_tiles, sh.seg_ccap, sh.seg_mcap);
-    else
-      rows_seg_kernel<T, 16, false><<<grid, threads, sh.seg_smem, st>>>(v, sh.n_row_tiles, sh.seg_ccap, sh.seg_mcap);
-  } else {
-    if (sh.seg_persist)
-      rows_seg_kernel<T, 32, true><<<grid, threads, sh.seg_smem, st>>>(v, sh.n_row_tiles, sh.seg_ccap, sh.seg_mcap);
-    else
-      rows_seg_kernel<T, 32, false><<<grid, threads, sh.seg_smem, st>>>(v, sh.n_row_tiles, sh.seg_ccap, sh.seg_mcap);
+  int base = 0;
+  for (int nw = 1; nw <= 16; ++nw) {
+    if (sh.rtT_n[nw] > 0) rowsT_kernel<T><<<sh.rtT_n[nw], 32 * nw, rowT_smem_bytes<T>(nw), st>>>(v, base);
+    base += sh.rtT_n[nw];
   }
+  for (int c = 0; c < 2; ++c) {
+    const int n = sh.rt_seg[c];
+    if (n > 0) {
+      const int grid = sh.seg_persist ? min(n, sh.seg_grid[c]) : n;
+      const size_t sm = sh.seg_smem[c];
+      const int cc = sh.seg_ccap[c], mc = sh.seg_mcap[c];
+      if (c == 0) {
+        if (sh.seg_persist)
+          rows_seg_kernel<T, 16, true><<<grid, threads, sm, st>>>(v, base, n, cc, mc);
+        else
+          rows_seg_kernel<T, 16, false><<<grid, threads, sm, st>>>(v, base, n, cc, mc);
+      } else {
+        if (sh.seg_persist)
+          rows_seg_kernel<T, 32, true><<<grid, threads, sm, st>>>(v, base, n, cc, mc);
+        else
+          rows_seg_kernel<T, 32, false><<<grid, threads, sm, st>>>(v, base, n, cc, mc);
+      }
+    }
+    base += n;
+  }
+  if (sh.n_row_tiles > base)
+    rows_kernel<T, false><<<sh.n_row_tiles - base, sh.rows_threads, sh.rows_smem, st>>>(v, base);
+}
+
+template <typename T>
+void colseg_launch(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
+  if (sh.cst_n[0] > 0)
+    colseg_kernel<T, 16><<<sh.cst_n[0], sh.colseg_threads[0], sh.colseg_smem[0], st>>>(v, 0);
+  if (sh.cst_n[1] > 0)
+    colseg_kernel<T, 32><<<sh.cst_n[1], sh.colseg_threads[1], sh.colseg_smem[1], st>>>(v, sh.cst_n[0]);
 }
 
 template <typename T>
@@ -1318,10 +1647,8 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
     case 0:
       if (sh.split)
         stencil_kernel<T><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
-      else if (sh.row_seg)
-        seg_launch<T>(v, sh, st);
       else
-        rows_kernel<T, false><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
+        seg_launch<T>(v, sh, st);
       break;
     case 1:
       if (!sh.split) return cudaSuccess;
@@ -1332,7 +1659,10 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
         rowsweep_kernel<T><<<sh.n_sweep_tiles, sh.sweep_threads, sh.sweep_smem, st>>>(v);
       break;
     default:
-      if (sh.stream)
+      colseg_launch<T>(v, sh, st);
+      if (sh.n_col_tiles == 0)
+        break;
+      else if (sh.stream)
         colstream_kernel<T><<<(sh.n_col_tiles + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps, 0, st>>>(
             v, sh.n_col_tiles);
       else if (sh.cols_persist)
@@ -1356,7 +1686,7 @@ cudaError_t step_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) 
 
 template <typename T>
 cudaError_t observe_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
-  if (sh.n_row_tiles > 0) rows_kernel<T, true><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
+  if (sh.n_row_tiles > 0) rows_kernel<T, true><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   obs_finalize_kernel<<<(v.m + 127) / 128, 128, 0, st>>>(v);
@@ -1372,6 +1702,8 @@ cudaError_t smem_limits_impl() {
   if ((e = cudaFuncSetAttribute(rows_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(stencil_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(rowsT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(rows_seg_kernel<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
       cudaSuccess)

@@ -342,6 +342,7 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
   cudaGetDevice(&h->device);
   h->hp.assign(max_members, MemberParams{});
   h->hseg.assign(max_members, chk::SegTable{});
+  h->hsegy.assign(max_members, chk::SegTable{});
   for (auto& p : h->hp) p.every = 1;
   h->present.assign(max_members, 0);
   h->tuning = chh::default_tuning();
@@ -354,6 +355,7 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
     cudaFree(h->dmp);
     cudaFree(h->dms);
     cudaFree(h->dseg);
+    cudaFree(h->dsegy);
     cudaFree(h->dobs);
     cudaFree(S->dlist);
     if (h->own) cudaStreamDestroy(h->own);
@@ -369,6 +371,7 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
       (e = cudaMalloc((void**)&h->dmp, sizeof(MemberParams) * max_members)) != cudaSuccess ||
       (e = cudaMalloc((void**)&h->dms, sizeof(MemberState) * max_members)) != cudaSuccess ||
       (e = cudaMalloc((void**)&h->dseg, sizeof(chk::SegTable) * max_members)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&h->dsegy, sizeof(chk::SegTable) * max_members)) != cudaSuccess ||
       (e = cudaMalloc((void**)&h->dobs, sizeof(double) * 3 * max_members)) != cudaSuccess ||
       (e = cudaMalloc((void**)&S->dlist, sizeof(int) * max_members)) != cudaSuccess)
     return cleanup(e == cudaErrorMemoryAllocation ? CH_ENOMEM : CH_ECUDA,
@@ -485,6 +488,8 @@ void ch_server_destroy(ch_server s) {
   cudaFree(h->dmp);
   cudaFree(h->dms);
   cudaFree(h->dseg);
+  cudaFree(h->dsegy);
+  cudaFree(h->dcst);
   cudaFree(h->drt);
   cudaFree(h->dst);
   cudaFree(h->dct);

@@ -366,14 +366,15 @@ SEG_MEMBERS = [
 SEG_TUNINGS = [dict(split=0, row_seg=0), dict(split=0, row_seg=16, rows_band=3, threads=64),
                dict(split=0, row_seg=32, rows_band=16, threads=256, persist=0),
                dict(split=0, row_seg=16, rows_band=1, threads=512, cols_panel=8, cols_p=2, persist=2),
-               dict(split=0, row_seg=16, rows_band=5, threads=128, persist=3)]
+               dict(split=0, row_seg=16, rows_band=5, threads=128, persist=3),
+               dict(split=0, row_seg=1), dict(split=0, row_seg=1, col_seg=-1, threads=64)]
 
 
 @pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
 @pytest.mark.parametrize("tuning", SEG_TUNINGS, ids=[str(i) for i in range(len(SEG_TUNINGS))])
 def test_segment_row_sweep_matches_oracle(orc, prec, tuning):
     descs, base = [], 0
-    members = SEG_MEMBERS if tuning.get("row_seg") != 32 else SEG_MEMBERS[1:]  # nx = 16 < S
+    members = SEG_MEMBERS if tuning.get("row_seg") in (0, 16) else SEG_MEMBERS[1:]  # nx = 16 < S, not 32 nw
     for k, d in enumerate(members):
         descs.append(dict(d, seed=SEED + 11 * k, counter_base=base))
         base += d["nx"] * d["ny"]
@@ -405,14 +406,76 @@ def test_segment_row_sweep_matches_oracle(orc, prec, tuning):
             np.testing.assert_allclose(ser[:, 2], ref.series[:, 2], rtol=1e-9 if prec == ch.CH_FP64 else 1e-3)
 
 
+# Members whose columns split into a power of two of 16- or 32-row segments: the segment
+# form of the column kernel, incl. one segment per column (ny = S), partial column tiles
+# (nx not a multiple of 32), several panels per CTA and s large.
+COLSEG_MEMBERS = [
+    dict(nx=33, ny=32, L=1.0, gamma=0.002, dt=1e-3, C0=0.3),
+    dict(nx=100, ny=64, L=TWO_PI, gamma=0.01, dt=1e-3, C0=0.4),
+    dict(nx=7, ny=128, L=TWO_PI, gamma=0.005, dt=1e-3, C0=-0.2),
+    dict(nx=64, ny=256, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.0),
+    dict(nx=48, ny=16, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.1),   # S = 32 does not fit
+]
+COLSEG_TUNINGS = [dict(split=0, col_seg=16), dict(split=0, col_seg=16, row_seg=-1, threads=128),
+                  dict(split=1, stream=1, col_seg=16), dict(split=0, col_seg=32)]
+
+
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+@pytest.mark.parametrize("tuning", COLSEG_TUNINGS, ids=[str(i) for i in range(len(COLSEG_TUNINGS))])
+def test_segment_column_kernel_matches_oracle(orc, prec, tuning):
+    members = COLSEG_MEMBERS if tuning["col_seg"] == 16 else COLSEG_MEMBERS[:4]
+    descs, base = [], 0
+    for k, d in enumerate(members):
+        descs.append(dict(d, seed=SEED + 13 * k, counter_base=base))
+        base += d["nx"] * d["ny"]
+    nsteps = 40
+    with ch.Ensemble.batch(descs, prec) as e:
+        e.set_tuning(**tuning)
+        assert e.tuning()["col_seg"] == tuning["col_seg"]
+        e.set_sampling(10, 0.0, capacity=8)
+        e.step(nsteps)
+        for k, d in enumerate(descs):
+            C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
+            ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps, every=10)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            assert err <= (1e-12 if prec == ch.CH_FP64 else 1e-4), (k, err)
+            ser = e.series(k, 8)
+            np.testing.assert_allclose(ser[:, 1], ref.series[:, 1], rtol=1e-11 if prec == ch.CH_FP64 else 1e-5)
+            assert e.step_index(k) == nsteps
+
+
+def test_segment_column_selection_and_errors():
+    d = dict(L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.0, seed=1)
+    with ch.Ensemble.batch([dict(d, nx=64, ny=64, counter_base=0), dict(d, nx=32, ny=1024, counter_base=4096)],
+                           ch.CH_FP32) as e:
+        assert e.tuning()["col_seg"] == 32  # 1024 = 32 x 32
+        with pytest.raises(ch.ChError) as err:
+            e.set_tuning(col_seg=16)  # 1024 / 16 = 64 segments: too many
+        assert err.value.code == ch.CH_EINVAL
+        assert e.tuning()["col_seg"] == 32
+    with ch.Ensemble.batch([dict(d, nx=64, ny=1024, counter_base=0)], ch.CH_FP64) as e:
+        assert e.tuning()["col_seg"] == -1  # FP64 default: streaming columns
+        with pytest.raises(ch.ChError):
+            e.set_tuning(col_seg=32)  # 32 segments of doubles: above the FP64 limit of 16
+        e.set_tuning(split=1, col_seg=-1)
+    with ens(64, 100, [0.0], prec=ch.CH_FP32) as e:
+        assert e.tuning()["col_seg"] == -1  # 100 rows: no power of two of segments
+
+
 def test_segment_form_selection_and_errors():
     with ch.Ensemble.batch([dict(nx=64, ny=16, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.0, seed=1, counter_base=0),
                             dict(nx=1024, ny=8, L=TWO_PI, gamma=0.005, dt=1e-3, C0=0.0, seed=1,
                                  counter_base=1024)], ch.CH_FP32) as e:
-        assert e.tuning()["row_seg"] == 32  # 1024 = 32 x 32 does not fit S = 16
+        # classes are per member: member 0 (nx = 64) takes the segment form with S = 16,
+        # member 1 (1024 = 32 x 32) S = 32
+        assert e.tuning()["row_seg"] == 16
         with pytest.raises(ch.ChError) as err:
-            e.set_tuning(row_seg=16)
+            e.set_tuning(row_seg=16)  # forced for every member: 1024 / 16 = 64 lanes is too many
         assert err.value.code == ch.CH_EINVAL
+        with pytest.raises(ch.ChError):
+            e.set_tuning(row_seg=1)  # 1024 = 32 x 32 warps: more than 16
+        assert e.tuning()["row_seg"] == 16
+        e.set_tuning(row_seg=32)
         assert e.tuning()["row_seg"] == 32
         with pytest.raises(ch.ChError):
             e.set_tuning(row_seg=8)
@@ -437,6 +500,33 @@ def test_tuning_round_trip_and_errors():
         assert e.tuning()["rows_band"] == 8  # a rejected request keeps the shape in effect
         ch.ch_set_tuning(e.h)  # defaults
         e.step(3)
+
+
+# ------------------------------------------------------------------------------------------
+# FP32 form at large s: one step from a random field against the oracle.  The factorised
+# solve's condition number is 1 + 16 s per direction, so the FP32 step's error relative to
+# the step grows like the unit round-off times s (both column kernels)
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [256, 512, 1024])
+@pytest.mark.parametrize("col_seg", [-1, 0])
+def test_fp32_single_step_error_grows_with_s(orc, n, col_seg):
+    L, gamma, dt = TWO_PI, 0.005, 1e-3
+    h = L / n
+    s = gamma * dt / h ** 4
+    # the FP32 form holds the field rounded to FP32: the oracle steps the same values
+    C = np.ascontiguousarray(wl.random_field(n, n, 7, amplitude=0.1, mean=0.3)).astype(np.float32).astype(np.float64)
+    ref = C.copy()
+    orc.step(ref, L, gamma, dt)
+    dref = ref - C
+    with ens(n, n, [0.0], gamma, dt, L, prec=ch.CH_FP32) as e:
+        e.set_tuning(split=0, col_seg=col_seg)
+        e.set_field(0, C)
+        e.step(1)
+        got = e.field(0)
+    err = np.max(np.abs((got - C) - dref))
+    # solve: 2 u (1 + 16 s) of the step; storing C + dC in FP32: u max|C|
+    bound = 2 * 2.0 ** -24 * (1 + 16 * s) * np.max(np.abs(dref)) + 2.0 ** -24 * np.max(np.abs(ref))
+    assert err <= bound, (err, bound)
 
 
 # ------------------------------------------------------------------------------------------
@@ -468,5 +558,11 @@ def test_fine_grid_nyquist_mode_decays_as_the_scheme_says(prec):
     assert abs(eps - amp) > 0.5 * abs(eps - want)  # the decay itself, not only the amplitude
     # away from the mode: rounding in R', which the operator passes to the smooth modes with
     # gain up to (1 + 16 s)^2 ~ 3e9 relative to this one; the oracle's own deviation here
-    # is 7e-13 (FP64)
-    assert np.max(np.abs(got - C0 - amp * phi)) <= (2e-12 if prec == ch.CH_FP64 else 1e-6)
+    # is 7e-13 (FP64).  FP32: once rounding breaks the pattern's symmetry, the rounding of
+    # R' (unit round-off of its largest value, |R'| = 8 |mu_1|, mu_1 = 8 gamma eps / h^2)
+    # reaches the smooth modes with gain up to dt / h^2 per step: a worst-case bound.
+    if prec == ch.CH_FP64:
+        bound = 2e-12
+    else:
+        bound = nsteps * (dt / h ** 2) * 2.0 ** -24 * 8 * (8 * gamma * eps / h ** 2)
+    assert np.max(np.abs(got - C0 - amp * phi)) <= bound
