@@ -271,10 +271,12 @@ def run_gpu_leg(ch, torch, p, prec, K, W, rank, world, dist, profile_kernels=Tru
     return out
 
 
-def run_descs_leg(ch, torch, descs, prec, nsteps, every, t1, warm=300):
+def run_descs_leg(ch, torch, descs, prec, nsteps, every, t1, warm=300, tuning=None):
     """Device-timed run of an uneven batch (member descriptors) for nsteps time steps after
     `warm` untimed ones (then reset): grid-point-steps/s, per-member window averages."""
     e = ch.Ensemble.batch(descs, prec)
+    if tuning:
+        e.set_tuning(**tuning)
     stream = torch.cuda.Stream()
     e.set_stream(stream.cuda_stream)
     e.set_sampling(every, t1, capacity=0)
@@ -494,7 +496,10 @@ def main():
                                                (lb["name"], ldescs, 1000, 100, 0.1)]:
             legs = {}
             for prec, pname in ((ch.CH_FP32, "fp32"), (ch.CH_FP64, "fp64")):
-                r = run_descs_leg(ch, torch, descs, prec, nsteps, every, t1)
+                # FP64 uneven batch: the fused segment forms (its few lines per size do not
+                # fill the GPU with the split form's thread-per-line streams)
+                tk = {"split": 0} if (prec == ch.CH_FP64 and descs is udescs) else None
+                r = run_descs_leg(ch, torch, descs, prec, nsteps, every, t1, tuning=tk)
                 r.pop("beta_avg")
                 legs[pname] = r
             legs["fp32_speedup"] = legs["fp32"]["value"] / legs["fp64"]["value"]

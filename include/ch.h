@@ -185,11 +185,13 @@ int ch_launch_phase(ch_handle h, int phase);
  *   cols_p      threads per column (default 1 FP64; FP32 chosen from ny).
  *   threads     threads per stencil / fused / column CTA, multiple of 32, <= 512
  *               (default 512 FP64, 256 FP32).
- *   stream      split form only: 1 = streaming sweeps (a warp streams 32 lines through
- *               small double-buffered tiles or straight from global memory, the pass
+ *   stream      1 = streaming sweeps (a warp streams 32 lines through small
+ *               double-buffered tiles or straight from global memory, the pass
  *               intermediate kept in the scratch field), so recurrences in flight are not
- *               limited by shared memory; 0 = whole lines resident in shared memory
- *               (sweep_band, cols_panel, cols_p apply).  Default: 1 for CH_FP64.
+ *               limited by shared memory: rows and columns in the split form, the columns
+ *               of members outside the segment column form in the fused form; 0 = whole
+ *               lines resident in shared memory (sweep_band, cols_panel, cols_p apply).
+ *               Default: 1 for CH_FP64, 0 for CH_FP32.
  *   persist     bit 0: the column kernel runs one CTA per resident slot and walks its
  *               panels with double-buffered copies (the next panel loads while the current
  *               one is swept); bit 1: the same for the segment-form row kernel (the next
@@ -215,9 +217,9 @@ int ch_launch_phase(ch_handle h, int phase);
  *               and HBM, and each recurrence is a local pass, a combination of the segment
  *               end states through shared memory and a second pass (no pre-roll, no
  *               panels in shared memory).  Needs ny/S to be a power of two <= 32 (<= 16 for
- *               CH_FP64) for every member.  0 = automatic (CH_FP32: 32 if every member
- *               fits, else 16 if every member fits, else panels; CH_FP64: panels or
- *               streaming); -1 = panels or streaming.
+ *               CH_FP64) for every member.  0 = automatic, per member: S = 32 if the
+ *               member fits, else 16 if it fits, else panels or streaming (CH_FP64 split
+ *               form: streaming for every member); -1 = panels or streaming.
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
  * size, lines too long for shared memory, a row_seg that some member's nx does not fit).

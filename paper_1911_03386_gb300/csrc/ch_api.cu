@@ -316,7 +316,9 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   const int want_bc = t.cols_panel > 0 ? t.cols_panel : 32;
   if (t.sweep_band > 512 || want_bc * std::max(1, t.cols_p) > threads || want_br * std::max(1, t.rows_p) > threads)
     return fail(CH_EINVAL, "band/panel times threads per line exceeds the CTA size");
-  const int stream = split ? (t.stream >= 0 ? (t.stream ? 1 : 0) : (f64 ? 1 : 0)) : 0;
+  // streaming sweeps: split form (rows and columns), or in the fused form for the columns
+  // of members outside the segment column form; default on for CH_FP64
+  const int stream = t.stream >= 0 ? (t.stream ? 1 : 0) : (f64 ? 1 : 0);
   const bool persist = t.persist > 0 && (t.persist & 1);
   const bool seg_persist = t.persist > 0 && (t.persist & 2) != 0;
   const int max_wp = f64 ? 16 : 32;
@@ -339,7 +341,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     return row_fits(p, 16) ? 16 : row_fits(p, 32) ? 32 : 0;
   };
   auto col_class = [&](const MemberParams& p) {
-    if (t.col_seg < 0 || (t.col_seg == 0 && f64)) return 0;
+    if (t.col_seg < 0 || (t.col_seg == 0 && f64 && split)) return 0;
     if (t.col_seg > 0) return t.col_seg;
     return col_fits(p, 32) ? 32 : col_fits(p, 16) ? 16 : 0;
   };

@@ -1634,8 +1634,7 @@ void seg_launch(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
 
 template <typename T>
 void colseg_launch(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
-  if (sh.cst_n[0] > 0)
-    colseg_kernel<T, 16><<<sh.cst_n[0], sh.colseg_threads[0], sh.colseg_smem[0], st>>>(v, 0);
+  if (sh.cst_n[0] > 0) colseg_kernel<T, 16><<<sh.cst_n[0], sh.colseg_threads[0], sh.colseg_smem[0], st>>>(v, 0);
   if (sh.cst_n[1] > 0)
     colseg_kernel<T, 32><<<sh.cst_n[1], sh.colseg_threads[1], sh.colseg_smem[1], st>>>(v, sh.cst_n[0]);
 }

@@ -345,7 +345,12 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
   h->hsegy.assign(max_members, chk::SegTable{});
   for (auto& p : h->hp) p.every = 1;
   h->present.assign(max_members, 0);
+  // Fused form for both precisions: segment-form rows and columns where a run's size
+  // allows (per run, so a result does not depend on the mix), streaming columns (FP64) or
+  // panels (FP32) for the others.  The split form's thread-per-line streams need many
+  // lines to fill the GPU, which a handful of served runs does not give.
   h->tuning = chh::default_tuning();
+  h->tuning.split = 0;
   S->slot_req.assign(max_members, 0);
   S->arena.init(elems);
   cudaError_t e;
