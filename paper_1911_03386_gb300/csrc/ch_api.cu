@@ -42,6 +42,12 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory per CTA on sm_103a
+// FP32 members with max(s_x, s_y) above this keep their field as the pair hi + lo
+// (compensated update): the delta-form factor damps the high diagonal modes by only
+// ~1/(4s) per step, so the rounding of an FP32 field would accumulate there; at s = 13.8
+// (256^2) the plain FP32 field reproduces the FP64 <beta> within one standard error, at
+// s = 882 (1024^2) it does not.
+constexpr double kCompS = 16.0;
 constexpr int kGraphSteps = 16;
 
 // ---------------------------------------------------------------------------------------
@@ -259,6 +265,8 @@ int fill_params(const ch_member_desc& d, int precision, MemberParams* p) {
   p->fp1y = (float)p->p1y;
   p->fp2y = (float)p->p2y;
   p->fkappa = (float)p->kappa;
+  p->comp = precision == CH_FP32 && std::max(sx, sy) > kCompS ? 1 : 0;
+  p->lo_offset = -1;
   p->every = 1;
   p->t1 = 0.0;
   return CH_OK;
@@ -578,6 +586,13 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
     h->max_points = std::max(h->max_points, np);
   }
   h->total_points = off;
+  // lo blocks of compensated members follow the fields in C
+  for (int k = 0; k < m; ++k)
+    if (h->hp[k].comp) {
+      h->hp[k].lo_offset = off;
+      off += ((int64_t)d[k].nx * d[k].ny + 3) & ~(int64_t)3;
+    }
+  h->c_points = off;
   int rc = build_tiles(h, default_tuning());
   if (rc) {
     delete h;
@@ -593,7 +608,8 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
   }
   h->stream = h->own;
   auto alloc = [&](void** p, size_t bytes) -> cudaError_t { return cudaMalloc(p, bytes == 0 ? 16 : bytes); };
-  if ((e = alloc(&h->C, h->elt * off)) != cudaSuccess || (e = alloc(&h->W, h->elt * off)) != cudaSuccess ||
+  if ((e = alloc(&h->C, h->elt * h->c_points)) != cudaSuccess ||
+      (e = alloc(&h->W, h->elt * h->total_points)) != cudaSuccess ||
       (e = alloc((void**)&h->dmp, sizeof(MemberParams) * m)) != cudaSuccess ||
       (e = alloc((void**)&h->dms, sizeof(MemberState) * m)) != cudaSuccess ||
       (e = alloc((void**)&h->dseg, sizeof(chk::SegTable) * m)) != cudaSuccess ||
@@ -607,7 +623,7 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
                 std::string("device allocation: ") + cudaGetErrorString(e));
   }
   if ((e = chk::set_kernel_smem_limits(precision)) != cudaSuccess ||
-      (e = cudaMemsetAsync(h->W, 0, h->elt * off, h->stream)) != cudaSuccess) {
+      (e = cudaMemsetAsync(h->W, 0, h->elt * h->total_points, h->stream)) != cudaSuccess) {
     int r = cuda_fail(e, "handle set-up");
     ch_destroy(h);
     return r;
@@ -847,17 +863,60 @@ int ch_series(ch_handle h, int member, double* out, int64_t cap, int64_t* n) {
   return CH_OK;
 }
 
-int ch_get_field(ch_handle h, int member, double* out) {
-  if (int rc = check_member(h, member)) return rc;
-  if (!out) return fail(CH_EINVAL, "out is NULL");
-  const MemberParams& p = h->hp[member];
+}  // extern "C"
+
+namespace chh {
+// Member k's field as FP64 values (FP32: hi, plus lo for compensated members).
+int read_member_field(ch_ensemble* h, int k, double* out) {
+  const MemberParams& p = h->hp[k];
   const int64_t np = (int64_t)p.nx * p.ny;
   if (h->precision == CH_FP64)
     return copy_out(h, out, static_cast<double*>(h->C) + p.offset, sizeof(double) * np, "read field");
-  std::vector<float> tmp(np);
+  std::vector<float> tmp(np), lo;
   if (int rc = copy_out(h, tmp.data(), static_cast<float*>(h->C) + p.offset, sizeof(float) * np, "read field")) return rc;
-  for (int64_t i = 0; i < np; ++i) out[i] = tmp[i];
+  if (p.comp) {
+    lo.resize(np);
+    if (int rc = copy_out(h, lo.data(), static_cast<float*>(h->C) + p.lo_offset, sizeof(float) * np, "read field"))
+      return rc;
+  }
+  for (int64_t i = 0; i < np; ++i) out[i] = p.comp ? (double)tmp[i] + (double)lo[i] : (double)tmp[i];
   return CH_OK;
+}
+
+// Member k's field from FP64 values (FP32: rounded to hi, the remainder to lo for
+// compensated members).  Synchronises.
+int write_member_field(ch_ensemble* h, int k, const double* in) {
+  const MemberParams& p = h->hp[k];
+  const int64_t np = (int64_t)p.nx * p.ny;
+  if (h->precision == CH_FP64) {
+    CH_CUDA(cudaMemcpyAsync(static_cast<double*>(h->C) + p.offset, in, sizeof(double) * np, cudaMemcpyHostToDevice,
+                            h->stream),
+            "write field");
+  } else {
+    std::vector<float> hi(np), lo(p.comp ? np : 0);
+    for (int64_t i = 0; i < np; ++i) {
+      hi[i] = (float)in[i];
+      if (p.comp) lo[i] = (float)(in[i] - (double)hi[i]);
+    }
+    CH_CUDA(cudaMemcpyAsync(static_cast<float*>(h->C) + p.offset, hi.data(), sizeof(float) * np,
+                            cudaMemcpyHostToDevice, h->stream),
+            "write field");
+    if (p.comp)
+      CH_CUDA(cudaMemcpyAsync(static_cast<float*>(h->C) + p.lo_offset, lo.data(), sizeof(float) * np,
+                              cudaMemcpyHostToDevice, h->stream),
+              "write field");
+  }
+  CH_CUDA(cudaStreamSynchronize(h->stream), "write field");
+  return CH_OK;
+}
+}  // namespace chh
+
+extern "C" {
+
+int ch_get_field(ch_handle h, int member, double* out) {
+  if (int rc = check_member(h, member)) return rc;
+  if (!out) return fail(CH_EINVAL, "out is NULL");
+  return read_member_field(h, member, out);
 }
 
 int ch_set_field(ch_handle h, int member, const double* in) {
@@ -867,27 +926,13 @@ int ch_set_field(ch_handle h, int member, const double* in) {
   const int64_t np = (int64_t)p.nx * p.ny;
   for (int64_t i = 0; i < np; ++i)
     if (!std::isfinite(in[i])) return fail(CH_EINVAL, "field value is not finite");
-  if (h->precision == CH_FP64) {
-    CH_CUDA(cudaMemcpyAsync(static_cast<double*>(h->C) + p.offset, in, sizeof(double) * np, cudaMemcpyHostToDevice,
-                            h->stream),
-            "write field");
-  } else {
-    std::vector<float> tmp(np);
-    for (int64_t i = 0; i < np; ++i) tmp[i] = (float)in[i];
-    CH_CUDA(cudaMemcpyAsync(static_cast<float*>(h->C) + p.offset, tmp.data(), sizeof(float) * np, cudaMemcpyHostToDevice,
-                            h->stream),
-            "write field");
-    CH_CUDA(cudaStreamSynchronize(h->stream), "write field");
-  }
-  CH_CUDA(cudaStreamSynchronize(h->stream), "write field");
-  return CH_OK;
+  return write_member_field(h, member, in);
 }
 
 int ch_set_fields(ch_handle h, const double* in) {
   if (int rc = check_handle(h)) return rc;
   if (!in) return fail(CH_EINVAL, "in is NULL");
   int64_t src = 0;
-  std::vector<float> tmp;
   for (int k = 0; k < h->m; ++k) {
     const MemberParams& p = h->hp[k];
     const int64_t np = (int64_t)p.nx * p.ny;
@@ -895,13 +940,8 @@ int ch_set_fields(ch_handle h, const double* in) {
       CH_CUDA(cudaMemcpyAsync(static_cast<double*>(h->C) + p.offset, in + src, sizeof(double) * np,
                               cudaMemcpyHostToDevice, h->stream),
               "write fields");
-    } else {
-      tmp.resize(np);
-      for (int64_t i = 0; i < np; ++i) tmp[i] = (float)in[src + i];
-      CH_CUDA(cudaMemcpyAsync(static_cast<float*>(h->C) + p.offset, tmp.data(), sizeof(float) * np,
-                              cudaMemcpyHostToDevice, h->stream),
-              "write fields");
-      CH_CUDA(cudaStreamSynchronize(h->stream), "write fields");
+    } else if (int rc = write_member_field(h, k, in + src)) {
+      return rc;
     }
     src += np;
   }
@@ -913,7 +953,6 @@ int ch_get_fields(ch_handle h, double* out) {
   if (int rc = check_handle(h)) return rc;
   if (!out) return fail(CH_EINVAL, "out is NULL");
   int64_t dst = 0;
-  std::vector<float> tmp;
   for (int k = 0; k < h->m; ++k) {
     const MemberParams& p = h->hp[k];
     const int64_t np = (int64_t)p.nx * p.ny;
@@ -921,11 +960,8 @@ int ch_get_fields(ch_handle h, double* out) {
       CH_CUDA(cudaMemcpyAsync(out + dst, static_cast<double*>(h->C) + p.offset, sizeof(double) * np,
                               cudaMemcpyDeviceToHost, h->stream),
               "read fields");
-    } else {
-      tmp.resize(np);
-      if (int rc = copy_out(h, tmp.data(), static_cast<float*>(h->C) + p.offset, sizeof(float) * np, "read fields"))
-        return rc;
-      for (int64_t i = 0; i < np; ++i) out[dst + i] = tmp[i];
+    } else if (int rc = read_member_field(h, k, out + dst)) {
+      return rc;
     }
     dst += np;
   }
@@ -1032,11 +1068,12 @@ int ch_debug_row_solve(ch_handle h, int member, double* out) {
 }
 
 // Checkpoint file: "CHCKPT01", int32 precision, int32 m, m x (int32 nx, int32 ny),
-// int64 series_cap, fields (elt * total_points bytes), MemberState[m], series ring.
+// int64 series_cap, fields (elt * c_points bytes: the fields, then the lo blocks of
+// compensated FP32 members), MemberState[m], series ring.
 int ch_save(ch_handle h, const char* path) {
   if (int rc = check_handle(h)) return rc;
   if (!path) return fail(CH_EINVAL, "path is NULL");
-  std::vector<unsigned char> fields(h->elt * h->total_points);
+  std::vector<unsigned char> fields(h->elt * h->c_points);
   if (int rc = copy_out(h, fields.data(), h->C, fields.size(), "read fields")) return rc;
   std::vector<MemberState> s;
   if (int rc = read_states(h, s)) return rc;
@@ -1076,7 +1113,7 @@ int ch_load(ch_handle h, const char* path) {
   }
   int64_t cap = -1;
   ok = ok && fread(&cap, sizeof cap, 1, f) == 1 && cap == h->series_cap;
-  std::vector<unsigned char> fields(h->elt * h->total_points);
+  std::vector<unsigned char> fields(h->elt * h->c_points);
   std::vector<MemberState> s(h->m);
   std::vector<double> series(4 * (size_t)h->series_cap * h->m);
   ok = ok && fread(fields.data(), 1, fields.size(), f) == fields.size();

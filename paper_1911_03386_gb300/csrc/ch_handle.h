@@ -30,6 +30,7 @@ struct ch_ensemble {
   chk::LaunchShape shape{};
   ch_tuning tuning{};             // as requested (0 / -1 = default)
   int64_t total_points = 0, max_points = 0;
+  int64_t c_points = 0;            // elements of C: the fields, then the lo blocks of compensated members
   int64_t total_bands = 0;
   int every = 1;
   double t1 = 0.0;
@@ -101,5 +102,8 @@ void drop_graph(ch_ensemble* h);
 int launch_steps_direct(ch_ensemble* h, int64_t n);
 int copy_out(ch_ensemble* h, void* dst, const void* src, size_t bytes, const char* what);
 int read_states(ch_ensemble* h, std::vector<MemberState>& s);
+// Member k's field to / from FP64 host values (FP32 compensated members: hi + lo).
+int read_member_field(ch_ensemble* h, int k, double* out);
+int write_member_field(ch_ensemble* h, int k, const double* in);
 
 }  // namespace chh

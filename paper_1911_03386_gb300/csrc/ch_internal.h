@@ -48,6 +48,10 @@ struct MemberParams {
   uint64_t seed, counter_base;
   // the constants above rounded to FP32, for the FP32 kernels
   float fa, fbx, fby, frho, fw0, fp1x, fp2x, fp1y, fp2y, fkappa;
+  // FP32 form at large s: the field is the unevaluated pair hi + lo of FP32 values (hi in
+  // C at offset, lo in C at lo_offset); the update keeps the rounding error of hi in lo
+  int comp;              // 1: compensated update (lo_offset valid)
+  int64_t lo_offset;     // first element of the lo part in C, -1 if none
 };
 
 // Scan tables of the segment form of the row sweep (S points per lane, G lanes per row),

@@ -83,7 +83,10 @@ __global__ void init_fields_kernel(DevView v, const int* list, int count) {
       const double u = (double)(sm64_draw(P.seed, P.counter_base + (uint64_t)p) >> 11) *
                        (1.0 / 9007199254740992.0);
       const double noise = __dmul_rn(0.1, __dsub_rn(__dmul_rn(2.0, u), 1.0));
-      C[p] = (T)__dadd_rn(P.C0, noise);
+      const double c = __dadd_rn(P.C0, noise);
+      C[p] = (T)c;
+      if (sizeof(T) == 4 && P.comp)  // lo part: the exact remainder of the FP64 value
+        static_cast<T*>(v.C)[P.lo_offset + p] = (T)__dsub_rn(c, (double)(T)c);
     }
   }
 }
@@ -394,11 +397,22 @@ __device__ __forceinline__ void compute_mu(const T* Cs, int lc, T* Ms, int lm, i
 // rows in registers; lane 31 holds the column after the chunk, so east neighbours come
 // from the next lane.  Fixed work split and order: deterministic.
 template <typename T>
-__device__ void band_partials_mu64(const T* Cs, int lc, int nx, int nr, const MemberParams& P, double2* slot,
-                                   double* red) {
+__device__ void band_partials_mu64(const DevView& v, const Tile& tl, int nx, int nr, const MemberParams& P,
+                                   double2* slot, double* red) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const double a = P.a, bx = P.bx, by = P.by;
+  // the stored field in FP64 (hi + lo for compensated members), read from global memory:
+  // band row q of the tile is field row j0 - 2 + q (periodic)
+  const T* Hg = static_cast<const T*>(v.C) + P.offset;
+  const T* Lg = P.comp ? static_cast<const T*>(v.C) + P.lo_offset : nullptr;
+  const int ny = P.ny;
+  auto at = [&](int q, int ii) {
+    int j = (tl.start - 2 + q) % ny;
+    if (j < 0) j += ny;
+    const int64_t k = (int64_t)j * nx + ii;
+    return Lg ? (double)Hg[k] + (double)Lg[k] : (double)Hg[k];
+  };
   const int nchunk = (nx + 30) / 31;
   const int nstrip = max(1, nwarps / nchunk);
   const int hs = (nr + nstrip - 1) / nstrip;
@@ -412,11 +426,11 @@ __device__ void band_partials_mu64(const T* Cs, int lc, int nx, int nr, const Me
     const bool own = lane < 31 && 31 * k + lane < nx;
     const int iw = i == 0 ? nx - 1 : i - 1, ie = i + 1 == nx ? 0 : i + 1;
     // C at tile row q in FP64, and its west / east neighbours (shuffles inside the chunk)
-    auto cload = [&](int q) { return (double)Cs[(size_t)q * lc + i]; };
+    auto cload = [&](int q) { return at(q, i); };
     auto mu_row = [&](int q, double cq, double cdn, double cup) {
       double w = __shfl_up_sync(full, cq, 1), e = __shfl_down_sync(full, cq, 1);
-      if (lane == 0) w = (double)Cs[(size_t)q * lc + iw];
-      if (lane == 31) e = (double)Cs[(size_t)q * lc + ie];
+      if (lane == 0) w = at(q, iw);
+      if (lane == 31) e = at(q, ie);
       return cq * (cq * cq - a) - bx * (e + w) - by * (cup + cdn);
     };
     const int q0 = r0 + 2;
@@ -455,11 +469,12 @@ __device__ void band_partials_mu64(const T* Cs, int lc, int nx, int nr, const Me
 // FP64 partial sums of the F and dF/dt densities over the band's nr rows (C tile rows
 // 2..nr+1, mu rows 1..nr), reduced in fixed order; thread 0 stores them.
 template <typename T>
-__device__ __forceinline__ void band_partials(const T* Cs, int lc, const T* Ms, int lm, int nx, int nr,
-                                              const MemberParams& P, double2* slot, double* red, int seg = 0) {
+__device__ __forceinline__ void band_partials(const DevView& v, const Tile& tl, const T* Cs, int lc, const T* Ms,
+                                              int lm, int nx, int nr, const MemberParams& P, double2* slot,
+                                              double* red, int seg = 0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   if (sizeof(T) == sizeof(float)) {
-    band_partials_mu64<T>(Cs, lc, nx, nr, P, slot, red);
+    band_partials_mu64<T>(v, tl, nx, nr, P, slot, red);
     return;
   }
   double sF = 0.0, sD = 0.0;
@@ -586,7 +601,7 @@ __global__ void __launch_bounds__(512) rows_kernel(DevView v, int tile_base) {
   compute_mu<T>(Cs, lc, Ms, lm, nx, nr + 2, (T)P.a, (T)P.bx, (T)P.by);
   __syncthreads();
   if (sample) {
-    band_partials<T>(Cs, lc, Ms, lm, nx, nr, P, v.partials + P.partial_base + tl.index, red);
+    band_partials<T>(v, tl, Cs, lc, Ms, lm, nx, nr, P, v.partials + P.partial_base + tl.index, red);
     __syncthreads();
   }
   if (OBS_ONLY) return;
@@ -648,6 +663,27 @@ __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
+// C update of one point, C <- C + kappa z.  For compensated FP32 members the field is the
+// pair hi + lo (lo at the same index of the member's lo block): Fast2Sum (|hi| >= |d|)
+// keeps the rounding error of the new hi in lo, so the rounding of the stored field does
+// not accumulate in the weakly damped modes.  lo is null otherwise.
+template <typename T>
+__device__ __forceinline__ T c_update(T c, T kap, T z, T* lo) {
+  if (sizeof(T) == 4 && lo) {
+    const T d = kap * z + *lo;
+    const T s = c + d;
+    *lo = d - (s - c);
+    return s;
+  }
+  return fma(kap, z, c);
+}
+
+// The lo block of member P at element index i of its field, or null (plain update).
+template <typename T>
+__device__ __forceinline__ T* lo_ptr(const DevView& v, const MemberParams& P, int64_t i) {
+  return (sizeof(T) == 4 && P.comp) ? static_cast<T*>(v.C) + P.lo_offset + i : nullptr;
+}
+
 // 4 consecutive elements (16-byte aligned for float, 32-byte for double).
 __device__ __forceinline__ void ld4(const float* p, float* v) {
   const float4 q = *reinterpret_cast<const float4*>(p);
@@ -677,52 +713,67 @@ __device__ __forceinline__ void st4(double* p, const double* v) {
 // l the points [l S, l S + S); Ks = the scan constants A[0..4] (M^(S 2^d)) then P
 // ((I - M^n)^-1); B = M^(S pos), pos = the lane's place in the recurrence's order.  Every
 // lane of the warp must call it (full-warp shuffles, width G).
-template <typename T, int S, bool REV>
-__device__ __forceinline__ void seg_sweep(T (&y)[S], T p1, T p2, int l, int G, int lg, const T* Ks,
+template <typename T, int S, int R, bool REV>
+__device__ __forceinline__ void seg_sweep(T (&y)[R][S], T p1, T p2, int l, int G, int lg, const T* Ks,
                                           const T (&B)[4]) {
-  T a = T(0), b = T(0);
+  // R rows at once, each stage interleaved over the rows (independent chains)
+  T a[R], b[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) a[t] = b[t] = T(0);
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    const T t = fma(p1, a, fma(p2, b, y[REV ? S - 1 - k : k]));
-    b = a;
-    a = t;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const T v = fma(p1, a[t], fma(p2, b[t], y[t][REV ? S - 1 - k : k]));
+      b[t] = a[t];
+      a[t] = v;
+    }
   }
   const int pos = REV ? G - 1 - l : l;
 #pragma unroll
   for (int d = 0; d < 5; ++d) {
     if (d < lg) {
       const int delta = 1 << d;
-      const T ya = REV ? __shfl_down_sync(kFull, a, delta, G) : __shfl_up_sync(kFull, a, delta, G);
-      const T yb = REV ? __shfl_down_sync(kFull, b, delta, G) : __shfl_up_sync(kFull, b, delta, G);
       T A[4];
       ld4(Ks + 4 * d, A);
-      if (pos >= delta) {
-        const T na = fma(A[0], ya, fma(A[1], yb, a));
-        b = fma(A[2], ya, fma(A[3], yb, b));
-        a = na;
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const T ya = REV ? __shfl_down_sync(kFull, a[t], delta, G) : __shfl_up_sync(kFull, a[t], delta, G);
+        const T yb = REV ? __shfl_down_sync(kFull, b[t], delta, G) : __shfl_up_sync(kFull, b[t], delta, G);
+        if (pos >= delta) {
+          const T na = fma(A[0], ya, fma(A[1], yb, a[t]));
+          b[t] = fma(A[2], ya, fma(A[3], yb, b[t]));
+          a[t] = na;
+        }
       }
     }
   }
   const int last = REV ? 0 : G - 1;
-  const T Ea = __shfl_sync(kFull, a, last, G), Eb = __shfl_sync(kFull, b, last, G);
   T Pm[4];
   ld4(Ks + 20, Pm);
-  const T xa = fma(Pm[0], Ea, Pm[1] * Eb), xb = fma(Pm[2], Ea, Pm[3] * Eb);
-  T pa = REV ? __shfl_down_sync(kFull, a, 1, G) : __shfl_up_sync(kFull, a, 1, G);
-  T pb = REV ? __shfl_down_sync(kFull, b, 1, G) : __shfl_up_sync(kFull, b, 1, G);
-  if (pos == 0) {
-    pa = T(0);
-    pb = T(0);
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const T Ea = __shfl_sync(kFull, a[t], last, G), Eb = __shfl_sync(kFull, b[t], last, G);
+    const T xa = fma(Pm[0], Ea, Pm[1] * Eb), xb = fma(Pm[2], Ea, Pm[3] * Eb);
+    T pa = REV ? __shfl_down_sync(kFull, a[t], 1, G) : __shfl_up_sync(kFull, a[t], 1, G);
+    T pb = REV ? __shfl_down_sync(kFull, b[t], 1, G) : __shfl_up_sync(kFull, b[t], 1, G);
+    if (pos == 0) {
+      pa = T(0);
+      pb = T(0);
+    }
+    a[t] = fma(B[0], xa, fma(B[1], xb, pa));
+    b[t] = fma(B[2], xa, fma(B[3], xb, pb));
   }
-  a = fma(B[0], xa, fma(B[1], xb, pa));
-  b = fma(B[2], xa, fma(B[3], xb, pb));
 #pragma unroll
   for (int k = 0; k < S; ++k) {
     const int u = REV ? S - 1 - k : k;
-    const T t = fma(p1, a, fma(p2, b, y[u]));
-    y[u] = t;
-    b = a;
-    a = t;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const T v = fma(p1, a[t], fma(p2, b[t], y[t][u]));
+      y[t][u] = v;
+      b[t] = a[t];
+      a[t] = v;
+    }
   }
 }
 
@@ -778,7 +829,7 @@ __device__ __forceinline__ void seg_tile(const DevView& v, const Tile& tl, const
   }
   __syncthreads();
   if (sample) {
-    band_partials<T>(Cs, nx, Ms, lmp, nx, nr, P, v.partials + P.partial_base + tl.index, red, S);
+    band_partials<T>(v, tl, Cs, nx, Ms, lmp, nx, nr, P, v.partials + P.partial_base + tl.index, red, S);
     __syncthreads();
   }
 
@@ -797,37 +848,45 @@ __device__ __forceinline__ void seg_tile(const DevView& v, const Tile& tl, const
   const T p1 = pick<T>(P.p1x, P.fp1x), p2 = pick<T>(P.p2x, P.fp2x), rho = pick<T>(P.rho, P.frho),
           w0 = pick<T>(P.w0, P.fw0);
   T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
-  const int rounds = (nr + ngroups - 1) / ngroups;
+  // FP32 with 16-point segments: two rows per group, their chains interleaved
+  constexpr int R = 1;  // rows per group (2 measured slower: fewer CTAs per SM)
+  const int rounds = (nr + R * ngroups - 1) / (R * ngroups);
   for (int k = 0; k < rounds; ++k) {
-    const int r = k * ngroups + grp;
-    const bool rv = r < nr;
-    const T* mrow = Ms + (size_t)((rv ? r : nr - 1) + 1) * lmp + l * (S + seg_pad<T>());
-    T m[S];
+    T m[R][S];
 #pragma unroll
-    for (int c = 0; c < S / 4; ++c) ld4(mrow + 4 * c, &m[4 * c]);
-    const T left = __shfl_sync(kFull, m[S - 1], (l + G - 1) & (G - 1), G);
-    const T right = __shfl_sync(kFull, m[0], (l + 1) & (G - 1), G);
-    T prev = left;
+    for (int t = 0; t < R; ++t) {
+      const int r = (k * ngroups + grp) * R + t;
+      const T* mrow = Ms + (size_t)((r < nr ? r : nr - 1) + 1) * lmp + l * (S + seg_pad<T>());
 #pragma unroll
-    for (int c = 0; c < S / 4; ++c) {
-      T up[4], dn[4];
-      ld4(mrow - lmp + 4 * c, up);
-      ld4(mrow + lmp + 4 * c, dn);
+      for (int c = 0; c < S / 4; ++c) ld4(mrow + 4 * c, &m[t][4 * c]);
+      const T left = __shfl_sync(kFull, m[t][S - 1], (l + G - 1) & (G - 1), G);
+      const T right = __shfl_sync(kFull, m[t][0], (l + 1) & (G - 1), G);
+      T prev = left;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int u = 4 * c + q;
-        const T cur = m[u];
-        const T e = u + 1 < S ? m[u + 1] : right;
-        m[u] = fma(w0, cur, fma(rho, dn[q] + up[q], e + prev));
-        prev = cur;
+      for (int c = 0; c < S / 4; ++c) {
+        T up[4], dn[4];
+        ld4(mrow - lmp + 4 * c, up);
+        ld4(mrow + lmp + 4 * c, dn);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = 4 * c + q;
+          const T cur = m[t][u];
+          const T e = u + 1 < S ? m[t][u + 1] : right;
+          m[t][u] = fma(w0, cur, fma(rho, dn[q] + up[q], e + prev));
+          prev = cur;
+        }
       }
     }
-    seg_sweep<T, S, false>(m, p1, p2, l, G, lg, Ks, Bf);
-    seg_sweep<T, S, true>(m, p1, p2, l, G, lg, Ks, Bb);
-    if (rv) {
-      T* dst = W + (int64_t)(j0 + r) * nx + l * S;
+    seg_sweep<T, S, R, false>(m, p1, p2, l, G, lg, Ks, Bf);
+    seg_sweep<T, S, R, true>(m, p1, p2, l, G, lg, Ks, Bb);
 #pragma unroll
-      for (int c = 0; c < S / 4; ++c) st4(dst + 4 * c, &m[4 * c]);
+    for (int t = 0; t < R; ++t) {
+      const int r = (k * ngroups + grp) * R + t;
+      if (r < nr) {
+        T* dst = W + (int64_t)(j0 + r) * nx + l * S;
+#pragma unroll
+        for (int c = 0; c < S / 4; ++c) st4(dst + 4 * c, &m[t][4 * c]);
+      }
     }
   }
 }
@@ -899,6 +958,8 @@ __device__ __noinline__ void rowT_partials(const DevView& v, const Tile& tl, con
   const int nx = P.nx, ny = P.ny, nr = tl.count;
   const double a = P.a, bx = P.bx, by = P.by;
   const int iww = iw == 0 ? nx - 1 : iw - 1;
+  const int64_t dlo = P.comp ? P.lo_offset - P.offset : 0;  // lo block relative to hi
+  auto val = [&](const T* r, int ii) { return P.comp ? (double)r[ii] + (double)r[dlo + ii] : (double)r[ii]; };
   int jn = tl.start - 2;
   if (jn < 0) jn += ny;
   const T* r0 = Cm + (int64_t)jn * nx;
@@ -908,13 +969,13 @@ __device__ __noinline__ void rowT_partials(const DevView& v, const Tile& tl, con
   for (int q = 0; q <= nr; ++q) {  // mu rows j0-1 .. j0+nr-1
     if (++jn == ny) jn = 0;
     const T* r2 = Cm + (int64_t)jn * nx;
-    const double cd = (double)r1[i], cs = (double)r0[i], cn = (double)r2[i];
+    const double cd = val(r1, i), cs = val(r0, i), cn = val(r2, i);
     double w = __shfl_up_sync(full, cd, 1), e = __shfl_down_sync(full, cd, 1);
-    if (lane == 0) w = (double)r1[iw];
-    if (lane == 31) e = (double)r1[ie];
+    if (lane == 0) w = val(r1, iw);
+    if (lane == 31) e = val(r1, ie);
     const double mu = cd * (cd * cd - a) - bx * (e + w) - by * (cn + cs);
     double muw = __shfl_up_sync(full, mu, 1);
-    if (lane == 0) muw = w * (w * w - a) - bx * (cd + (double)r1[iww]) - by * ((double)r2[iw] + (double)r0[iw]);
+    if (lane == 0) muw = w * (w * w - a) - bx * (cd + val(r1, iww)) - by * (val(r2, iw) + val(r0, iw));
     if (q >= 1) {
       const double gx = cd - w, gy = cd - cs, wv = cd * cd - 1.0, mx = mu - muw, my = mu - mu_prev;
       sw += wv * wv;
@@ -1129,7 +1190,7 @@ __global__ void __launch_bounds__(512) stencil_kernel(DevView v) {
   __syncthreads();
   compute_mu<T>(Cs, lc, Ms, lm, nx, nr + 2, (T)P.a, (T)P.bx, (T)P.by);
   __syncthreads();
-  if (sample) band_partials<T>(Cs, lc, Ms, lm, nx, nr, P, v.partials + P.partial_base + tl.index, red);
+  if (sample) band_partials<T>(v, tl, Cs, lc, Ms, lm, nx, nr, P, v.partials + P.partial_base + tl.index, red);
 
   T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
   const T rho = (T)P.rho, w0 = (T)P.w0;
@@ -1266,11 +1327,12 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
             const T* c = Cs + (size_t)j * nc + E * tv;
             T* g = C + (int64_t)j * nx + i0 + E * tv;
             if (E == 4) {
+              const int64_t idx = (int64_t)j * nx + i0 + E * tv;
               float4 o;
-              o.x = (float)fma(kap, w[0], c[0]);
-              o.y = (float)fma(kap, w[1], c[1]);
-              o.z = (float)fma(kap, w[2], c[2]);
-              o.w = (float)fma(kap, w[3], c[3]);
+              o.x = (float)c_update<T>(c[0], kap, w[0], lo_ptr<T>(v, P, idx));
+              o.y = (float)c_update<T>(c[1], kap, w[1], lo_ptr<T>(v, P, idx + 1));
+              o.z = (float)c_update<T>(c[2], kap, w[2], lo_ptr<T>(v, P, idx + 2));
+              o.w = (float)c_update<T>(c[3], kap, w[3], lo_ptr<T>(v, P, idx + 3));
               *reinterpret_cast<float4*>(g) = o;
             } else {
               double2 o;
@@ -1283,7 +1345,8 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
         const int tx = threadIdx.x % nc, ty = threadIdx.x / nc, ry = blockDim.x / nc;
         if (ty < ry)
           for (int j = ty; j < ny; j += ry)
-            C[(int64_t)j * nx + i0 + tx] = fma(kap, Ws[(size_t)j * ldc + tx], Cs[(size_t)j * ldc + tx]);
+            C[(int64_t)j * nx + i0 + tx] = c_update<T>(Cs[(size_t)j * ldc + tx], kap, Ws[(size_t)j * ldc + tx],
+                                                       lo_ptr<T>(v, P, (int64_t)j * nx + i0 + tx));
       }
       // Panel 0 finalises the member's sample of this step (partials written by the
       // stencil phase of the same step) and advances the member's step counter.  No other
@@ -1386,7 +1449,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) colseg_kernel(Dev
 #pragma unroll
       for (int u = 0; u < 8; ++u) c[u] = Cg[(int64_t)(u0 + u) * nx];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) Cg[(int64_t)(u0 + u) * nx] = fma(kap, y[u0 + u], c[u]);
+      for (int u = 0; u < 8; ++u) {
+        const int64_t idx = (int64_t)(wseg * S + u0 + u) * nx + col;
+        Cg[(int64_t)(u0 + u) * nx] = c_update<T>(c[u], kap, y[u0 + u], lo_ptr<T>(v, P, idx));
+      }
     }
   }
   // The first tile of the member finalises its sample of this step and advances its step
@@ -1473,7 +1539,10 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
           const T x = fma(p1, x1, fma(p2, x2, r[u]));
           x2 = x1;
           x1 = x;
-          if (q0 + u >= K) Cc[(int64_t)(ny - 1 - (q0 + u - K)) * nx] = fma(kap, x, c[u]);
+          if (q0 + u >= K) {
+            const int64_t jj = ny - 1 - (q0 + u - K);
+            Cc[jj * nx] = c_update<T>(c[u], kap, x, lo_ptr<T>(v, P, jj * nx + tl.start + lane));
+          }
         }
       }
     }

@@ -97,6 +97,8 @@ struct Req {
   double* field_out = nullptr;
   int slot = -1;
   int64_t offset = -1, elems = 0;
+  bool comp = false;          // FP32 run at large s: a second arena block holds the lo part
+  int64_t lo_offset = -1;
   int status = CH_PENDING;
   Clock::time_point t_submit, t_admit, t_done;
   ch_result res{};
@@ -148,6 +150,7 @@ int admit_slots(ch_server_s* S, const std::vector<int>& slots, const std::vector
     const Req& r = *reqs[i];
     if (int rc = chh::fill_params(r.d, h->precision, &h->hp[k])) return rc;
     h->hp[k].offset = r.offset;
+    h->hp[k].lo_offset = r.comp ? r.lo_offset : -1;
     h->hp[k].every = r.every;
     h->hp[k].t1 = r.t1;
     h->hp[k].series_cap = 0;
@@ -174,7 +177,6 @@ void worker_main(ch_server_s* S) {
   cudaSetDevice(h->device);
   std::vector<MemberState> states;
   std::vector<double> obs(3 * (size_t)h->m), fbuf;
-  std::vector<float> fbuf32;
   for (;;) {
     std::vector<int> slots;
     std::vector<Req*> admitted;
@@ -188,8 +190,14 @@ void worker_main(ch_server_s* S) {
         if (free_slot == S->slot_req.end()) break;
         const int64_t off = S->arena.alloc(r.elems);
         if (off < 0) break;
+        int64_t lo = -1;
+        if (r.comp && (lo = S->arena.alloc(r.elems)) < 0) {
+          S->arena.release(off, r.elems);
+          break;
+        }
         r.slot = (int)(free_slot - S->slot_req.begin());
         r.offset = off;
+        r.lo_offset = lo;
         r.t_admit = Clock::now();
         *free_slot = r.id;
         slots.push_back(r.slot);
@@ -250,18 +258,8 @@ void worker_main(ch_server_s* S) {
         id = S->slot_req[k];
         fout = S->reqs[id].field_out;
       }
-      const MemberParams& p = h->hp[k];
-      const int64_t np = (int64_t)p.nx * p.ny;
       if (fout) {
-        int rc;
-        if (h->precision == CH_FP64) {
-          rc = chh::copy_out(h, fout, static_cast<double*>(h->C) + p.offset, sizeof(double) * np, "field");
-        } else {
-          fbuf32.resize(np);
-          rc = chh::copy_out(h, fbuf32.data(), static_cast<float*>(h->C) + p.offset, sizeof(float) * np, "field");
-          for (int64_t i = 0; i < np && rc == CH_OK; ++i) fout[i] = fbuf32[i];
-        }
-        if (rc) {
+        if (int rc = chh::read_member_field(h, k, fout)) {
           server_fail_all(S, rc, "field read failed");
           return;
         }
@@ -311,6 +309,7 @@ void worker_main(ch_server_s* S) {
         r.res.t_total_s = seconds(r.t_done - r.t_submit);
         r.status = r.res.nonfinite ? CH_ENONFINITE : CH_OK;
         S->arena.release(r.offset, r.elems);
+        if (r.comp) S->arena.release(r.lo_offset, r.elems);
         S->slot_req[r.slot] = 0;
         S->running -= 1;
         S->completed += 1;
@@ -408,9 +407,12 @@ int ch_submit(ch_server s, const ch_request* r, uint64_t* id) {
   if (r->nsteps < 1) return fail(CH_EINVAL, "nsteps must be >= 1");
   if (r->every < 0) return fail(CH_EINVAL, "every must be >= 0");
   const int64_t elems = (int64_t)r->nx * r->ny;
+  MemberParams probe;
+  if (int rc = chh::fill_params(d, s->h->precision, &probe)) return rc;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->error) return fail(s->error, "server failed: " + s->error_msg);
-  if (Arena::round(elems) > s->arena.capacity) return fail(CH_ENOMEM, "request larger than the server's HBM budget");
+  if (Arena::round(elems) * (probe.comp ? 2 : 1) > s->arena.capacity)
+    return fail(CH_ENOMEM, "request larger than the server's HBM budget");
   if ((int64_t)s->queue.size() >= kMaxQueue) return fail(CH_EBUSY, "request queue full");
   Req q;
   q.id = s->next_id++;
@@ -420,6 +422,7 @@ int ch_submit(ch_server s, const ch_request* r, uint64_t* id) {
   q.t1 = r->t1 >= 0.0 ? r->t1 : 0.2 * (double)r->nsteps * r->dt;
   q.field_out = r->field_out;
   q.elems = elems;
+  q.comp = probe.comp != 0;
   q.t_submit = Clock::now();
   s->reqs.emplace(q.id, q);
   s->queue.push_back(q.id);

@@ -182,6 +182,62 @@ def test_fp32_form_200_steps(orc):
 
 
 # ------------------------------------------------------------------------------------------
+# FP32 form at large s: the field is kept as the pair hi + lo (compensated update) for
+# members with max(s_x, s_y) > 16; the pair holds the FP64 initial field to ~2^-48
+# ------------------------------------------------------------------------------------------
+COMP = dict(nx=64, ny=48, L=TWO_PI, gamma=0.5, dt=4e-3)  # s_x = 21.5 > 16, dt < 0.7 gamma
+
+
+def test_fp32_compensated_initial_field_and_round_trip(orc):
+    d = COMP
+    with ens(d["nx"], d["ny"], [0.2, -0.1], d["gamma"], d["dt"], d["L"], prec=ch.CH_FP32) as e:
+        for k, c0 in enumerate([0.2, -0.1]):
+            ref = orc.initial_field(d["nx"], d["ny"], c0, SEED, k * d["nx"] * d["ny"])
+            got = e.field(k)
+            assert np.max(np.abs(got - ref)) <= 2.0 ** -46 * np.max(np.abs(ref))  # plain FP32: 2^-24
+            assert not np.array_equal(got, ref.astype(np.float32).astype(np.float64))
+        x = np.ascontiguousarray(wl.random_field(d["ny"], d["nx"], 3, amplitude=0.7, mean=0.05))
+        e.set_field(1, x)
+        assert np.max(np.abs(e.field(1) - x)) <= 2.0 ** -46
+    # below the threshold the FP32 field is plain FP32
+    with ens(d["nx"], d["ny"], [0.2], 0.01, 1e-3, d["L"], prec=ch.CH_FP32) as e:
+        ref = orc.initial_field(d["nx"], d["ny"], 0.2, SEED, 0)
+        assert np.array_equal(e.field(0), ref.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("tuning", [dict(), dict(split=0, col_seg=-1), dict(split=1, stream=1)],
+                         ids=["segment", "panels", "streaming"])
+def test_fp32_compensated_run_matches_oracle(orc, tuning):
+    d = COMP
+    C0 = orc.initial_field(d["nx"], d["ny"], 0.3, SEED, 0)
+    nsteps = 200
+    ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps, every=20)
+    with ens(d["nx"], d["ny"], [0.3], d["gamma"], d["dt"], d["L"], prec=ch.CH_FP32) as e:
+        e.set_tuning(**tuning)
+        e.set_sampling(20, 0.0, capacity=16)
+        e.step(nsteps)
+        err = np.max(np.abs(e.field(0) - ref.C))
+        ser = e.series(0, 16)
+    assert err <= 1e-4, err
+    np.testing.assert_allclose(ser[:, 1], ref.series[:, 1], rtol=1e-5)
+    np.testing.assert_allclose(ser[:, 2], ref.series[:, 2], rtol=1e-3)
+
+
+def test_fp32_compensated_checkpoint(tmp_path):
+    d = COMP
+    path = str(tmp_path / "ck32.bin")
+    with ens(d["nx"], d["ny"], [0.0, 0.3], d["gamma"], d["dt"], d["L"], prec=ch.CH_FP32) as e:
+        e.step(30)
+        e.save(path)
+        e.step(20)
+        a = [e.field(k) for k in range(2)]
+        e.load(path)
+        e.step(20)
+        for k in range(2):
+            assert np.array_equal(a[k], e.field(k))
+
+
+# ------------------------------------------------------------------------------------------
 # Observables on their own; non-finite detection
 # ------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])

@@ -76,6 +76,22 @@ def test_result_same_alone_and_in_mix(prec):
         assert alone[k] == mixed[k], k
 
 
+def test_fp32_compensated_run_served_equals_ensemble():
+    # s_x = 21.5 > 16: the served FP32 run keeps hi + lo in two arena blocks
+    r = req(64, 48, 150, C0=0.3, seed=5, gamma=0.5, dt=4e-3, L=TWO_PI)
+    with ch.Server(16 << 20, ch.CH_FP32) as s:
+        res = s.wait(s.submit(**r), 120.0)
+    with ch.Ensemble.create(64, 48, TWO_PI, 0.5, 4e-3, [0.3], 5, ch.CH_FP32) as e:
+        e.set_tuning(split=0)
+        e.set_sampling(10, 0.2 * 150 * 4e-3, 0)
+        e.step(150)
+        field = e.field(0)
+        F, D, B = e.observables()
+        avg, cnt = e.beta_avg()
+    assert np.array_equal(r["field_out"].reshape(48, 64), field)
+    assert res["F"] == F[0] and res["beta_avg"] == avg[0]
+
+
 def test_admission_respects_hbm_budget():
     # FP32: a 128x128 run needs 2 x 64 KiB (field + scratch); the budget fits one at a time
     budget = 2 * 128 * 128 * 4 + 4096
