@@ -503,6 +503,15 @@ def main():
                 r.pop("beta_avg")
                 legs[pname] = r
             legs["fp32_speedup"] = legs["fp32"]["value"] / legs["fp64"]["value"]
+            if descs is udescs:
+                # the same batch with the autotuner's choice of shape per precision
+                from paper_1911_03386_gb300 import autotune
+                for prec, pname in ((ch.CH_FP32, "fp32"), (ch.CH_FP64, "fp64")):
+                    best, table = autotune.tune(descs, prec)
+                    r = run_descs_leg(ch, torch, descs, prec, nsteps, every, t1, tuning=best)
+                    r.pop("beta_avg")
+                    r["candidates"] = len(table)
+                    legs[pname + "_autotuned"] = r
             batches[name] = legs
         if args.long_beta:
             # <beta> over the whole horizon, t in [20, 100] (the paper's window), FP32 vs FP64

@@ -407,9 +407,10 @@ __device__ void band_partials_mu64(const DevView& v, const Tile& tl, int nx, int
   const T* Hg = static_cast<const T*>(v.C) + P.offset;
   const T* Lg = P.comp ? static_cast<const T*>(v.C) + P.lo_offset : nullptr;
   const int ny = P.ny;
+  // field row of band row q (q from -1 to nr + 3, j0 - 3 .. j0 + nr + 1): one wrap at most
   auto at = [&](int q, int ii) {
-    int j = (tl.start - 2 + q) % ny;
-    if (j < 0) j += ny;
+    int j = tl.start - 2 + q;
+    j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
     const int64_t k = (int64_t)j * nx + ii;
     return Lg ? (double)Hg[k] + (double)Lg[k] : (double)Hg[k];
   };
@@ -1315,6 +1316,7 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
       }
       __syncthreads();
       T* __restrict__ C = static_cast<T*>(v.C) + P.offset;
+      T* const Lb = lo_ptr<T>(v, P, 0);  // lo block of compensated members, else null
       const T kap = (T)P.kappa;
       if (vec) {
         // 16-byte pieces: 4 floats or 2 doubles per thread and row
@@ -1327,12 +1329,12 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
             const T* c = Cs + (size_t)j * nc + E * tv;
             T* g = C + (int64_t)j * nx + i0 + E * tv;
             if (E == 4) {
-              const int64_t idx = (int64_t)j * nx + i0 + E * tv;
+              T* lo = Lb ? Lb + (int64_t)j * nx + i0 + E * tv : nullptr;
               float4 o;
-              o.x = (float)c_update<T>(c[0], kap, w[0], lo_ptr<T>(v, P, idx));
-              o.y = (float)c_update<T>(c[1], kap, w[1], lo_ptr<T>(v, P, idx + 1));
-              o.z = (float)c_update<T>(c[2], kap, w[2], lo_ptr<T>(v, P, idx + 2));
-              o.w = (float)c_update<T>(c[3], kap, w[3], lo_ptr<T>(v, P, idx + 3));
+              o.x = (float)c_update<T>(c[0], kap, w[0], lo);
+              o.y = (float)c_update<T>(c[1], kap, w[1], lo ? lo + 1 : nullptr);
+              o.z = (float)c_update<T>(c[2], kap, w[2], lo ? lo + 2 : nullptr);
+              o.w = (float)c_update<T>(c[3], kap, w[3], lo ? lo + 3 : nullptr);
               *reinterpret_cast<float4*>(g) = o;
             } else {
               double2 o;
@@ -1346,7 +1348,7 @@ __global__ void __launch_bounds__(512) cols_kernel(DevView v, int ntiles, int pa
         if (ty < ry)
           for (int j = ty; j < ny; j += ry)
             C[(int64_t)j * nx + i0 + tx] = c_update<T>(Cs[(size_t)j * ldc + tx], kap, Ws[(size_t)j * ldc + tx],
-                                                       lo_ptr<T>(v, P, (int64_t)j * nx + i0 + tx));
+                                                       Lb ? Lb + (int64_t)j * nx + i0 + tx : nullptr);
       }
       // Panel 0 finalises the member's sample of this step (partials written by the
       // stencil phase of the same step) and advances the member's step counter.  No other
@@ -1442,16 +1444,32 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) colseg_kernel(Dev
   colseg_pass<T, S, true>(y, p1, p2, tab, xb, warp, lane, wseg, wp, pbase);
   if (cv) {
     const T kap = pick<T>(P.kappa, P.fkappa);
-    T* __restrict__ Cg = static_cast<T*>(v.C) + P.offset + (int64_t)wseg * S * nx + col;
+    const int64_t base = (int64_t)wseg * S * nx + col;
+    T* __restrict__ Cg = static_cast<T*>(v.C) + P.offset + base;
+    T* const Lg = lo_ptr<T>(v, P, base);  // lo part of compensated members, else null
+    if (Lg) {
 #pragma unroll
-    for (int u0 = 0; u0 < S; u0 += 8) {  // 8 loads in flight, few extra registers
-      T c[8];
+      for (int u0 = 0; u0 < S; u0 += 4) {  // hi and lo of 4 rows in flight, then the pair update
+        T c[4], lo[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) c[u] = Cg[(int64_t)(u0 + u) * nx];
+        for (int u = 0; u < 4; ++u) {
+          c[u] = Cg[(int64_t)(u0 + u) * nx];
+          lo[u] = Lg[(int64_t)(u0 + u) * nx];
+        }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t idx = (int64_t)(wseg * S + u0 + u) * nx + col;
-        Cg[(int64_t)(u0 + u) * nx] = c_update<T>(c[u], kap, y[u0 + u], lo_ptr<T>(v, P, idx));
+        for (int u = 0; u < 4; ++u) {
+          Cg[(int64_t)(u0 + u) * nx] = c_update<T>(c[u], kap, y[u0 + u], &lo[u]);
+          Lg[(int64_t)(u0 + u) * nx] = lo[u];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u0 = 0; u0 < S; u0 += 8) {  // 8 loads in flight, few extra registers
+        T c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) c[u] = Cg[(int64_t)(u0 + u) * nx];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) Cg[(int64_t)(u0 + u) * nx] = fma(kap, y[u0 + u], c[u]);
       }
     }
   }
@@ -1502,6 +1520,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
     T* Wc = static_cast<T*>(v.W) + P.offset + tl.start + lane;
     T* Cc = static_cast<T*>(v.C) + P.offset + tl.start + lane;
     const T p1 = (T)P.p1y, p2 = (T)P.p2y, kap = (T)P.kappa;
+    T* const Lc = lo_ptr<T>(v, P, tl.start + lane);  // lo column of compensated members, else null
     constexpr int kUnroll = 8;  // loads issued ahead of the recurrence
     const int len = K + ny;
     // forward: y_j = W'_j + p1 y_{j-1} + p2 y_{j-2}; y written over W'
@@ -1541,7 +1560,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
           x1 = x;
           if (q0 + u >= K) {
             const int64_t jj = ny - 1 - (q0 + u - K);
-            Cc[jj * nx] = c_update<T>(c[u], kap, x, lo_ptr<T>(v, P, jj * nx + tl.start + lane));
+            Cc[jj * nx] = c_update<T>(c[u], kap, x, Lc ? Lc + jj * nx : nullptr);
           }
         }
       }
