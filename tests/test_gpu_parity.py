@@ -366,6 +366,67 @@ def test_ensemble_256_full_size_sampled_members(orc):
             assert abs(C.sum() - C0.sum()) <= 1e-9
 
 
+def test_ensemble_256_fp32_full_size_sampled_members(orc):
+    # the FP32 leg of the benchmark: default kernel classes (segment rows and columns)
+    p = wl.ENSEMBLE_256
+    nsteps = 200
+    with ens(p["nx"], p["ny"], p["C0"], p["gamma"], p["dt"], p["L"], prec=ch.CH_FP32) as e:
+        t = e.tuning()
+        assert t["row_seg"] == 16 and t["col_seg"] == 32
+        e.set_sampling(p["every"], p["t1"], capacity=4)
+        e.step(nsteps)
+        F, D, B = e.observables()
+        s = p["gamma"] * p["dt"] / (p["L"] / p["nx"]) ** 4
+        for k in (3, 255):
+            C0 = orc.initial_field(p["nx"], p["ny"], p["C0"][k], SEED, k * p["nx"] * p["ny"])
+            C1 = C0.copy()
+            orc.step(C1, p["L"], p["gamma"], p["dt"])
+            ref = orc.run(C0, p["L"], p["gamma"], p["dt"], nsteps)
+            # at s = 13.8 the FP32 step's error is up to 2 u (1 + 16 s) of the step (see
+            # test_fp32_single_step_error_grows_with_s); bound: that of the first (largest)
+            # step, accumulated over the run
+            bound = nsteps * 2 * 2.0 ** -24 * (1 + 16 * s) * np.max(np.abs(C1 - C0))
+            err = np.max(np.abs(e.field(k) - ref.C))
+            assert err <= bound, (err, bound)
+            Fo, Do = orc.field_observables(ref.C, p["L"], p["gamma"])
+            assert abs(F[k] - Fo) <= 1e-5 * abs(Fo)
+
+
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+def test_uneven_full_size_sampled_members(orc, prec):
+    # 64 x 128^2 + 32 x 256^2 + 8 x 512^2 in one batch (the benchmark's uneven leg)
+    descs = wl.uneven_members()
+    nsteps = 20
+    with ch.Ensemble.batch(descs, prec) as e:
+        if prec == ch.CH_FP64:
+            e.set_tuning(split=0)  # the fused segment forms the benchmark uses for this batch
+        e.step(nsteps)
+        for k in (0, 95, 103):  # a 128^2, a 256^2 and a 512^2 member (FP32: compensated, s = 220)
+            d = descs[k]
+            C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
+            ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            assert err <= (1e-12 if prec == ch.CH_FP64 else 1e-4), (k, err)
+
+
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+def test_long_1024_full_size_sampled_members(orc, prec):
+    # 32 x 1024^2, gamma 0.0025, dt 5e-4 (s = 882): two members against the oracle
+    lb = wl.LONG_1024
+    descs = [dict(nx=lb["nx"], ny=lb["ny"], L=lb["L"], gamma=lb["gamma"], dt=lb["dt"], C0=c0, seed=SEED,
+                  counter_base=k * lb["nx"] * lb["ny"]) for k, c0 in enumerate(lb["C0"])]
+    nsteps = 10
+    with ch.Ensemble.batch(descs, prec) as e:
+        e.step(nsteps)
+        for k in (0, 31):
+            d = descs[k]
+            C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
+            ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            # FP64: single-step round-off times cond(I + s D^4) <= 1 + 16 s per direction
+            assert err <= (1e-10 if prec == ch.CH_FP64 else 1e-4), (k, err)
+
+
 # ------------------------------------------------------------------------------------------
 # Every launch shape gives the oracle's result (tuning changes only the round-off order)
 # ------------------------------------------------------------------------------------------
