@@ -348,6 +348,15 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     if (t.row_seg > 0) return t.row_seg;
     return row_fits(p, 16) ? 16 : row_fits(p, 32) ? 32 : 0;
   };
+  // split form: segment-form row sweep (rowseg_kernel) for FP32 members that fit, or for
+  // every member with an explicit S; the pre-rolled sweeps otherwise (FP64 default: one
+  // thread per line costs fewer FP64 operations)
+  auto sweep_class = [&](const MemberParams& p) {
+    if (!split || t.row_seg < 0 || t.row_seg == 1) return 0;
+    if (t.row_seg > 1) return t.row_seg;
+    if (f64) return 0;
+    return row_fits(p, 16) ? 16 : row_fits(p, 32) ? 32 : 0;
+  };
   auto col_class = [&](const MemberParams& p) {
     if (t.col_seg < 0 || (t.col_seg == 0 && f64 && split)) return 0;
     if (t.col_seg > 0) return t.col_seg;
@@ -359,7 +368,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     const MemberParams& p = h->hp[k];
     if (t.row_seg == 1 && !split && !rowT_fits(p))
       return fail(CH_EINVAL, "row_seg 1: some member's nx is not 32 times at most 16");
-    if (t.row_seg > 1 && !split && !row_fits(p, t.row_seg))
+    if (t.row_seg > 1 && !row_fits(p, t.row_seg))
       return fail(CH_EINVAL, "row_seg: some member's nx is not S times a power of two <= 32");
     if (t.col_seg > 0 && !col_fits(p, t.col_seg))
       return fail(CH_EINVAL, "col_seg: some member's ny is not S times a power of two <= 32 (<= 16 for FP64)");
@@ -367,7 +376,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     if (cc) cwarps[cc == 32] = std::max(cwarps[cc == 32], p.ny / cc);
   }
 
-  std::vector<Tile> rts[3], csts[2], st, ct;  // rows: S = 16, S = 32, chunked; columns: S = 16, 32
+  std::vector<Tile> rts[3], csts[2], sts[3], ct;  // rows: S = 16, S = 32, chunked; columns: S = 16, 32
   std::vector<Tile> rtT[17];                   // rows, transposed-block form, by nw
   chk::LaunchShape sh{};
   sh.split = split;
@@ -384,6 +393,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       continue;
     }
     const int rc = row_class(p), cc = col_class(p), ri = rc == 16 ? 0 : rc == 32 ? 1 : 2;
+    const int sc = sweep_class(p), si = sc == 16 ? 0 : sc == 32 ? 1 : 2;
     const bool seg = rc > 1;
     int br = std::min(p.ny, rc == 1 ? 32 : seg ? want_br_seg : want_br);
     auto row_bytes = [&](int nr) {
@@ -395,10 +405,11 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     if (seg && t.rows_band <= 0)
       while (br > 4 && row_bytes(br) > kSmemMax / 2) br = (br + 1) / 2;
     if (rc != 1 && row_bytes(br) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
-    p.seg_g = seg ? p.nx / rc : 0;
+    p.seg_g = seg ? p.nx / rc : sc ? p.nx / sc : 0;
     p.row_t = rc == 1 ? p.nx / 32 : 0;
     p.col_s = cc;
     if (rc == 1) seg_tables(p.p1x, p.p2x, 32, p.nx / 32, &h->hseg[k]);
+    if (sc) seg_tables(p.p1x, p.p2x, sc, p.nx / sc, &h->hseg[k]);
     if (seg) {
       seg_tables(p.p1x, p.p2x, rc, p.seg_g, &h->hseg[k]);
       sh.seg_ccap[ri] = std::max(sh.seg_ccap[ri], (int)seg_ctile(br, p.nx));
@@ -422,9 +433,14 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     p.nbands = b;
     p.partial_base = part;
     part += b;
-    if (split) {
+    if (split && sc) {
+      // segment-form sweep: one row per lane group, two rounds per CTA
+      const int rows = 2 * (std::min(threads, 256) / 32) * (32 / (p.nx / sc));
       int q = 0;
-      for (int j0 = 0; j0 < p.ny; j0 += bs, ++q) st.push_back(Tile{k, j0, std::min(bs, p.ny - j0), q});
+      for (int j0 = 0; j0 < p.ny; j0 += rows, ++q) sts[si].push_back(Tile{k, j0, std::min(rows, p.ny - j0), q});
+    } else if (split) {
+      int q = 0;
+      for (int j0 = 0; j0 < p.ny; j0 += bs, ++q) sts[2].push_back(Tile{k, j0, std::min(bs, p.ny - j0), q});
       if (!stream) {
         sh.sweep_smem = std::max(sh.sweep_smem, sweep_smem_bytes(bs, p.nx, h->elt));
         sh.sweep_threads = std::max(sh.sweep_threads, std::max(128, round_warps(bs)));
@@ -475,7 +491,9 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     sh.colseg_threads[c] = 32 * cwarps[c];
     sh.colseg_smem[c] = (size_t)2 * 2 * 32 * cwarps[c] * h->elt;
   }
-  std::vector<Tile> rt, cst;
+  std::vector<Tile> rt, cst, st;
+  for (int c = 0; c < 2; ++c) sh.st_seg[c] = (int)sts[c].size();
+  for (int c = 0; c < 3; ++c) st.insert(st.end(), sts[c].begin(), sts[c].end());
   for (int nw = 1; nw <= 16; ++nw) {
     sh.rtT_n[nw] = (int)rtT[nw].size();
     rt.insert(rt.end(), rtT[nw].begin(), rtT[nw].end());
@@ -526,7 +544,7 @@ int upload_tiles(ch_ensemble* h) {
           "upload member parameters");
   int n_rowT = 0;
   for (int nw = 1; nw <= 16; ++nw) n_rowT += h->shape.rtT_n[nw];
-  if (h->shape.rt_seg[0] + h->shape.rt_seg[1] + n_rowT)
+  if (h->shape.rt_seg[0] + h->shape.rt_seg[1] + h->shape.st_seg[0] + h->shape.st_seg[1] + n_rowT)
     CH_CUDA(cudaMemcpyAsync(h->dseg, h->hseg.data(), sizeof(chk::SegTable) * h->m, cudaMemcpyHostToDevice, h->stream),
             "upload scan tables");
   if (!h->cst.empty()) {
@@ -1013,7 +1031,7 @@ int ch_get_tuning(ch_handle h, ch_tuning* t) {
   t->stream = h->shape.stream;
   t->persist = h->shape.cols_persist | (h->shape.seg_persist << 1);
   // kernel classes of member 0
-  t->row_seg = h->shape.split ? 0 : h->hp[0].row_t ? 1 : (h->hp[0].seg_g ? h->hp[0].nx / h->hp[0].seg_g : -1);
+  t->row_seg = h->hp[0].row_t ? 1 : (h->hp[0].seg_g ? h->hp[0].nx / h->hp[0].seg_g : (h->shape.split ? 0 : -1));
   t->col_seg = h->hp[0].col_s ? h->hp[0].col_s : -1;
   return CH_OK;
 }

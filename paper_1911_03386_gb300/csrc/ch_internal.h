@@ -121,6 +121,9 @@ struct LaunchShape {
   // with S = 16 (rt_seg[0] tiles) and S = 32 (rt_seg[1]), then the chunked form.
   int rtT_n[17];
   int rt_seg[2];
+  // split form: sweep tiles ordered S = 16 (st_seg[0]), S = 32 (st_seg[1]) segment-form
+  // members (rowseg_kernel), then the others
+  int st_seg[2];
   int seg_persist;       // 1: the segment row kernel walks its tiles with a double-buffered C band
   int seg_grid[2];       // CTAs of the persistent segment row kernel
   int seg_ccap[2], seg_mcap[2];  // elements of one C tile buffer / of the mu tile (max over the class)

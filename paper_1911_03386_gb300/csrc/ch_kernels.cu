@@ -1207,9 +1207,9 @@ __global__ void __launch_bounds__(512) stencil_kernel(DevView v) {
 // shared memory (pitch nx+1).
 // -------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(512) rowsweep_kernel(DevView v) {
+__global__ void __launch_bounds__(512) rowsweep_kernel(DevView v, int tile_base) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const Tile tl = v.sweep_tiles[blockIdx.x];
+  const Tile tl = v.sweep_tiles[tile_base + blockIdx.x];
   if (!v.ms[tl.member].active) return;
   const MemberParams& P = v.mp[tl.member];
   const int nx = P.nx, j0 = tl.start, nr = tl.count;
@@ -1226,6 +1226,54 @@ __global__ void __launch_bounds__(512) rowsweep_kernel(DevView v) {
     const T* src = Bs + (size_t)r * ld;
     T* dst = W + (int64_t)(j0 + r) * nx;
     for (int i = lane; i < nx; i += 32) dst[i] = src[i];
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// Split form, kernel 2, segment form: the row recurrences of R' (held in W) for a band of
+// rows, each row in the registers of G = nx / S lanes (S consecutive points per lane,
+// 16-byte loads and stores straight from HBM), solved by segment scans (top of this
+// file); W' written back in place.  No shared-memory tiles, one barrier at set-up.
+// -------------------------------------------------------------------------------------
+template <typename T, int S>
+__global__ void __launch_bounds__(256) rowseg_kernel(DevView v, int tile_base) {
+  __shared__ __align__(16) T Ks[24];
+  const Tile tl = v.sweep_tiles[tile_base + blockIdx.x];
+  if (!v.ms[tl.member].active) return;
+  const MemberParams& P = v.mp[tl.member];
+  const SegTable& tab = v.seg[tl.member];
+  if (threadIdx.x < 24)
+    Ks[threadIdx.x] = threadIdx.x < 20
+                          ? pick<T>(tab.A[threadIdx.x >> 2][threadIdx.x & 3], tab.Af[threadIdx.x >> 2][threadIdx.x & 3])
+                          : pick<T>(tab.P[threadIdx.x - 20], tab.Pf[threadIdx.x - 20]);
+  __syncthreads();
+  const int nx = P.nx, j0 = tl.start, nr = tl.count;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int G = P.seg_g;
+  const int lg = __ffs(G) - 1;
+  const int gpw = 32 / G, ngroups = nwarps * gpw;
+  const int l = lane & (G - 1), grp = warp * gpw + (lane >> lg);
+  T Bf[4], Bb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    Bf[k] = pick<T>(tab.B[l][k], tab.Bf[l][k]);
+    Bb[k] = pick<T>(tab.B[G - 1 - l][k], tab.Bf[G - 1 - l][k]);
+  }
+  const T p1 = pick<T>(P.p1x, P.fp1x), p2 = pick<T>(P.p2x, P.fp2x);
+  T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
+  const int rounds = (nr + ngroups - 1) / ngroups;
+  for (int k = 0; k < rounds; ++k) {
+    const int r = k * ngroups + grp;
+    T* row = W + (int64_t)(j0 + (r < nr ? r : nr - 1)) * nx + l * S;
+    T m[1][S];
+#pragma unroll
+    for (int c = 0; c < S / 4; ++c) ld4(row + 4 * c, &m[0][4 * c]);
+    seg_sweep<T, S, 1, false>(m, p1, p2, l, G, lg, Ks, Bf);
+    seg_sweep<T, S, 1, true>(m, p1, p2, l, G, lg, Ks, Bb);
+    if (r < nr) {
+#pragma unroll
+      for (int c = 0; c < S / 4; ++c) st4(row + 4 * c, &m[0][4 * c]);
+    }
   }
 }
 
@@ -1580,14 +1628,14 @@ struct StreamChunk {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v, int ntiles) {
+__global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v, int ntiles, int tile_base) {
   constexpr int CW = StreamChunk<T>::CW;
   constexpr int RPI = 32 / CW;  // rows covered by one warp-wide copy instruction
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kStreamWarps + w;
   if (wt >= ntiles) return;
-  const Tile tl = v.sweep_tiles[wt];
+  const Tile tl = v.sweep_tiles[tile_base + wt];
   if (!v.ms[tl.member].active) return;
   const MemberParams& P = v.mp[tl.member];
   const int nx = P.nx, K = P.kx, nr = tl.count;
@@ -1737,14 +1785,21 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
       else
         seg_launch<T>(v, sh, st);
       break;
-    case 1:
+    case 1: {
       if (!sh.split) return cudaSuccess;
+      // segment-form members first (sweep tiles ordered S = 16, S = 32, others)
+      const int threads = min(sh.rows_threads, 256);
+      if (sh.st_seg[0] > 0) rowseg_kernel<T, 16><<<sh.st_seg[0], threads, 0, st>>>(v, 0);
+      if (sh.st_seg[1] > 0) rowseg_kernel<T, 32><<<sh.st_seg[1], threads, 0, st>>>(v, sh.st_seg[0]);
+      const int base = sh.st_seg[0] + sh.st_seg[1], rest = sh.n_sweep_tiles - base;
+      if (rest <= 0) break;
       if (sh.stream)
-        rowstream_kernel<T><<<(sh.n_sweep_tiles + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps,
-                              rowstream_smem_bytes(sizeof(T)), st>>>(v, sh.n_sweep_tiles);
+        rowstream_kernel<T><<<(rest + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps,
+                              rowstream_smem_bytes(sizeof(T)), st>>>(v, rest, base);
       else
-        rowsweep_kernel<T><<<sh.n_sweep_tiles, sh.sweep_threads, sh.sweep_smem, st>>>(v);
+        rowsweep_kernel<T><<<rest, sh.sweep_threads, sh.sweep_smem, st>>>(v, base);
       break;
+    }
     default:
       colseg_launch<T>(v, sh, st);
       if (sh.n_col_tiles == 0)

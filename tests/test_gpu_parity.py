@@ -484,7 +484,8 @@ SEG_TUNINGS = [dict(split=0, row_seg=0), dict(split=0, row_seg=16, rows_band=3, 
                dict(split=0, row_seg=32, rows_band=16, threads=256, persist=0),
                dict(split=0, row_seg=16, rows_band=1, threads=512, cols_panel=8, cols_p=2, persist=2),
                dict(split=0, row_seg=16, rows_band=5, threads=128, persist=3),
-               dict(split=0, row_seg=1), dict(split=0, row_seg=1, col_seg=-1, threads=64)]
+               dict(split=0, row_seg=1), dict(split=0, row_seg=1, col_seg=-1, threads=64),
+               dict(split=1, row_seg=16), dict(split=1, stream=0, row_seg=32, threads=128)]
 
 
 @pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
