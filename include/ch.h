@@ -216,10 +216,14 @@ int ch_launch_phase(ch_handle h, int phase);
  *               warps, W and C move as coalesced row pieces straight between registers
  *               and HBM, and each recurrence is a local pass, a combination of the segment
  *               end states through shared memory and a second pass (no pre-roll, no
- *               panels in shared memory).  Needs ny/S to be a power of two <= 32 (<= 16 for
- *               CH_FP64) for every member.  0 = automatic, per member: S = 32 if the
- *               member fits, else 16 if it fits, else panels or streaming (CH_FP64 split
- *               form: streaming for every member); -1 = panels or streaming.
+ *               panels in shared memory).  Up to 32 segments (16 for CH_FP64) sit in one
+ *               CTA; taller columns (up to 64 / 32 segments) are split over the two CTAs
+ *               of a thread-block cluster, which exchange their segment end states through
+ *               distributed shared memory.  Needs ny/S to be a power of two within those
+ *               limits for every member.  0 = automatic, per member: S = 32 in one CTA,
+ *               else S = 16 in one CTA, else S = 32, else 16 over a CTA pair, else panels
+ *               or streaming (CH_FP64 split form: streaming for every member); -1 = panels
+ *               or streaming.
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
  * size, lines too long for shared memory, a row_seg that some member's nx does not fit).

@@ -139,6 +139,7 @@ static void mat2_mul(const double* a, const double* b, double* c) {
 // companion matrix M = [[p1, p2], [1, 0]]; products of M in FP64.
 void seg_tables(double p1, double p2, int S, int G, chk::SegTable* t) {
   std::memset(t, 0, sizeof *t);
+  if (G > 64) G = 64;  // callers keep G <= 64 (B holds 64 segment powers)
   const double M[4] = {p1, p2, 1.0, 0.0};
   double MS[4] = {1.0, 0.0, 0.0, 1.0};
   for (int k = 0; k < S; ++k) mat2_mul(M, MS, MS);
@@ -160,7 +161,7 @@ void seg_tables(double p1, double p2, int S, int G, chk::SegTable* t) {
   t->P[2] = -c / det;
   t->P[3] = a / det;
   for (int i = 0; i < 20; ++i) (&t->Af[0][0])[i] = (float)(&t->A[0][0])[i];
-  for (int i = 0; i < 128; ++i) (&t->Bf[0][0])[i] = (float)(&t->B[0][0])[i];
+  for (int i = 0; i < 256; ++i) (&t->Bf[0][0])[i] = (float)(&t->B[0][0])[i];
   for (int i = 0; i < 4; ++i) t->Pf[i] = (float)t->P[i];
 }
 
@@ -338,9 +339,13 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   auto row_fits = [&](const MemberParams& p, int S) {
     return p.nx % S == 0 && is_pow2_upto32(p.nx / S) && (p.nx * (int)h->elt) % 16 == 0;
   };
+  // segment columns: ny / S segments in one CTA (at most max_wp warps) or over a pair of
+  // CTAs of a cluster (at most 2 max_wp)
   auto col_fits = [&](const MemberParams& p, int S) {
-    return p.ny % S == 0 && is_pow2_upto32(p.ny / S) && p.ny / S <= max_wp;
+    const int wp = p.ny / S;
+    return p.ny % S == 0 && wp >= 1 && (wp & (wp - 1)) == 0 && wp <= 2 * max_wp;
   };
+  auto col_pair = [&](const MemberParams& p, int S) { return p.ny / S > max_wp; };
   // transposed-block rows: nx = 32 nw, nw <= 16
   auto rowT_fits = [&](const MemberParams& p) { return p.nx % 32 == 0 && p.nx / 32 <= 16; };
   auto row_class = [&](const MemberParams& p) {  // 1: transposed-block, 16 / 32: segment, 0: chunked
@@ -360,9 +365,14 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   auto col_class = [&](const MemberParams& p) {
     if (t.col_seg < 0 || (t.col_seg == 0 && f64 && split)) return 0;
     if (t.col_seg > 0) return t.col_seg;
-    return col_fits(p, 32) ? 32 : col_fits(p, 16) ? 16 : 0;
+    for (int pass = 0; pass < 2; ++pass)  // one CTA per panel first, then CTA pairs
+      for (int S : {32, 16})
+        if (col_fits(p, S) && col_pair(p, S) == (pass == 1)) return S;
+    return 0;
   };
-  int cwarps[2] = {8, 8};  // warps per CTA of the segment column kernel, S = 16 / 32
+  // class index of a segment-form member's columns: S = 16, 32 in one CTA, then over pairs
+  auto col_index = [&](const MemberParams& p, int S) { return (S == 32 ? 1 : 0) + (col_pair(p, S) ? 2 : 0); };
+  int cwarps[4] = {8, 8, max_wp, max_wp};  // warps per CTA of each class
   for (int k = 0; k < h->m; ++k) {
     if (!h->has(k)) continue;
     const MemberParams& p = h->hp[k];
@@ -371,12 +381,12 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     if (t.row_seg > 1 && !row_fits(p, t.row_seg))
       return fail(CH_EINVAL, "row_seg: some member's nx is not S times a power of two <= 32");
     if (t.col_seg > 0 && !col_fits(p, t.col_seg))
-      return fail(CH_EINVAL, "col_seg: some member's ny is not S times a power of two <= 32 (<= 16 for FP64)");
+      return fail(CH_EINVAL, "col_seg: some member's ny is not S times a power of two <= 64 (<= 32 for FP64)");
     const int cc = col_class(p);
-    if (cc) cwarps[cc == 32] = std::max(cwarps[cc == 32], p.ny / cc);
+    if (cc && !col_pair(p, cc)) cwarps[col_index(p, cc)] = std::max(cwarps[col_index(p, cc)], p.ny / cc);
   }
 
-  std::vector<Tile> rts[3], csts[2], sts[3], ct;  // rows: S = 16, S = 32, chunked; columns: S = 16, 32
+  std::vector<Tile> rts[3], csts[4], sts[3], ct;  // rows: S = 16, S = 32, chunked; columns: 4 classes
   std::vector<Tile> rtT[17];                   // rows, transposed-block form, by nw
   chk::LaunchShape sh{};
   sh.split = split;
@@ -447,11 +457,11 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       }
     }
     if (cc) {
-      const int wp = p.ny / cc, width = 32 * (cwarps[cc == 32] / wp);
+      const int ci = col_index(p, cc), wp = p.ny / cc;
+      const int width = ci >= 2 ? 32 : 32 * (cwarps[ci] / wp);  // pairs: one 32-column panel
       seg_tables(p.p1y, p.p2y, cc, wp, &h->hsegy[k]);
       int q = 0;
-      for (int i0 = 0; i0 < p.nx; i0 += width, ++q)
-        csts[cc == 32].push_back(Tile{k, i0, std::min(width, p.nx - i0), q});
+      for (int i0 = 0; i0 < p.nx; i0 += width, ++q) csts[ci].push_back(Tile{k, i0, std::min(width, p.nx - i0), q});
     } else {
       int q = 0;
       for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
@@ -486,7 +496,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       sh.seg_grid[c] = std::max(1, sms * std::max(1, per_sm));
     }
   }
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < 4; ++c) {
     sh.cst_n[c] = (int)csts[c].size();
     sh.colseg_threads[c] = 32 * cwarps[c];
     sh.colseg_smem[c] = (size_t)2 * 2 * 32 * cwarps[c] * h->elt;
@@ -499,7 +509,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     rt.insert(rt.end(), rtT[nw].begin(), rtT[nw].end());
   }
   for (int c = 0; c < 3; ++c) rt.insert(rt.end(), rts[c].begin(), rts[c].end());
-  for (int c = 0; c < 2; ++c) cst.insert(cst.end(), csts[c].begin(), csts[c].end());
+  for (int c = 0; c < 4; ++c) cst.insert(cst.end(), csts[c].begin(), csts[c].end());
   sh.n_row_tiles = (int)rt.size();
   sh.n_sweep_tiles = (int)st.size();
   sh.n_col_tiles = (int)ct.size();
@@ -1172,7 +1182,7 @@ int ch_seg_tables(double s, int seg, int groups, double* out) {
   chk::SegTable t;
   seg_tables(q1, q2, seg, groups, &t);
   std::memcpy(out, &t.A[0][0], sizeof t.A);
-  std::memcpy(out + 20, &t.B[0][0], sizeof t.B);
+  std::memcpy(out + 20, &t.B[0][0], 32 * 4 * sizeof(double));  // groups <= 32
   std::memcpy(out + 148, t.P, sizeof t.P);
   return CH_OK;
 }

@@ -55,15 +55,15 @@ struct MemberParams {
 };
 
 // Scan tables of the segment form of the row sweep (S points per lane, G lanes per row),
-// for the companion matrix M = [[p1x, p2x], [1, 0]] of the x recurrence, 2x2 row-major:
+// for the companion matrix M = [[p1, p2], [1, 0]] of the recurrence, 2x2 row-major:
 // A[d] = M^(S 2^d) (scan steps), B[l] = M^(S l) (start state of lane l from the periodic
 // start state), P = (I - M^nx)^-1 (periodic start state from the scan total).
 struct SegTable {
   double A[5][4];
-  double B[32][4];
+  double B[64][4];       // up to 64 segments: columns over a CTA pair (rows use at most 32)
   double P[4];
   float Af[5][4];        // the same rounded to FP32
-  float Bf[32][4];
+  float Bf[64][4];
   float Pf[4];
 };
 
@@ -128,10 +128,11 @@ struct LaunchShape {
   int seg_grid[2];       // CTAs of the persistent segment row kernel
   int seg_ccap[2], seg_mcap[2];  // elements of one C tile buffer / of the mu tile (max over the class)
   size_t seg_smem[2];    // dynamic shared memory of the segment-form row kernel
-  // Column tiles of the segment form: cst_n[0] with S = 16, then cst_n[1] with S = 32.
-  int cst_n[2];
-  int colseg_threads[2];
-  size_t colseg_smem[2];
+  // Column tiles of the segment form: cst_n[0] with S = 16, cst_n[1] with S = 32 (one CTA
+  // per tile), then cst_n[2], cst_n[3] with S = 16, 32 over CTA pairs (tall columns).
+  int cst_n[4];
+  int colseg_threads[4];
+  size_t colseg_smem[4];
 };
 
 // Kernel launchers (ch_kernels.cu).  Each returns the launch status.

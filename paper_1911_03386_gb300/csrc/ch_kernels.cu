@@ -1527,6 +1527,145 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) colseg_kernel(Dev
 }
 
 // -------------------------------------------------------------------------------------
+// Column kernel, segment form over a cluster of two CTAs: columns taller than one CTA's
+// warps can hold (FP64: more than 16 segments of S rows, FP32: more than 32) split their
+// wp = ny / S segments over the pair; each CTA writes its warps' segment end states to its
+// own shared memory and the combination reads the partner's through distributed shared
+// memory (mapa + ld.shared::cluster) after a cluster barrier.  One 32-column panel per pair.
+// -------------------------------------------------------------------------------------
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Shared-memory address of p in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned peer_addr(const void* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ float ld_peer(unsigned addr, float) {
+  float x;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(x) : "r"(addr) : "memory");
+  return x;
+}
+__device__ __forceinline__ double ld_peer(unsigned addr, double) {
+  double x;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(x) : "r"(addr) : "memory");
+  return x;
+}
+
+template <typename T, int S, bool REV>
+__device__ __forceinline__ void colseg2_pass(T (&y)[S], T p1, T p2, const SegTable& tab, T* xs, int warp, int lane,
+                                             int nw, unsigned rank) {
+  const int wp = 2 * nw, wseg = (int)rank * nw + warp;
+  T a = T(0), b = T(0);
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const T t = fma(p1, a, fma(p2, b, y[REV ? S - 1 - k : k]));
+    b = a;
+    a = t;
+  }
+  xs[2 * (warp * 32 + lane)] = a;
+  xs[2 * (warp * 32 + lane) + 1] = b;
+  cluster_sync();
+  const unsigned peer = peer_addr(xs, rank ^ 1u);  // the partner's end-state buffer
+  const T A0 = pick<T>(tab.A[0][0], tab.Af[0][0]), A1 = pick<T>(tab.A[0][1], tab.Af[0][1]);
+  const T A2 = pick<T>(tab.A[0][2], tab.Af[0][2]), A3 = pick<T>(tab.A[0][3], tab.Af[0][3]);
+  const int pos = REV ? wp - 1 - wseg : wseg;
+  T ya = T(0), yb = T(0), pa = T(0), pb = T(0);
+  for (int k = 0; k < wp; ++k) {
+    const int w = REV ? wp - 1 - k : k;  // segment in recurrence order
+    const int ow = w % nw;
+    T ea, eb;
+    if ((unsigned)(w / nw) == rank) {
+      ea = xs[2 * (ow * 32 + lane)];
+      eb = xs[2 * (ow * 32 + lane) + 1];
+    } else {
+      ea = ld_peer(peer + (unsigned)(2 * (ow * 32 + lane)) * (unsigned)sizeof(T), T(0));
+      eb = ld_peer(peer + (unsigned)(2 * (ow * 32 + lane) + 1) * (unsigned)sizeof(T), T(0));
+    }
+    const T na = fma(A0, ya, fma(A1, yb, ea));
+    yb = fma(A2, ya, fma(A3, yb, eb));
+    ya = na;
+    if (k + 1 == pos) {
+      pa = ya;
+      pb = yb;
+    }
+  }
+  const T P0 = pick<T>(tab.P[0], tab.Pf[0]), P1 = pick<T>(tab.P[1], tab.Pf[1]);
+  const T P2 = pick<T>(tab.P[2], tab.Pf[2]), P3 = pick<T>(tab.P[3], tab.Pf[3]);
+  const T xa = fma(P0, ya, P1 * yb), xb = fma(P2, ya, P3 * yb);
+  const T B0 = pick<T>(tab.B[pos][0], tab.Bf[pos][0]), B1 = pick<T>(tab.B[pos][1], tab.Bf[pos][1]);
+  const T B2 = pick<T>(tab.B[pos][2], tab.Bf[pos][2]), B3 = pick<T>(tab.B[pos][3], tab.Bf[pos][3]);
+  a = fma(B0, xa, fma(B1, xb, pa));
+  b = fma(B2, xa, fma(B3, xb, pb));
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const int u = REV ? S - 1 - k : k;
+    const T t = fma(p1, a, fma(p2, b, y[u]));
+    y[u] = t;
+    b = a;
+    a = t;
+  }
+}
+
+template <typename T, int S>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(sizeof(T) == 4 ? 1024 : 512)
+    colseg2_kernel(DevView v, int tile_base) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tile tl = v.colseg_tiles[tile_base + blockIdx.x / 2];  // both CTAs of a pair: one tile
+  MemberState* st = v.ms + tl.member;
+  if (!st->active) return;  // taken by both CTAs of the pair alike
+  const unsigned rank = cluster_rank();
+  const MemberParams& P = v.mp[tl.member];
+  const SegTable& tab = v.segy[tl.member];
+  const int nx = P.nx;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int wseg = (int)rank * nw + warp;
+  const bool cv = lane < tl.count;
+  const int col = tl.start + (cv ? lane : 0);
+  T* xf = reinterpret_cast<T*>(smem);
+  T* xb = xf + 2 * 32 * nw;
+  const T* __restrict__ Wg = static_cast<const T*>(v.W) + P.offset + (int64_t)wseg * S * nx + col;
+  T y[S];
+#pragma unroll
+  for (int u = 0; u < S; ++u) y[u] = cv ? Wg[(int64_t)u * nx] : T(0);
+  const T p1 = pick<T>(P.p1y, P.fp1y), p2 = pick<T>(P.p2y, P.fp2y);
+  colseg2_pass<T, S, false>(y, p1, p2, tab, xf, warp, lane, nw, rank);
+  colseg2_pass<T, S, true>(y, p1, p2, tab, xb, warp, lane, nw, rank);
+  if (cv) {
+    const T kap = pick<T>(P.kappa, P.fkappa);
+    const int64_t base = (int64_t)wseg * S * nx + col;
+    T* __restrict__ Cg = static_cast<T*>(v.C) + P.offset + base;
+    T* const Lg = lo_ptr<T>(v, P, base);
+#pragma unroll
+    for (int u0 = 0; u0 < S; u0 += 4) {
+      T c[4], lo[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = Cg[(int64_t)(u0 + u) * nx];
+        lo[u] = Lg ? Lg[(int64_t)(u0 + u) * nx] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        Cg[(int64_t)(u0 + u) * nx] = c_update<T>(c[u], kap, y[u0 + u], Lg ? &lo[u] : nullptr);
+        if (Lg) Lg[(int64_t)(u0 + u) * nx] = lo[u];
+      }
+    }
+  }
+  if (tl.index == 0 && rank == 0 && threadIdx.x == 0) finalize_sample(v, tl.member, st, P);
+  cluster_sync();  // the partner may still read this CTA's end states
+}
+
+// -------------------------------------------------------------------------------------
 // Streaming sweeps (split form).  Lines are not held on chip: each warp owns 32 lines (one
 // per lane) and streams them, so the number of recurrences in flight per SM is bounded by
 // registers rather than by shared memory.  The intermediate y of the two-pass solve lives
@@ -1770,9 +1909,18 @@ void seg_launch(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
 
 template <typename T>
 void colseg_launch(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
-  if (sh.cst_n[0] > 0) colseg_kernel<T, 16><<<sh.cst_n[0], sh.colseg_threads[0], sh.colseg_smem[0], st>>>(v, 0);
-  if (sh.cst_n[1] > 0)
-    colseg_kernel<T, 32><<<sh.cst_n[1], sh.colseg_threads[1], sh.colseg_smem[1], st>>>(v, sh.cst_n[0]);
+  // column tiles ordered by class: S = 16, S = 32 (one CTA per tile), then S = 16, S = 32
+  // over CTA pairs (two CTAs per tile)
+  int base = 0;
+  if (sh.cst_n[0] > 0) colseg_kernel<T, 16><<<sh.cst_n[0], sh.colseg_threads[0], sh.colseg_smem[0], st>>>(v, base);
+  base += sh.cst_n[0];
+  if (sh.cst_n[1] > 0) colseg_kernel<T, 32><<<sh.cst_n[1], sh.colseg_threads[1], sh.colseg_smem[1], st>>>(v, base);
+  base += sh.cst_n[1];
+  if (sh.cst_n[2] > 0)
+    colseg2_kernel<T, 16><<<2 * sh.cst_n[2], sh.colseg_threads[2], sh.colseg_smem[2], st>>>(v, base);
+  base += sh.cst_n[2];
+  if (sh.cst_n[3] > 0)
+    colseg2_kernel<T, 32><<<2 * sh.cst_n[3], sh.colseg_threads[3], sh.colseg_smem[3], st>>>(v, base);
 }
 
 template <typename T>

@@ -567,17 +567,44 @@ def test_segment_column_selection_and_errors():
     with ch.Ensemble.batch([dict(d, nx=64, ny=64, counter_base=0), dict(d, nx=32, ny=1024, counter_base=4096)],
                            ch.CH_FP32) as e:
         assert e.tuning()["col_seg"] == 32  # 1024 = 32 x 32
+        e.set_tuning(col_seg=16)  # 1024 / 16 = 64 segments: over a CTA pair
+        assert e.tuning()["col_seg"] == 16
+        e.step(2)
         with pytest.raises(ch.ChError) as err:
-            e.set_tuning(col_seg=16)  # 1024 / 16 = 64 segments: too many
+            e.set_tuning(col_seg=8)  # S is 16 or 32
         assert err.value.code == ch.CH_EINVAL
-        assert e.tuning()["col_seg"] == 32
     with ch.Ensemble.batch([dict(d, nx=64, ny=1024, counter_base=0)], ch.CH_FP64) as e:
         assert e.tuning()["col_seg"] == -1  # FP64 default: streaming columns
+        e.set_tuning(split=0)
+        assert e.tuning()["col_seg"] == 32  # 32 segments of doubles: over a CTA pair
         with pytest.raises(ch.ChError):
-            e.set_tuning(col_seg=32)  # 32 segments of doubles: above the FP64 limit of 16
+            e.set_tuning(col_seg=16)  # 64 segments of doubles: above the pair limit of 32
         e.set_tuning(split=1, col_seg=-1)
     with ens(64, 100, [0.0], prec=ch.CH_FP32) as e:
         assert e.tuning()["col_seg"] == -1  # 100 rows: no power of two of segments
+
+
+@pytest.mark.parametrize("prec", [ch.CH_FP64, ch.CH_FP32])
+def test_segment_columns_over_cta_pairs_match_oracle(orc, prec):
+    # columns taller than one CTA holds: FP64 1024 rows (32 segments of 32), FP32 2048 rows
+    # (64 segments), split over the two CTAs of a cluster; a short member beside them
+    ny = 1024 if prec == ch.CH_FP64 else 2048
+    # L = 8 pi (FP64) / 16 pi (FP32) keeps s_y moderate (14 and 3.5) for the FP32 bound
+    d = dict(L=4 * TWO_PI if prec == ch.CH_FP64 else 8 * TWO_PI, gamma=0.005, dt=1e-3, seed=SEED)
+    descs = [dict(d, nx=40, ny=ny, C0=0.2, counter_base=0), dict(d, nx=33, ny=ny, C0=-0.1, counter_base=40 * ny),
+             dict(d, nx=64, ny=64, C0=0.3, counter_base=73 * ny)]
+    nsteps = 6
+    with ch.Ensemble.batch(descs, prec) as e:
+        e.set_tuning(split=0, col_seg=32)
+        e.set_sampling(3, 0.0, capacity=4)
+        e.step(nsteps)
+        for k, dd in enumerate(descs):
+            C0 = orc.initial_field(dd["nx"], dd["ny"], dd["C0"], dd["seed"], dd["counter_base"])
+            ref = orc.run(C0, dd["L"], dd["gamma"], dd["dt"], nsteps, every=3)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            assert err <= (1e-10 if prec == ch.CH_FP64 else 1e-4), (k, err)
+            np.testing.assert_allclose(e.series(k, 4)[:, 1], ref.series[:, 1],
+                                       rtol=1e-11 if prec == ch.CH_FP64 else 1e-5)
 
 
 def test_segment_form_selection_and_errors():
