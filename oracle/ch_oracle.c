@@ -17,9 +17,12 @@
  *     the flux of Eq. (3));
  *   - the coarsening rate beta = -(t/F) dF/dt, Sec. 1 Eq. (6), and its time average
  *     over a window [t1, T], Sec. 3.3 Eq. (42) (the paper's beta_0 estimate,
- *     applied to the CH ensembles in Sec. 4.2, Table 4).
- * The discretisation (Sec. 4.1 says only "semi-implicit ADI finite differences,
- * periodic") is read as the delta-form approximate factorisation
+ *     applied to the CH ensembles in Sec. 4.2, Table 4);
+ *   - statistics of beta across an ensemble: the moments of Sec. 3.3 Eqs. (41a,b) per
+ *     sample time, histograms (the empirical p_beta(b, t) of Sec. 1 Eq. (7)), the window
+ *     mean of mu_1 (Eq. (42)) and the slope k of the least-squares line mu_2 = k t.
+ * The discretisation (Sec. 4.1 names only a semi-implicit ADI finite-difference method
+ * with periodic boundaries) is read as the delta-form approximate factorisation
  *     (I + s D_x^4)(I + s D_y^4)(C^{n+1} - C^n) = dt * lap_h( C^3 - C - gamma lap_h C )^n,
  *     s = gamma*dt,  D^4 = (D^2)^2,  lap_h the 5-point Laplacian,
  * i.e. the nonlinear and cross terms explicit and gamma*lap^2 implicit per direction.
@@ -333,4 +336,120 @@ int or_run(int nx, int ny, double L, double gamma, double dt, double* C, int64_t
   }
   if (nsamples) *nsamples = ns;
   return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Ensemble statistics of beta across the M runs of one ensemble.                   */
+/* beta[j * ld + s] is run j's beta at sample s (j < M, s < T); every run is sampled */
+/* at the same times.  A non-finite value (a diverged run) is left out of sample s's */
+/* statistics, and the count of values used is reported.                             */
+/* ------------------------------------------------------------------------------ */
+
+/*
+ * Moments across the ensemble per sample time, Sec. 3.3 Eqs. (41a,b) (applied to the
+ * Cahn-Hilliard ensembles in Secs. 4.2-4.3):
+ *     mu_1 = (1/M) sum_j beta_j,    mu_p = (1/M) sum_j (beta_j - mu_1)^p,  p = 2, 3, 4,
+ * with M the number of finite values.  out[s * 5 + 0] = that count, out[s * 5 + p] = mu_p
+ * (NaN when the count is 0).
+ */
+void or_beta_moments(int64_t M, int64_t T, int64_t ld, const double* beta, double* out) {
+  for (int64_t s = 0; s < T; ++s) {
+    int64_t count = 0;
+    double sum = 0.0;
+    for (int64_t j = 0; j < M; ++j) {
+      double b = beta[j * ld + s];
+      if (isfinite(b)) {
+        sum += b;
+        count += 1;
+      }
+    }
+    double mu1 = count > 0 ? sum / (double)count : NAN;
+    double c2 = 0.0, c3 = 0.0, c4 = 0.0;
+    for (int64_t j = 0; j < M; ++j) {
+      double b = beta[j * ld + s];
+      if (isfinite(b)) {
+        double d = b - mu1;
+        c2 += d * d;
+        c3 += d * d * d;
+        c4 += d * d * d * d;
+      }
+    }
+    out[s * 5 + 0] = (double)count;
+    out[s * 5 + 1] = mu1;
+    out[s * 5 + 2] = count > 0 ? c2 / (double)count : NAN;
+    out[s * 5 + 3] = count > 0 ? c3 / (double)count : NAN;
+    out[s * 5 + 4] = count > 0 ? c4 / (double)count : NAN;
+  }
+}
+
+/*
+ * Histogram of beta across the ensemble per sample time, the empirical form of
+ * p_beta(b, t), Sec. 1 Eq. (7).  Bin width w = (hi - lo) / nbins; a finite value b < lo
+ * counts in out[s][0]; otherwise k = floor((b - lo) / w) selects out[s][k + 1] when
+ * k < nbins, else out[s][nbins + 1].  Non-finite values are not counted.
+ * out is T x (nbins + 2).  Returns OR_EINVAL unless lo < hi (finite) and nbins >= 1.
+ */
+int or_beta_histogram(int64_t M, int64_t T, int64_t ld, const double* beta, double lo, double hi,
+                      int nbins, int64_t* out) {
+  if (!(isfinite(lo) && isfinite(hi) && lo < hi) || nbins < 1) return OR_EINVAL;
+  double w = (hi - lo) / (double)nbins;
+  for (int64_t s = 0; s < T; ++s) {
+    int64_t* row = out + s * (int64_t)(nbins + 2);
+    for (int k = 0; k < nbins + 2; ++k) row[k] = 0;
+    for (int64_t j = 0; j < M; ++j) {
+      double b = beta[j * ld + s];
+      if (!isfinite(b)) continue;
+      if (b < lo) {
+        row[0] += 1;
+        continue;
+      }
+      double k = floor((b - lo) / w);
+      if (k < (double)nbins)
+        row[(int64_t)k + 1] += 1;
+      else
+        row[nbins + 1] += 1;
+    }
+  }
+  return OR_OK;
+}
+
+/*
+ * Trend statistics of the moment series (t[s], mu1[s], mu2[s]), s < T, t increasing.
+ *   out[0]: the window estimate of beta_0, Sec. 3.3 Eq. (42):
+ *           (1/(t_b - t_a)) * integral of mu_1 over the samples with t1 <= t <= t2,
+ *           the integral by the trapezoid rule between consecutive such samples, t_a and
+ *           t_b the first and last of them (t_b - t_a = t2 - t1 when samples fall on both
+ *           ends of the window); NaN with fewer than two samples in the window.
+ *   out[1]: k of the least-squares fit mu_2 = k t (a line through the origin), Sec. 3.3
+ *           and Sec. 4.2 Table 4, over the samples with tf1 <= t <= tf2:
+ *           k minimises sum (mu_2 - k t)^2, i.e. k = sum(t mu_2) / sum(t^2); NaN when that
+ *           denominator is 0.
+ *   out[2], out[3]: the numbers of samples in the two windows.
+ */
+void or_beta_trend(int64_t T, const double* t, const double* mu1, const double* mu2, double t1,
+                   double t2, double tf1, double tf2, double* out) {
+  double integral = 0.0, ta = 0.0, tb = 0.0;
+  int64_t nw = 0;
+  for (int64_t s = 0; s < T; ++s) {
+    if (t[s] >= t1 && t[s] <= t2) {
+      if (nw == 0) ta = t[s];
+      tb = t[s];
+      nw += 1;
+      if (s + 1 < T && t[s + 1] >= t1 && t[s + 1] <= t2)
+        integral += 0.5 * (t[s + 1] - t[s]) * (mu1[s] + mu1[s + 1]);
+    }
+  }
+  double stm = 0.0, stt = 0.0;
+  int64_t nf = 0;
+  for (int64_t s = 0; s < T; ++s) {
+    if (t[s] >= tf1 && t[s] <= tf2) {
+      stm += t[s] * mu2[s];
+      stt += t[s] * t[s];
+      nf += 1;
+    }
+  }
+  out[0] = nw >= 2 ? integral / (tb - ta) : NAN;
+  out[1] = stt > 0.0 ? stm / stt : NAN;
+  out[2] = (double)nw;
+  out[3] = (double)nf;
 }

@@ -27,6 +27,9 @@ _SIGS = {
     "or_step": (_i, [_i, _i, _d, _d, _d, _dp, _dp]),
     "or_field_observables": (_i, [_i, _i, _d, _d, _dp, _dp, _dp]),
     "or_run": (_i, [_i, _i, _d, _d, _d, _dp, _i64, _i64, _i, _d, _dp, _i64, _i64p, _dp, _i64p]),
+    "or_beta_moments": (None, [_i64, _i64, _i64, _dp, _dp]),
+    "or_beta_histogram": (_i, [_i64, _i64, _i64, _dp, _d, _d, _i, _i64p]),
+    "or_beta_trend": (None, [_i64, _dp, _dp, _dp, _d, _d, _d, _d, _dp]),
 }
 
 
@@ -135,6 +138,38 @@ class Oracle:
         if rc != 0:
             raise ValueError("or_run rc=%d" % rc)
         return RunResult(C, series[: ns.value].copy(), bsum.value, bcnt.value)
+
+    # ---- ensemble statistics of beta (Sec. 3.3 Eqs. (41a,b), (42); Sec. 1 Eq. (7)) ----
+    def beta_moments(self, beta):
+        """beta: (M, T) array, run j's beta at sample s.  Returns (T, 5): count of finite
+        values, mu_1, mu_2, mu_3, mu_4 per sample."""
+        beta = np.ascontiguousarray(beta, dtype=np.float64)
+        M, T = beta.shape
+        out = np.zeros((T, 5))
+        if T > 0:
+            self._L.or_beta_moments(M, T, T, _ptr(beta), _ptr(out))
+        return out
+
+    def beta_histogram(self, beta, lo, hi, nbins):
+        """Counts (T, nbins + 2): below lo, nbins bins of width (hi - lo) / nbins, at or above hi."""
+        beta = np.ascontiguousarray(beta, dtype=np.float64)
+        M, T = beta.shape
+        out = np.zeros((T, nbins + 2), dtype=np.int64)
+        rc = self._L.or_beta_histogram(M, T, T, _ptr(beta), lo, hi, nbins, out.ctypes.data_as(_i64p))
+        if rc != 0:
+            raise ValueError("or_beta_histogram rc=%d" % rc)
+        return out
+
+    def beta_trend(self, t, mu1, mu2, t1, t2, tf1, tf2):
+        """(window mean of mu_1 over [t1, t2], k of mu_2 = k t over [tf1, tf2], samples in
+        each window)."""
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        mu1 = np.ascontiguousarray(mu1, dtype=np.float64)
+        mu2 = np.ascontiguousarray(mu2, dtype=np.float64)
+        assert t.shape == mu1.shape == mu2.shape
+        out = np.zeros(4)
+        self._L.or_beta_trend(t.size, _ptr(t), _ptr(mu1), _ptr(mu2), t1, t2, tf1, tf2, _ptr(out))
+        return out[0], out[1], int(out[2]), int(out[3])
 
 
 _default = None

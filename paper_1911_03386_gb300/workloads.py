@@ -65,3 +65,21 @@ def random_field(ny, nx, seed, amplitude=0.1, mean=0.0):
     """A seeded i.i.d. uniform test field (numpy generator), for tests that set fields."""
     rng = np.random.default_rng(seed)
     return mean + amplitude * (2.0 * rng.random((ny, nx)) - 1.0)
+
+
+def beta_ensemble(members, samples, seed=BASE_SEED, t_end=100.0, beta0=0.28, k=0.0056, diverged=0):
+    """A seeded synthetic ensemble of beta series with the structure the paper reports
+    (Secs. 3.3, 4.2): every run fluctuates about a common beta0, the spread grows like
+    sqrt(k t) and the law has a positive tail.  Returns (t, beta): t of shape (samples,)
+    from 0 to t_end, beta of shape (members, samples).  The last `diverged` runs turn NaN
+    half way (runs whose F or dF/dt stopped being finite).  Inputs for the statistics
+    tests; a stand-in for the paper's runs, not a model of them."""
+    rng = np.random.default_rng(seed)
+    t = np.linspace(0.0, t_end, samples)
+    g = rng.standard_normal((members, samples))
+    e = rng.exponential(size=(members, samples))
+    z = (g + 0.5 * (e - 1.0)) / math.sqrt(1.25)
+    beta = beta0 + np.sqrt(k * t)[None, :] * z
+    if diverged:
+        beta[members - diverged:, samples // 2:] = np.nan
+    return t, beta

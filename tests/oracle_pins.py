@@ -310,6 +310,126 @@ def pin_run_sampling(orc):
     assert abs(res.beta_sum - sum(betas_in_window)) <= 1e-14 * abs(res.beta_sum)
 
 
+# ------------------------------------------------------------------------------------------
+# Ensemble statistics of beta (Sec. 3.3 Eqs. (41a,b), (42); Sec. 1 Eq. (7))
+# ------------------------------------------------------------------------------------------
+def pin_moments_discrete_uniform(orc):
+    """Values 1..M: mean (M+1)/2, central moments (M^2-1)/12, 0, (M^2-1)(3M^2-7)/240;
+    an affine map a x + c maps mu_1 to a mu_1 + c and mu_p to a^p mu_p."""
+    M = 11
+    x = np.arange(1, M + 1, dtype=np.float64)
+    a, c = -2.0, 0.5
+    beta = np.stack([x, a * x + c, x[::-1]], axis=1)  # (M, 3): member j, sample s
+    m = orc.beta_moments(beta)
+    mu1, mu2, mu3, mu4 = (M + 1) / 2.0, (M * M - 1) / 12.0, 0.0, (M * M - 1) * (3.0 * M * M - 7.0) / 240.0
+    for s, (scale, shift) in enumerate([(1.0, 0.0), (a, c), (1.0, 0.0)]):
+        assert m[s, 0] == M
+        assert abs(m[s, 1] - (scale * mu1 + shift)) <= 1e-14 * abs(scale * mu1 + shift)
+        assert abs(m[s, 2] - scale ** 2 * mu2) <= 1e-13 * scale ** 2 * mu2
+        assert abs(m[s, 3] - scale ** 3 * mu3) <= 1e-12 * abs(scale) ** 3 * mu2 ** 1.5
+        assert abs(m[s, 4] - scale ** 4 * mu4) <= 1e-13 * scale ** 4 * mu4
+
+
+def pin_moments_two_point(orc):
+    """A two-point law (value c with weight 1-p, c+d with weight p) has central moments
+    p(1-p) d^2, p(1-p)(1-2p) d^3, p(1-p)(1-3p+3p^2) d^4 (the skew's sign follows p < 1/2)."""
+    c, d = 0.25, 2.0
+    for ones, zeros in [(1, 3), (3, 1), (2, 6)]:
+        col = np.array([c + d] * ones + [c] * zeros)
+        p = ones / float(ones + zeros)
+        m = orc.beta_moments(col[:, None])
+        q = p * (1.0 - p)
+        want = [ones + zeros, c + p * d, q * d ** 2, q * (1.0 - 2.0 * p) * d ** 3,
+                q * (1.0 - 3.0 * p + 3.0 * p * p) * d ** 4]
+        for k in range(5):
+            assert abs(m[0, k] - want[k]) <= 1e-14 * max(1.0, abs(want[k])), (ones, zeros, k, m[0], want)
+
+
+def pin_moments_library_with_nonfinite(orc):
+    """Random ensembles against scipy.stats.moment (central moments, 1/M normalisation) on
+    the finite values; NaN and infinite entries (diverged runs) are left out and counted."""
+    from scipy import stats
+    rng = np.random.default_rng(7)
+    M, T = 37, 9
+    beta = 0.3 + rng.standard_normal((M, T)) * np.linspace(0.01, 0.2, T) + 0.05 * rng.exponential(size=(M, T))
+    beta[3, 2] = np.nan
+    beta[5, 2] = np.inf
+    beta[:, 7] = np.nan  # every run diverged at this sample
+    m = orc.beta_moments(beta)
+    for s in range(T):
+        v = beta[:, s][np.isfinite(beta[:, s])]
+        assert m[s, 0] == v.size
+        if v.size == 0:
+            assert np.all(np.isnan(m[s, 1:]))
+            continue
+        assert abs(m[s, 1] - v.mean()) <= 1e-14
+        for p in (2, 3, 4):
+            want = float(stats.moment(v, moment=p))
+            assert abs(m[s, p] - want) <= 1e-12 * np.mean(np.abs(v - v.mean()) ** p) + 1e-300, (s, p)
+
+
+def pin_histogram_brute_force(orc):
+    """Bins of dyadic width (edges exact in binary) against comparison with the edges:
+    value b falls in bin k when lo + k w <= b < lo + (k+1) w; b < lo and b >= hi in the
+    two outer counters; values on an edge go to the bin above; non-finite ones nowhere."""
+    lo, hi, nb = -0.5, 1.5, 16
+    w = (hi - lo) / nb
+    rng = np.random.default_rng(3)
+    M, T = 53, 4
+    beta = rng.uniform(-1.0, 2.0, size=(M, T))
+    edges = lo + w * np.arange(nb + 1)
+    beta[:8, 0] = edges[:8]          # exactly on lower edges
+    beta[8, 0] = hi                  # exactly at hi: overflow
+    beta[9, 0] = lo                  # exactly at lo: first bin
+    beta[10:14, 1] = edges[1:5] + 0.5 * w   # bin centres
+    beta[14, 1] = np.nan
+    beta[15, 1] = -np.inf
+    beta[16, 1] = np.inf
+    h = orc.beta_histogram(beta, lo, hi, nb)
+    assert h.shape == (T, nb + 2)
+    for s in range(T):
+        want = np.zeros(nb + 2, dtype=np.int64)
+        for b in beta[:, s]:
+            if not np.isfinite(b):
+                continue
+            if b < lo:
+                want[0] += 1
+            elif b >= hi:
+                want[nb + 1] += 1
+            else:
+                k = [i for i in range(nb) if edges[i] <= b < edges[i + 1]]
+                assert len(k) == 1
+                want[k[0] + 1] += 1
+        assert np.array_equal(h[s], want), (s, h[s], want)
+    assert h[1].sum() == M - 3
+
+
+def pin_trend_closed_forms(orc):
+    """Trapezoid window mean: exact for mu_1 linear in t; for mu_1 = t^2 on a uniform grid
+    of step h it exceeds the exact mean (t1^2 + t1 t2 + t2^2)/3 by h^2/6; the mean of a
+    constant is that constant also when the window extends beyond the samples.  Least
+    squares through the origin: k = 0.3 for mu_2 = 0.3 t; k = 3n(n+1)/(2(2n+1)) for
+    mu_2 = t^2 on t = 1..n (sum t^3 / sum t^2)."""
+    h = 0.25
+    t = np.arange(0, 41) * h            # 0 .. 10
+    t1, t2 = 2.0, 7.0
+    mean_lin, _, nw, _ = orc.beta_trend(t, 0.2 + 0.05 * t, 0 * t, t1, t2, 0.0, 10.0)
+    assert nw == 21
+    assert abs(mean_lin - (0.2 + 0.05 * (t1 + t2) / 2.0)) <= 1e-15
+    mean_sq, _, _, _ = orc.beta_trend(t, t * t, 0 * t, t1, t2, 0.0, 10.0)
+    assert abs(mean_sq - ((t1 * t1 + t1 * t2 + t2 * t2) / 3.0 + h * h / 6.0)) <= 1e-13
+    mean_c, _, nw, _ = orc.beta_trend(t, np.full_like(t, 0.28), 0 * t, -3.0, 2.1, 0.0, 10.0)
+    assert nw == 9 and mean_c == 0.28
+    _, k, _, nf = orc.beta_trend(t, 0 * t, 0.3 * t, t1, t2, 2.0, 7.0)
+    assert nf == 21 and abs(k - 0.3) <= 1e-15
+    n = 40
+    tt = np.arange(1, n + 1, dtype=np.float64)
+    _, k, _, nf = orc.beta_trend(tt, 0 * tt, tt * tt, 0.0, 1.0, 1.0, float(n))
+    assert nf == n and abs(k - 3.0 * n * (n + 1) / (2.0 * (2 * n + 1))) <= 1e-13 * k
+    mean_none, k_none, nw, nf = orc.beta_trend(t, t, t, 20.0, 30.0, 20.0, 30.0)
+    assert nw == 0 and nf == 0 and np.isnan(mean_none) and np.isnan(k_none)
+
+
 ALL_PINS = [
     pin_splitmix_golden,
     pin_uniform_exact,
@@ -330,4 +450,9 @@ ALL_PINS = [
     pin_single_mode_energy,
     pin_interface_energy,
     pin_run_sampling,
+    pin_moments_discrete_uniform,
+    pin_moments_two_point,
+    pin_moments_library_with_nonfinite,
+    pin_histogram_brute_force,
+    pin_trend_closed_forms,
 ]

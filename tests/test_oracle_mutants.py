@@ -44,6 +44,19 @@ MUTANTS = {
     "mix_constant": ("0xbf58476d1ce4e5b9ULL", "0xbf58476d1ce4e5b8ULL"),
     "uniform_bits": ("or_splitmix64(seed, k) >> 11", "or_splitmix64(seed, k) >> 12"),
     "sample_after_update": ("int take = (n % every) == 0;", "int take = ((n + 1) % every) == 0;"),
+    "moment_raw": ("double d = b - mu1;", "double d = b;"),
+    "moment_unbiased": ("c2 / (double)count : NAN;", "c2 / (double)(count - 1) : NAN;"),
+    "mu3_sign": ("c3 += d * d * d;", "c3 -= d * d * d;"),
+    "mu4_power": ("c4 += d * d * d * d;", "c4 += d * d * d;"),
+    "moment_counts_inf": ("if (isfinite(b)) {\n        sum += b;", "if (!isnan(b)) {\n        sum += b;"),
+    "hist_counts_inf": ("if (!isfinite(b)) continue;", "if (isnan(b)) continue;"),
+    "hist_lower_edge": ("if (b < lo) {", "if (b <= lo) {"),
+    "hist_round": ("double k = floor((b - lo) / w);", "double k = round((b - lo) / w);"),
+    "trend_rectangle": ("integral += 0.5 * (t[s + 1] - t[s]) * (mu1[s] + mu1[s + 1]);",
+                        "integral += (t[s + 1] - t[s]) * mu1[s];"),
+    "trend_span": ("integral / (tb - ta)", "integral / (t2 - t1)"),
+    "fit_drops_t": ("stm += t[s] * mu2[s];", "stm += mu2[s];"),
+    "fit_window_strict": ("if (t[s] >= tf1 && t[s] <= tf2) {", "if (t[s] > tf1 && t[s] <= tf2) {"),
 }
 
 
