@@ -16,6 +16,8 @@ Reported:
                  device-to-host read of F, dF/dt, beta (ch_observables).
   fp32           the FP32 form on the same workload (throughput, <beta> against FP64).
   roofline       the dominant kernel against its bound (FP64 pipe for the FP64 path).
+  ensemble_stats moments, histograms and trend statistics of beta across runs: kernel
+                 times on a paper-size synthetic ensemble and the workload's own values.
   cpu_baseline   the FP64 CPU oracle timed on this host's cores (bounded sample).
   --impl reference  times the oracle alone (the reference arm), same metric and config.
 """
@@ -299,6 +301,77 @@ def run_descs_leg(ch, torch, descs, prec, nsteps, every, t1, warm=300, tuning=No
     return out
 
 
+def run_stats_leg(ch, torch, p, prec, nsteps=2000, every=10):
+    """Ensemble statistics of beta (Sec. 3.3 Eqs. (41a,b), (42); Sec. 1 Eq. (7)).
+    (a) The statistics kernels timed with CUDA events on a synthetic beta ensemble of the
+        paper's Sec. 4.2 size (1024 runs; 32768 sample times, about t = 100 at dt = 0.0012
+        sampled every 2-3 steps): 256 MiB of beta, above the L2.
+    (b) The statistics of the workload's own ensemble over its first nsteps time steps,
+        sampled every `every` steps, per initial mean C0: mu_1 and mu_2 at the last sample,
+        the window mean of mu_1 over the second half and k of mu_2 = k t."""
+    import numpy as np
+    from paper_1911_03386_gb300 import workloads as wl
+    M, T, nb = 1024, 32768, 100
+    t, beta = wl.beta_ensemble(M, T, seed=wl.BASE_SEED + 77, t_end=100.0, diverged=8)
+    tb = torch.from_numpy(t).cuda()
+    bb = torch.from_numpy(beta).cuda()
+    mom = torch.empty((T, ch.CH_MOMENTS), dtype=torch.float64, device="cuda")
+    hist = torch.empty((T, nb + 2), dtype=torch.int64, device="cuda")
+    tr = torch.empty(4, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    calls = {
+        "moments": lambda: ch.ch_stats_moments(tb.data_ptr(), bb.data_ptr(), M, T, T, mom.data_ptr(), st.cuda_stream),
+        "histogram": lambda: ch.ch_stats_histogram(bb.data_ptr(), M, T, T, 0.0, 0.6, nb, hist.data_ptr(),
+                                                   st.cuda_stream),
+        "trend": lambda: ch.ch_stats_trend(mom.data_ptr(), T, 20.0, 100.0, 20.0, 100.0, tr.data_ptr(), st.cuda_stream),
+    }
+    dense = {"members": M, "samples": T, "bins": nb, "beta_bytes": M * T * 8}
+    for name, fn in calls.items():
+        for _ in range(3):
+            fn()
+        reps = 10
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        dense[name + "_ms"] = ms
+        if name != "trend":
+            # algorithmic bytes: beta read once (plus t and the output rows)
+            byts = M * T * 8 + (T * 8 * (1 + ch.CH_MOMENTS) if name == "moments" else T * (nb + 2) * 8)
+            dense[name + "_gbs"] = byts / (ms * 1e-3) / 1e9
+            dense[name + "_frac_of_measured_hbm"] = byts / (ms * 1e-3) / HBM_PEAK
+    tv = tr.cpu().numpy()
+    dense["synthetic_beta0_window_20_100"] = float(tv[0])
+    dense["synthetic_k_fit_20_100"] = float(tv[1])
+    dense["synthetic_law"] = "beta0 = 0.28, mu_2 = 0.0056 t (the generator's parameters)"
+    del tb, bb, mom, hist
+
+    descs = [dict(nx=p["nx"], ny=p["ny"], L=p["L"], gamma=p["gamma"], dt=p["dt"], C0=c0, seed=wl.BASE_SEED,
+                  counter_base=k * p["nx"] * p["ny"]) for k, c0 in enumerate(p["C0"])]
+    own = {"time_steps": nsteps, "sample_every": every}
+    with ch.Ensemble.batch(descs, prec) as e:
+        e.set_sampling(every, 0.0, nsteps // every + 1)
+        e.step(nsteps)
+        e.synchronize()
+        t_end = nsteps * p["dt"]
+        for c0 in sorted(set(p["C0"])):
+            members = [k for k, c in enumerate(p["C0"]) if c == c0]
+            t0 = time.perf_counter()
+            m = e.moments(members=members)
+            wall = time.perf_counter() - t0
+            b0, k, nw, nf = e.trend(0.5 * t_end, t_end, 0.0, t_end, members=members)
+            own["C0=%g" % c0] = {"members": len(members), "samples": int(m.shape[0]), "mu1_last": float(m[-1, 2]),
+                                 "mu2_last": float(m[-1, 3]), "mu3_last": float(m[-1, 4]),
+                                 "mu4_last": float(m[-1, 5]),
+                                 "beta0_window": float(b0), "window": [0.5 * t_end, t_end], "k_fit": float(k),
+                                 "fit_window": [0.0, t_end], "moments_call_wall_ms": 1e3 * wall}
+    return {"dense_synthetic": dense, "workload_ensemble": own}
+
+
 def run_e2e_leg(ch, torch, p, prec, K, rank, dist):
     """End to end through the C ABI with host buffers (see module docstring)."""
     import numpy as np
@@ -391,6 +464,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=120)
     ap.add_argument("--no-batches", action="store_true", help="skip the uneven-batch and 1024^2 legs")
+    ap.add_argument("--no-stats", action="store_true", help="skip the ensemble-statistics leg")
     ap.add_argument("--long-beta", action="store_true",
                     help="also run the 32 x 1024^2 coarsening ensemble over its whole horizon in both precisions "
                          "and compare <beta> (minutes of GPU time)")
@@ -525,6 +599,10 @@ def main():
                                      <= long["fp64"]["beta_avg"][k]["se"] for k in long["fp64"]["beta_avg"]}
             batches[lb["name"] + "/whole-horizon"] = long
 
+    stats = None
+    if not args.no_stats and rank == 0:
+        stats = run_stats_leg(ch, torch, p, ch.CH_FP64)
+
     from paper_1911_03386_gb300 import replicas
     tdist = torch.distributed if dist else None
 
@@ -604,7 +682,7 @@ def main():
             "dtype": "f64", "data": "synthetic", "config": workload_config(p, "fp64"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_line,
             "gpu_launches": r64["launches"], "clocks": r64["clocks"], "fp32": fp32,
-            "beta_avg": beta_stats(avg64), "serving": serving, "batches": batches,
+            "beta_avg": beta_stats(avg64), "serving": serving, "batches": batches, "ensemble_stats": stats,
             "kernel_source": kernel_source_hash()}
     print(json.dumps(finite_or_none(line), allow_nan=False), flush=True)
     if dist:

@@ -327,6 +327,71 @@ int ch_step_field_noalloc(double* C, int nx, int ny, double L, double gamma, dou
                           void* stream);
 
 /* ------------------------------------------------------------------------------------ */
+/* Ensemble statistics of beta, computed on the device from sampled series.               */
+/*                                                                                        */
+/* The paper's analysis of an ensemble (Sec. 3.3 Eqs. (41a,b), (42); Secs. 4.2-4.3,        */
+/* Tables 4-5) works on beta_j(t) of M runs sampled at common times.  A value that is not */
+/* finite (a diverged run) is left out of its sample's statistics, and the number of      */
+/* values used is reported.  The dense forms take device arrays and are asynchronous on  */
+/* `stream` (a cudaStream_t, NULL = legacy default stream); the ensemble forms read a     */
+/* handle's series rings and return host arrays.                                          */
+/* ------------------------------------------------------------------------------------ */
+
+#define CH_MOMENTS 6      /* doubles per row of a moments table */
+#define CH_MAX_BINS 1024  /* largest histogram bin count */
+
+/*
+ * Moments across the runs per sample time, Eqs. (41a,b).  beta[j * ld + s] is run j's
+ * beta at sample s (members runs, samples times, ld >= samples), t[s] the sample times
+ * (device arrays).  Row s of out (device, samples x CH_MOMENTS) = t_s, the count c_s of
+ * finite values, mu_1 = (1/c_s) sum beta, and mu_p = (1/c_s) sum (beta - mu_1)^p for
+ * p = 2, 3, 4 (NaN when c_s = 0), all in FP64.  Errors: CH_EINVAL (members < 1,
+ * samples < 0, ld < samples, a NULL array with samples > 0), CH_ECUDA.
+ */
+int ch_stats_moments(const double* t, const double* beta, int64_t members, int64_t samples, int64_t ld,
+                     double* out, void* stream);
+
+/*
+ * Histogram per sample time: the empirical distribution p_beta(b, t) of Sec. 1 Eq. (7).
+ * Row s of out (device, samples x (nbins + 2) counts) = the values below lo, then nbins
+ * bins of width w = (hi - lo) / nbins (value b >= lo goes to bin floor((b - lo) / w),
+ * both operations in FP64 with round-to-nearest division), then the values past the
+ * last bin.  beta as in ch_stats_moments.  Errors: CH_EINVAL (as ch_stats_moments;
+ * lo < hi finite, 1 <= nbins <= CH_MAX_BINS), CH_ECUDA.
+ */
+int ch_stats_histogram(const double* beta, int64_t members, int64_t samples, int64_t ld, double lo, double hi,
+                       int nbins, int64_t* out, void* stream);
+
+/*
+ * Trend statistics of a moments table (device, samples rows, t increasing):
+ *   out[0]  the window estimate of beta_0, Eq. (42): the integral of mu_1 by the trapezoid
+ *           rule between consecutive samples with t1 <= t <= t2, divided by the time
+ *           between the first and the last of them (NaN with fewer than two);
+ *   out[1]  k of the least-squares line mu_2 = k t through the origin (Sec. 3.3, Sec. 4.2
+ *           Table 4) over the samples with tf1 <= t <= tf2: sum t mu_2 / sum t^2 (NaN
+ *           when no sample has t != 0);
+ *   out[2], out[3]  the numbers of samples in the two windows.
+ * out: device, 4 doubles.  Errors: CH_EINVAL (samples < 0, NULL arrays), CH_ECUDA.
+ */
+int ch_stats_trend(const double* moments, int64_t samples, double t1, double t2, double tf1, double tf2,
+                   double* out, void* stream);
+
+/*
+ * The same three statistics over a handle's series (ch_set_sampling with capacity > 0)
+ * for the runs members[0 .. count) (host array of member indices; NULL = every member,
+ * count ignored), on the samples that all of them still hold, oldest first.  The runs
+ * must share dt and the sampling period and hold their samples at equal times (checked
+ * on the device); else CH_EINVAL.  out is host memory: cap rows of CH_MOMENTS doubles or
+ * of nbins + 2 counts (*n receives the rows written), or 4 doubles for the trend.
+ * Synchronise the stream.  Errors: CH_EINVAL, CH_ENOMEM, CH_ECUDA.
+ */
+int ch_ensemble_moments(ch_handle h, const int* members, int count, double* out, int64_t cap, int64_t* n);
+int ch_ensemble_histogram(ch_handle h, const int* members, int count, double lo, double hi, int nbins,
+                          int64_t* out, int64_t cap, int64_t* n);
+int ch_ensemble_trend(ch_handle h, const int* members, int count, double t1, double t2, double tf1, double tf2,
+                      double* out);
+
+/* ------------------------------------------------------------------------------------ */
 /* Serving: a stream of single-run requests with continuous batching.                    */
 /*                                                                                        */
 /* The paper (Sec. 4.1) ran its ensembles as M separate processes sharing the GPUs        */

@@ -19,6 +19,8 @@ __all__ = [
     "ch_set_field", "ch_set_fields", "ch_get_fields", "ch_launch_phase", "ch_set_tuning", "ch_get_tuning", "Tuning",
     "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
     "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_seg_tables", "ch_step_field_noalloc", "ch_last_error", "ch_version",
+    "CH_MOMENTS", "CH_MAX_BINS", "ch_stats_moments", "ch_stats_histogram", "ch_stats_trend", "ch_ensemble_moments",
+    "ch_ensemble_histogram", "ch_ensemble_trend",
     "Ensemble", "Server", "Request", "Result", "ServerStats", "ch_server_create", "ch_submit", "ch_poll",
     "ch_server_wait", "ch_server_stats", "ch_server_destroy",
 ]
@@ -26,6 +28,7 @@ __all__ = [
 CH_OK, CH_PENDING = 0, 1
 CH_EINVAL, CH_ENOMEM, CH_ECUDA, CH_ENONFINITE, CH_ETIMEOUT, CH_EBUSY, CH_ENOTFOUND = -1, -2, -3, -4, -5, -6, -7
 CH_FP64, CH_FP32 = 0, 1
+CH_MOMENTS, CH_MAX_BINS = 6, 1024
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "_build", "libch.so")
@@ -118,6 +121,12 @@ _SIGS = {
     "ch_penta_factor": (_c_int, [_c_dbl, _c_int, _dp, _dp, _dp, _ip]),
     "ch_seg_tables": (_c_int, [_c_dbl, _c_int, _c_int, _dp]),
     "ch_step_field_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
+    "ch_stats_moments": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _vp, _vp]),
+    "ch_stats_histogram": (_c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_dbl, _c_dbl, _c_int, _vp, _vp]),
+    "ch_stats_trend": (_c_int, [_vp, _c_i64, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _vp, _vp]),
+    "ch_ensemble_moments": (_c_int, [_vp, _ip, _c_int, _dp, _c_i64, _i64p]),
+    "ch_ensemble_histogram": (_c_int, [_vp, _ip, _c_int, _c_dbl, _c_dbl, _c_int, _i64p, _c_i64, _i64p]),
+    "ch_ensemble_trend": (_c_int, [_vp, _ip, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _dp]),
     "ch_server_create": (_c_int, [ctypes.c_size_t, _c_int, _c_int, ctypes.POINTER(_vp)]),
     "ch_submit": (_c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "ch_poll": (_c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result)]),
@@ -261,6 +270,56 @@ def ch_series(h, member, cap):
     n = ctypes.c_int64()
     _check(lib().ch_series(h, member, _ptr(out), cap, ctypes.byref(n)))
     return out[: n.value].copy()
+
+
+# ---- ensemble statistics of beta (dense forms: device pointers as ints) ----
+def ch_stats_moments(t_ptr, beta_ptr, members, samples, ld, out_ptr, stream_ptr=None):
+    _check(lib().ch_stats_moments(t_ptr, beta_ptr, members, samples, ld, out_ptr, stream_ptr))
+
+
+def ch_stats_histogram(beta_ptr, members, samples, ld, lo, hi, nbins, out_ptr, stream_ptr=None):
+    _check(lib().ch_stats_histogram(beta_ptr, members, samples, ld, lo, hi, nbins, out_ptr, stream_ptr))
+
+
+def ch_stats_trend(moments_ptr, samples, t1, t2, tf1, tf2, out_ptr, stream_ptr=None):
+    _check(lib().ch_stats_trend(moments_ptr, samples, t1, t2, tf1, tf2, out_ptr, stream_ptr))
+
+
+def _member_list(members):
+    if members is None:
+        return None, 0, None
+    arr = np.ascontiguousarray(members, dtype=np.int32)
+    return arr.ctypes.data_as(_ip), arr.size, arr
+
+
+def ch_ensemble_moments(h, members=None, cap=None):
+    """(T, CH_MOMENTS) table: t, count, mu_1 .. mu_4 per sample time."""
+    mp, cnt, keep = _member_list(members)
+    if cap is None:
+        cap = 1 << 20
+    out = np.zeros((max(cap, 1), CH_MOMENTS))
+    n = ctypes.c_int64()
+    _check(lib().ch_ensemble_moments(h, mp, cnt, _ptr(out), cap, ctypes.byref(n)))
+    return out[: n.value].copy()
+
+
+def ch_ensemble_histogram(h, lo, hi, nbins, members=None, cap=None):
+    """(T, nbins + 2) int64 counts: below lo, the bins, past the last bin."""
+    mp, cnt, keep = _member_list(members)
+    if cap is None:
+        cap = 1 << 16
+    out = np.zeros((max(cap, 1), nbins + 2), dtype=np.int64)
+    n = ctypes.c_int64()
+    _check(lib().ch_ensemble_histogram(h, mp, cnt, lo, hi, nbins, out.ctypes.data_as(_i64p), cap, ctypes.byref(n)))
+    return out[: n.value].copy()
+
+
+def ch_ensemble_trend(h, t1, t2, tf1, tf2, members=None):
+    """(window mean of mu_1, k of mu_2 = k t, samples in the window, samples in the fit)."""
+    mp, cnt, keep = _member_list(members)
+    out = np.zeros(4)
+    _check(lib().ch_ensemble_trend(h, mp, cnt, t1, t2, tf1, tf2, _ptr(out)))
+    return out[0], out[1], int(out[2]), int(out[3])
 
 
 def ch_get_field(h, member):
@@ -459,6 +518,15 @@ class Ensemble:
 
     def series(self, member, cap):
         return ch_series(self.h, member, cap)
+
+    def moments(self, members=None, cap=None):
+        return ch_ensemble_moments(self.h, members, cap)
+
+    def histogram(self, lo, hi, nbins, members=None, cap=None):
+        return ch_ensemble_histogram(self.h, lo, hi, nbins, members, cap)
+
+    def trend(self, t1, t2, tf1, tf2, members=None):
+        return ch_ensemble_trend(self.h, t1, t2, tf1, tf2, members)
 
     def field(self, member):
         return ch_get_field(self.h, member)

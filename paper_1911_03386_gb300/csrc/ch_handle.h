@@ -88,6 +88,7 @@ struct ch_ensemble {
 namespace chh {
 
 int fail(int code, const std::string& msg);
+int check_handle(ch_handle h);
 int cuda_fail(cudaError_t e, const char* what);
 bool finite_pos(double x);
 int validate_desc(const ch_member_desc& d, int k);
