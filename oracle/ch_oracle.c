@@ -20,7 +20,8 @@
  *     applied to the CH ensembles in Sec. 4.2, Table 4);
  *   - statistics of beta across an ensemble: the moments of Sec. 3.3 Eqs. (41a,b) per
  *     sample time, histograms (the empirical p_beta(b, t) of Sec. 1 Eq. (7)), the window
- *     mean of mu_1 (Eq. (42)) and the slope k of the least-squares line mu_2 = k t.
+ *     mean of mu_1 (Eq. (42)) and the slope k of the least-squares line mu_2 = k t;
+ *   - the grid-refinement error E_n of Appendix A (2 x 2 restriction, L1 distance).
  * The discretisation (Sec. 4.1 names only a semi-implicit ADI finite-difference method
  * with periodic boundaries) is read as the delta-form approximate factorisation
  *     (I + s D_x^4)(I + s D_y^4)(C^{n+1} - C^n) = dt * lap_h( C^3 - C - gamma lap_h C )^n,
@@ -452,4 +453,32 @@ void or_beta_trend(int64_t T, const double* t, const double* mu1, const double* 
   out[1] = stt > 0.0 ? stm / stt : NAN;
   out[2] = (double)nw;
   out[3] = (double)nf;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Grid-refinement error, Appendix A: the L1 distance between a field on an n-grid   */
+/* and the same run on the n/2-grid, the fine field restricted by averaging 2 x 2    */
+/* blocks.  Grid points are taken at cell centres, so fine points (2i, 2j),          */
+/* (2i+1, 2j), (2i, 2j+1), (2i+1, 2j+1) surround coarse point (i, j) symmetrically.   */
+/* ------------------------------------------------------------------------------ */
+
+/*
+ * E = (1/|Omega|) sum_{i,j} | 1/4 [f(2i,2j) + f(2i+1,2j) + f(2i,2j+1) + f(2i+1,2j+1)]
+ *                             - c(i,j) | dx_c dy_c
+ *   = mean over the coarse points of |restricted fine - coarse|,
+ * fine[j * nx + i] on nx x ny points (both even), coarse[j * (nx/2) + i] on nx/2 x ny/2.
+ * Returns NAN unless nx and ny are even and >= 2.
+ */
+double or_refinement_error(int nx, int ny, const double* fine, const double* coarse) {
+  if (nx < 2 || ny < 2 || nx % 2 || ny % 2) return NAN;
+  int mx = nx / 2, my = ny / 2;
+  double sum = 0.0;
+  for (int j = 0; j < my; ++j) {
+    for (int i = 0; i < mx; ++i) {
+      double r = 0.25 * (fine[(size_t)(2 * j) * nx + 2 * i] + fine[(size_t)(2 * j) * nx + 2 * i + 1] +
+                         fine[(size_t)(2 * j + 1) * nx + 2 * i] + fine[(size_t)(2 * j + 1) * nx + 2 * i + 1]);
+      sum += fabs(r - coarse[(size_t)j * mx + i]);
+    }
+  }
+  return sum / ((double)mx * (double)my);
 }

@@ -30,6 +30,7 @@ _SIGS = {
     "or_beta_moments": (None, [_i64, _i64, _i64, _dp, _dp]),
     "or_beta_histogram": (_i, [_i64, _i64, _i64, _dp, _d, _d, _i, _i64p]),
     "or_beta_trend": (None, [_i64, _dp, _dp, _dp, _d, _d, _d, _d, _dp]),
+    "or_refinement_error": (_d, [_i, _i, _dp, _dp]),
 }
 
 
@@ -170,6 +171,15 @@ class Oracle:
         out = np.zeros(4)
         self._L.or_beta_trend(t.size, _ptr(t), _ptr(mu1), _ptr(mu2), t1, t2, tf1, tf2, _ptr(out))
         return out[0], out[1], int(out[2]), int(out[3])
+
+    # ---- grid-refinement error (Appendix A) ----
+    def refinement_error(self, fine, coarse):
+        """E_n between a (ny, nx) fine field and its (ny/2, nx/2) coarse counterpart."""
+        fine = np.ascontiguousarray(fine, dtype=np.float64)
+        coarse = np.ascontiguousarray(coarse, dtype=np.float64)
+        ny, nx = fine.shape
+        assert coarse.shape == (ny // 2, nx // 2)
+        return float(self._L.or_refinement_error(nx, ny, _ptr(fine), _ptr(coarse)))
 
 
 _default = None

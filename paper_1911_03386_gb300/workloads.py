@@ -83,3 +83,30 @@ def beta_ensemble(members, samples, seed=BASE_SEED, t_end=100.0, beta0=0.28, k=0
     if diverged:
         beta[members - diverged:, samples // 2:] = np.nan
     return t, beta
+
+
+# Appendix A grid-refinement study: [0, 2 pi]^2, gamma = 0.01, final time T = 10,
+# dt = 0.1 dx per grid, a single-droplet start; E_n compares the n-grid with the n/2-grid.
+REFINEMENT = dict(name="appendix-A refinement study", L=TWO_PI, gamma=0.01, T=10.0, cfl=0.1,
+                  sizes=[64, 128, 256, 512, 1024, 2048, 4096, 8192])
+
+
+def droplet_field(n, L=TWO_PI, gamma=0.01):
+    """The single-droplet start of the refinement study on an n x n grid (row-major (y, x)):
+    C = tanh((r - L/2) / sqrt(2 gamma)), r the periodic distance of the cell centre
+    ((i + 1/2) L/n, (j + 1/2) L/n) from the origin.  tanh(d / sqrt(2 gamma)) is the
+    equilibrium profile across a flat interface of the free energy 1/4 (C^2 - 1)^2 +
+    gamma/2 |grad C|^2, so the start is smooth on every grid of the study."""
+    h = L / n
+    x = (np.arange(n) + 0.5) * h
+    d = np.minimum(x, L - x)
+    r = np.sqrt(d[None, :] ** 2 + d[:, None] ** 2)
+    return np.tanh((r - 0.5 * L) / math.sqrt(2.0 * gamma))
+
+
+def refinement_steps(n, preset=REFINEMENT):
+    """(steps, dt) of the n-grid: dt nominally cfl * dx, rounded so that every grid ends
+    exactly at T."""
+    dx = preset["L"] / n
+    steps = max(1, int(round(preset["T"] / (preset["cfl"] * dx))))
+    return steps, preset["T"] / steps

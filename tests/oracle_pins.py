@@ -7,6 +7,7 @@ conservation, energy decay and the continuum interface energy.  The pin tests ru
 on the oracle; the mutation test runs them on deliberately broken builds and requires
 every break to be caught.
 """
+import ctypes
 import math
 import os
 
@@ -430,6 +431,48 @@ def pin_trend_closed_forms(orc):
     assert nw == 0 and nf == 0 and np.isnan(mean_none) and np.isnan(k_none)
 
 
+# ------------------------------------------------------------------------------------------
+# Grid-refinement error (Appendix A)
+# ------------------------------------------------------------------------------------------
+def _cell_centres(n, L):
+    return (np.arange(n) + 0.5) * (L / n)
+
+
+def pin_refinement_prolongation_and_linear(orc):
+    """A fine field that repeats every coarse value over its 2 x 2 block, and a linear
+    function sampled at cell centres (whose 2 x 2 means are its values at the coarse
+    centres), restrict exactly: E = 0 to rounding.  Odd sizes are rejected (NaN)."""
+    rng = np.random.default_rng(5)
+    coarse = rng.standard_normal((9, 14))
+    fine = np.kron(coarse, np.ones((2, 2)))
+    assert orc.refinement_error(fine, coarse) <= 4e-16 * np.max(np.abs(coarse))
+    L = 2.0 * math.pi
+    xf, yf = _cell_centres(28, L), _cell_centres(18, L)
+    xc, yc = _cell_centres(14, L), _cell_centres(9, L)
+    lin = lambda x, y: 0.3 + 0.7 * x[None, :] - 0.2 * y[:, None]
+    assert orc.refinement_error(lin(xf, yf), lin(xc, yc)) <= 1e-14
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert math.isnan(orc._L.or_refinement_error(7, 4, fine.ctypes.data_as(dp), coarse.ctypes.data_as(dp)))
+
+
+def pin_refinement_fourier_mode(orc):
+    """cos(kx) cos(ly) on cell-centred grids: the mean of a 2 x 2 block of the fine samples
+    is the coarse sample times cos(k h_x/2) cos(l h_y/2) (h the fine spacings), so
+    E = (1 - cos(k h_x/2) cos(l h_y/2)) * mean_i |cos(k x_i)| * mean_j |cos(l y_j)| over
+    the coarse points.  A restriction off by one point or a wrong normalisation fails."""
+    L = 2.0 * math.pi
+    for (nx, ny, k, l) in [(24, 16, 3, 2), (40, 40, 5, 1), (12, 20, 1, 4)]:
+        xf, yf = _cell_centres(nx, L), _cell_centres(ny, L)
+        xc, yc = _cell_centres(nx // 2, L), _cell_centres(ny // 2, L)
+        fine = np.cos(l * yf)[:, None] * np.cos(k * xf)[None, :]
+        coarse = np.cos(l * yc)[:, None] * np.cos(k * xc)[None, :]
+        hx, hy = L / nx, L / ny
+        want = (1.0 - math.cos(k * hx / 2) * math.cos(l * hy / 2)) * np.mean(np.abs(np.cos(k * xc))) * \
+            np.mean(np.abs(np.cos(l * yc)))
+        got = orc.refinement_error(fine, coarse)
+        assert abs(got - want) <= 1e-13 * want + 1e-16, (nx, ny, k, l, got, want)
+
+
 ALL_PINS = [
     pin_splitmix_golden,
     pin_uniform_exact,
@@ -455,4 +498,6 @@ ALL_PINS = [
     pin_moments_library_with_nonfinite,
     pin_histogram_brute_force,
     pin_trend_closed_forms,
+    pin_refinement_prolongation_and_linear,
+    pin_refinement_fourier_mode,
 ]

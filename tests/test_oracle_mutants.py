@@ -57,6 +57,11 @@ MUTANTS = {
     "trend_span": ("integral / (tb - ta)", "integral / (t2 - t1)"),
     "fit_drops_t": ("stm += t[s] * mu2[s];", "stm += mu2[s];"),
     "fit_window_strict": ("if (t[s] >= tf1 && t[s] <= tf2) {", "if (t[s] > tf1 && t[s] <= tf2) {"),
+    "restrict_offset": ("fine[(size_t)(2 * j) * nx + 2 * i + 1] +", "fine[(size_t)(2 * j) * nx + 2 * i + 2] +"),
+    "restrict_no_abs": ("sum += fabs(r - coarse[(size_t)j * mx + i]);", "sum += r - coarse[(size_t)j * mx + i];"),
+    "restrict_half": ("double r = 0.25 * (fine[", "double r = 0.5 * (fine["),
+    "restrict_norm_fine": ("return sum / ((double)mx * (double)my);", "return sum / ((double)nx * (double)my);"),
+    "restrict_transposed": ("sum += fabs(r - coarse[(size_t)j * mx + i]);", "sum += fabs(r - coarse[(size_t)i * my + j]);"),
 }
 
 
