@@ -18,6 +18,8 @@ Reported:
   roofline       the dominant kernel against its bound (FP64 pipe for the FP64 path).
   ensemble_stats moments, histograms and trend statistics of beta across runs: kernel
                  times on a paper-size synthetic ensemble and the workload's own values.
+  refinement     the Appendix-A grid-refinement study (E_n and observed order) up to
+                 --refinement-nmax points per axis.
   cpu_baseline   the FP64 CPU oracle timed on this host's cores (bounded sample).
   --impl reference  times the oracle alone (the reference arm), same metric and config.
 """
@@ -465,6 +467,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=120)
     ap.add_argument("--no-batches", action="store_true", help="skip the uneven-batch and 1024^2 legs")
     ap.add_argument("--no-stats", action="store_true", help="skip the ensemble-statistics leg")
+    ap.add_argument("--refinement-nmax", type=int, default=1024,
+                    help="largest grid of the Appendix-A refinement study leg (0: skip)")
     ap.add_argument("--long-beta", action="store_true",
                     help="also run the 32 x 1024^2 coarsening ensemble over its whole horizon in both precisions "
                          "and compare <beta> (minutes of GPU time)")
@@ -602,6 +606,14 @@ def main():
     stats = None
     if not args.no_stats and rank == 0:
         stats = run_stats_leg(ch, torch, p, ch.CH_FP64)
+    refine = None
+    if args.refinement_nmax >= 128 and rank == 0:
+        # Appendix A: E_n between the n- and n/2-grids of a single-droplet run to T = 10,
+        # dt = 0.1 dx, FP64 (the paper's table runs n = 128 ... 8192)
+        from paper_1911_03386_gb300 import refinement
+        sizes = [n for n in wl.REFINEMENT["sizes"] if n <= args.refinement_nmax]
+        refine = {"workload": wl.REFINEMENT["name"], "gamma": wl.REFINEMENT["gamma"], "T": wl.REFINEMENT["T"],
+                  "dt": "0.1 dx", "precision": "fp64", "rows": refinement.study(sizes)}
 
     from paper_1911_03386_gb300 import replicas
     tdist = torch.distributed if dist else None
@@ -683,6 +695,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_line,
             "gpu_launches": r64["launches"], "clocks": r64["clocks"], "fp32": fp32,
             "beta_avg": beta_stats(avg64), "serving": serving, "batches": batches, "ensemble_stats": stats,
+            "refinement": refine,
             "kernel_source": kernel_source_hash()}
     print(json.dumps(finite_or_none(line), allow_nan=False), flush=True)
     if dist:

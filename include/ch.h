@@ -391,6 +391,26 @@ int ch_ensemble_histogram(ch_handle h, const int* members, int count, double lo,
 int ch_ensemble_trend(ch_handle h, const int* members, int count, double t1, double t2, double tf1, double tf2,
                       double* out);
 
+/*
+ * Grid-refinement error of Appendix A: E = (1/|Omega|) sum over the coarse points of
+ * |restricted fine - coarse| dx_c dy_c, the fine field restricted by the mean of each
+ * 2 x 2 block: fine points (2i, 2j), (2i+1, 2j), (2i, 2j+1), (2i+1, 2j+1) against coarse
+ * point (i, j), which is their centre when both grids sample cell centres.  fine is an
+ * nx x ny FP64 device array (row-major, x fastest; nx, ny even), coarse nx/2 x ny/2.
+ * out (device, 1 + ny/2 doubles) receives E, then the mean over each coarse row.
+ * Asynchronous on `stream`.  Errors: CH_EINVAL (odd or < 2 sizes, NULL arrays), CH_ECUDA.
+ */
+int ch_refinement_error(const double* fine, const double* coarse, int nx, int ny, double* out, void* stream);
+
+/*
+ * The same between member fine_member of handle `fine` and member coarse_member of handle
+ * `coarse` (both FP64; the coarse member has half the points per axis).  Waits for the
+ * coarse handle's stream, runs on the fine handle's stream and writes E to *out (host).
+ * Errors: CH_EINVAL (handles, members, precision or sizes), CH_ENOMEM, CH_ECUDA.
+ */
+int ch_ensemble_refinement_error(ch_handle fine, int fine_member, ch_handle coarse, int coarse_member,
+                                 double* out);
+
 /* ------------------------------------------------------------------------------------ */
 /* Serving: a stream of single-run requests with continuous batching.                    */
 /*                                                                                        */

@@ -20,7 +20,7 @@ __all__ = [
     "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
     "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_seg_tables", "ch_step_field_noalloc", "ch_last_error", "ch_version",
     "CH_MOMENTS", "CH_MAX_BINS", "ch_stats_moments", "ch_stats_histogram", "ch_stats_trend", "ch_ensemble_moments",
-    "ch_ensemble_histogram", "ch_ensemble_trend",
+    "ch_ensemble_histogram", "ch_ensemble_trend", "ch_refinement_error", "ch_ensemble_refinement_error",
     "Ensemble", "Server", "Request", "Result", "ServerStats", "ch_server_create", "ch_submit", "ch_poll",
     "ch_server_wait", "ch_server_stats", "ch_server_destroy",
 ]
@@ -127,6 +127,8 @@ _SIGS = {
     "ch_ensemble_moments": (_c_int, [_vp, _ip, _c_int, _dp, _c_i64, _i64p]),
     "ch_ensemble_histogram": (_c_int, [_vp, _ip, _c_int, _c_dbl, _c_dbl, _c_int, _i64p, _c_i64, _i64p]),
     "ch_ensemble_trend": (_c_int, [_vp, _ip, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _dp]),
+    "ch_refinement_error": (_c_int, [_vp, _vp, _c_int, _c_int, _vp, _vp]),
+    "ch_ensemble_refinement_error": (_c_int, [_vp, _c_int, _vp, _c_int, _dp]),
     "ch_server_create": (_c_int, [ctypes.c_size_t, _c_int, _c_int, ctypes.POINTER(_vp)]),
     "ch_submit": (_c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "ch_poll": (_c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result)]),
@@ -320,6 +322,18 @@ def ch_ensemble_trend(h, t1, t2, tf1, tf2, members=None):
     out = np.zeros(4)
     _check(lib().ch_ensemble_trend(h, mp, cnt, t1, t2, tf1, tf2, _ptr(out)))
     return out[0], out[1], int(out[2]), int(out[3])
+
+
+def ch_refinement_error(fine_ptr, coarse_ptr, nx, ny, out_ptr, stream_ptr=None):
+    """Appendix A's E between device fields (fine nx x ny, coarse nx/2 x ny/2); out gets
+    1 + ny/2 doubles."""
+    _check(lib().ch_refinement_error(fine_ptr, coarse_ptr, nx, ny, out_ptr, stream_ptr))
+
+
+def ch_ensemble_refinement_error(fine_h, fine_member, coarse_h, coarse_member):
+    out = ctypes.c_double()
+    _check(lib().ch_ensemble_refinement_error(fine_h, fine_member, coarse_h, coarse_member, ctypes.byref(out)))
+    return out.value
 
 
 def ch_get_field(h, member):

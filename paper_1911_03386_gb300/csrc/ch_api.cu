@@ -300,6 +300,13 @@ size_t rows_seg_smem_bytes(int nr, int nx, int S, size_t elt, int threads, int n
   return seg_smem_bytes(seg_ctile(nr, nx), seg_mtile(nr, nx, S, elt), nbuf, elt, threads);
 }
 
+// Stencil block: C (nr+4) x (nc+4), mu (nr+2) x (nc+2), then the FP64 reduction buffer.
+size_t blk_smem_bytes(int nr, int nc, size_t elt, int threads) {
+  size_t b = ((size_t)(nr + 4) * (nc + 4) + (size_t)(nr + 2) * (nc + 2)) * elt;
+  b = (b + 15) & ~(size_t)15;
+  return b + (size_t)2 * (threads / 32) * sizeof(double);
+}
+
 size_t sweep_smem_bytes(int nr, int nx, size_t elt) { return (size_t)nr * (nx + 1) * elt; }
 
 // W panel swept in place + C panel, twice when double-buffered
@@ -387,6 +394,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   }
 
   std::vector<Tile> rts[3], csts[4], sts[3], ct;  // rows: S = 16, S = 32, chunked; columns: 4 classes
+  std::vector<Tile> rtb;                          // stencil blocks of long rows (last)
   std::vector<Tile> rtT[17];                   // rows, transposed-block form, by nw
   chk::LaunchShape sh{};
   sh.split = split;
@@ -410,11 +418,14 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       return seg ? rows_seg_smem_bytes(nr, p.nx, rc, h->elt, threads, seg_persist ? 2 : 1)
                  : rows_smem_bytes(nr, p.nx, h->elt, threads);
     };
-    while (rc != 1 && br > 1 && row_bytes(br) > kSmemMax) br = (br + 1) / 2;
+    // FP64 split form: rows too long for a band of the requested height run the stencil in
+    // blocks of br rows x kBlockCols columns
+    const bool blk = split && f64 && row_bytes(br) > kSmemMax;
+    while (!blk && rc != 1 && br > 1 && row_bytes(br) > kSmemMax) br = (br + 1) / 2;
     // segment form without an explicit band: at least two CTAs per SM (wide rows)
     if (seg && t.rows_band <= 0)
       while (br > 4 && row_bytes(br) > kSmemMax / 2) br = (br + 1) / 2;
-    if (rc != 1 && row_bytes(br) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
+    if (!blk && rc != 1 && row_bytes(br) > kSmemMax) return fail(CH_EINVAL, "row too long for shared memory");
     p.seg_g = seg ? p.nx / rc : sc ? p.nx / sc : 0;
     p.row_t = rc == 1 ? p.nx / 32 : 0;
     p.col_s = cc;
@@ -439,7 +450,16 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     if (bc * p.cols_p > threads) p.cols_p = std::max(1, threads / bc);
     int b = 0;
     std::vector<Tile>& rdst = rc == 1 ? rtT[p.nx / 32] : rts[ri];
-    for (int j0 = 0; j0 < p.ny; j0 += br, ++b) rdst.push_back(Tile{k, j0, std::min(br, p.ny - j0), b});
+    if (blk) {
+      const int nc = std::min(p.nx, chk::kBlockCols);
+      while (br > 1 && blk_smem_bytes(br, nc, h->elt, threads) > kSmemMax) br = (br + 1) / 2;
+      for (int j0 = 0; j0 < p.ny; j0 += br)
+        for (int x0 = 0; x0 < p.nx; x0 += nc, ++b)
+          rtb.push_back(Tile{k, j0, std::min(br, p.ny - j0), b, x0, std::min(nc, p.nx - x0)});
+      sh.blk_smem = std::max(sh.blk_smem, blk_smem_bytes(br, nc, h->elt, threads));
+    } else {
+      for (int j0 = 0; j0 < p.ny; j0 += br, ++b) rdst.push_back(Tile{k, j0, std::min(br, p.ny - j0), b});
+    }
     p.nbands = b;
     p.partial_base = part;
     part += b;
@@ -467,7 +487,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       for (int i0 = 0; i0 < p.nx; i0 += bc, ++q) ct.push_back(Tile{k, i0, std::min(bc, p.nx - i0), q});
       if (!stream) sh.cols_panel_cap = std::max(sh.cols_panel_cap, (int)cols_panel_elems(bc, p.ny));
     }
-    sh.rows_smem = std::max(sh.rows_smem, rows_smem_bytes(br, p.nx, h->elt, threads));
+    if (!blk) sh.rows_smem = std::max(sh.rows_smem, rows_smem_bytes(br, p.nx, h->elt, threads));
   }
   // Panel buffers start on 16-byte boundaries (the 16-byte copies need it): round the
   // panel capacity to 4 elements and size the shared memory from the rounded capacity.
@@ -509,6 +529,8 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     rt.insert(rt.end(), rtT[nw].begin(), rtT[nw].end());
   }
   for (int c = 0; c < 3; ++c) rt.insert(rt.end(), rts[c].begin(), rts[c].end());
+  sh.rt_blk = (int)rtb.size();
+  rt.insert(rt.end(), rtb.begin(), rtb.end());
   for (int c = 0; c < 4; ++c) cst.insert(cst.end(), csts[c].begin(), csts[c].end());
   sh.n_row_tiles = (int)rt.size();
   sh.n_sweep_tiles = (int)st.size();

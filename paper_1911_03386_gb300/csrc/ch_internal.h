@@ -19,6 +19,8 @@ namespace chk {
 
 constexpr int64_t kUnbounded = INT64_MAX;
 
+constexpr int kBlockCols = 256;  // columns of a stencil block (long rows, FP64 split form)
+
 struct MemberParams {
   int64_t offset;        // first element of the member's field in C and W
   int nx, ny;
@@ -83,6 +85,7 @@ struct Tile {
   int start;             // first row (row tiles) or first column (column tiles)
   int count;             // rows / columns in the tile
   int index;             // band / panel number within the member
+  int x0, xn;            // stencil blocks of long rows: first column and width (else 0, 0)
 };
 
 struct DevView {
@@ -121,6 +124,10 @@ struct LaunchShape {
   // with S = 16 (rt_seg[0] tiles) and S = 32 (rt_seg[1]), then the chunked form.
   int rtT_n[17];
   int rt_seg[2];
+  // split form, FP64: members whose rows do not fit a shared-memory band run the stencil in
+  // blocks of rows x kBlockCols columns (stencil_block_kernel); their rt_blk tiles come last
+  int rt_blk;
+  size_t blk_smem;
   // split form: sweep tiles ordered S = 16 (st_seg[0]), S = 32 (st_seg[1]) segment-form
   // members (rowseg_kernel), then the others
   int st_seg[2];

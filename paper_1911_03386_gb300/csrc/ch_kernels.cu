@@ -1203,6 +1203,86 @@ __global__ void __launch_bounds__(512) stencil_kernel(DevView v) {
 }
 
 // -------------------------------------------------------------------------------------
+// Split form, kernel 1 for rows too long for a shared-memory band (FP64): the same
+// stencil on a block of nr rows x nc columns.  C is staged with a 2-point halo on every
+// side (periodic, both axes), mu on a 1-point halo; mu and R' are formed in exactly the
+// operation order of compute_mu and rprime_at, so W equals the whole-row kernel's bit for
+// bit.  Each block writes its own partial slot (index = band x blocks per band + block).
+// Shared memory: Cs (nr+4) x (nc+4), Ms (nr+2) x (nc+2), then the FP64 reduction buffer.
+// -------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) stencil_block_kernel(DevView v, int tile_base) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tile tl = v.row_tiles[tile_base + blockIdx.x];
+  const MemberParams& P = v.mp[tl.member];
+  MemberState* st = v.ms + tl.member;
+  bool sample = true;
+  if (!stencil_prologue(tl, st, P, sample)) return;
+  const int nx = P.nx, ny = P.ny, j0 = tl.start, nr = tl.count, i0 = tl.x0, nc = tl.xn;
+  const int lc = nc + 4, lm = nc + 2;
+  T* Cs = reinterpret_cast<T*>(smem);
+  T* Ms = Cs + (size_t)(nr + 4) * lc;
+  double* red = red_buffer(smem, ((size_t)(nr + 4) * lc + (size_t)(nr + 2) * lm) * sizeof(T));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const T* Cg = static_cast<const T*>(v.C) + P.offset;
+  // rows j0-2 .. j0+nr+1 and columns i0-2 .. i0+nc+1, one wrap at most (nx, ny >= 5)
+  for (int r = warp; r < nr + 4; r += nwarps) {
+    int j = j0 - 2 + r;
+    j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
+    const T* src = Cg + (int64_t)j * nx;
+    T* dst = Cs + (size_t)r * lc;
+    for (int c = lane; c < lc; c += 32) {
+      int i = i0 - 2 + c;
+      i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
+      dst[c] = src[i];
+    }
+  }
+  __syncthreads();
+  const T a = (T)P.a, bx = (T)P.bx, by = (T)P.by;
+  for (int r = warp; r < nr + 2; r += nwarps) {
+    const T* c0 = Cs + (size_t)(r + 1) * lc + 1;
+    const T* cm = c0 - lc;
+    const T* cp = c0 + lc;
+    T* mrow = Ms + (size_t)r * lm;
+    for (int c = lane; c < nc + 2; c += 32) {
+      const T x = c0[c];
+      const T u = x * fma(x, x, -a);
+      mrow[c] = fma(-by, cp[c] + cm[c], fma(-bx, c0[c + 1] + c0[c - 1], u));
+    }
+  }
+  __syncthreads();
+  if (sample) {
+    double sF = 0.0, sD = 0.0;
+    const double hxi = 1.0 / P.hx, hyi = 1.0 / P.hy, hg = 0.5 * P.gamma;
+    for (int r = warp; r < nr; r += nwarps) {
+      const T* c0 = Cs + (size_t)(r + 2) * lc + 2;
+      const T* m0 = Ms + (size_t)(r + 1) * lm + 1;
+      for (int c = lane; c < nc; c += 32) {
+        const double x = (double)c0[c];
+        const double gx = ((double)c0[c + 1] - x) * hxi;
+        const double gy = ((double)c0[c + lc] - x) * hyi;
+        const double w = x * x - 1.0;
+        sF += 0.25 * w * w + hg * (gx * gx + gy * gy);
+        const double mu = (double)m0[c];
+        const double mx = ((double)m0[c + 1] - mu) * hxi;
+        const double my = ((double)m0[c + lm] - mu) * hyi;
+        sD += mx * mx + my * my;
+      }
+    }
+    block_sum2(sF, sD, red);
+    if (threadIdx.x == 0) v.partials[P.partial_base + tl.index] = make_double2(sF, sD);
+  }
+  T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
+  const T rho = (T)P.rho, w0 = (T)P.w0;
+  for (int r = warp; r < nr; r += nwarps) {
+    const T* m0 = Ms + (size_t)(r + 1) * lm + 1;
+    T* dst = W + (int64_t)(j0 + r) * nx + i0;
+    for (int c = lane; c < nc; c += 32)
+      dst[c] = fma(w0, m0[c], fma(rho, m0[c + lm] + m0[c - lm], m0[c + 1] + m0[c - 1]));
+  }
+}
+
+// -------------------------------------------------------------------------------------
 // Split form, kernel 2: row sweep of a band of rows, one thread per row, in place in
 // shared memory (pitch nx+1).
 // -------------------------------------------------------------------------------------
@@ -1928,9 +2008,14 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
   if (sh.n_row_tiles == 0) return cudaSuccess;  // no member present
   switch (phase) {
     case 0:
-      if (sh.split)
-        stencil_kernel<T><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v);
-      else
+      if (sh.split) {
+        const int whole = sh.n_row_tiles - sh.rt_blk;
+        if (whole > 0) stencil_kernel<T><<<whole, sh.rows_threads, sh.rows_smem, st>>>(v);
+        if (sh.rt_blk > 0) {
+          if (sizeof(T) != sizeof(double)) return cudaErrorInvalidValue;  // FP64 only
+          stencil_block_kernel<T><<<sh.rt_blk, sh.rows_threads, sh.blk_smem, st>>>(v, whole);
+        }
+      } else
         seg_launch<T>(v, sh, st);
       break;
     case 1: {
@@ -1992,6 +2077,9 @@ cudaError_t smem_limits_impl() {
   if ((e = cudaFuncSetAttribute(rows_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(stencil_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(stencil_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
+      cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(rowsT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;

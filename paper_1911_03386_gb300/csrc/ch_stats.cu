@@ -21,6 +21,10 @@
 // runs (mean, then central sums), both in FP64; the second pass re-reads from L2.  The
 // histogram counts in shared memory with atomics and writes each time's row once.  The
 // trend statistics are one CTA over the moments table.
+//
+// Also here: the grid-refinement error E_n of Appendix A (the mean L1 distance between a
+// field restricted by 2 x 2 block means and the same run on the grid of half the points
+// per axis), one CTA per coarse row and a second CTA over the row values.
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -231,6 +235,56 @@ __global__ void __launch_bounds__(kThreads) trend_kernel(const double* __restric
   }
 }
 
+// row[j] = mean over coarse row j of |1/4 (f(2i,2j) + f(2i+1,2j) + f(2i,2j+1) + f(2i+1,2j+1)) - c(i,j)|.
+__global__ void __launch_bounds__(kThreads) refine_rows_kernel(const double* __restrict__ fine,
+                                                               const double* __restrict__ coarse, int nx,
+                                                               double* __restrict__ row) {
+  __shared__ double red[kThreads];
+  const int j = blockIdx.x, mx = nx / 2;
+  const double* f0 = fine + (size_t)(2 * j) * nx;
+  const double* f1 = f0 + nx;
+  const double* c = coarse + (size_t)j * mx;
+  double sum = 0.0;
+  for (int i = threadIdx.x; i < mx; i += kThreads) {
+    const double r = 0.25 * (f0[2 * i] + f0[2 * i + 1] + f1[2 * i] + f1[2 * i + 1]);
+    sum += fabs(r - c[i]);
+  }
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int h = kThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) row[j] = red[0] / (double)mx;
+}
+
+// out[0] = mean of row[0 .. my).
+__global__ void __launch_bounds__(kThreads) refine_total_kernel(const double* __restrict__ row, int my,
+                                                                double* __restrict__ out) {
+  __shared__ double red[kThreads];
+  double sum = 0.0;
+  for (int j = threadIdx.x; j < my; j += kThreads) sum += row[j];
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int h = kThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0] / (double)my;
+}
+
+// out: 1 + ny/2 doubles (E, then the row means).
+cudaError_t launch_refinement(const double* fine, const double* coarse, int nx, int ny, double* out,
+                              cudaStream_t st) {
+  refine_rows_kernel<<<ny / 2, kThreads, 0, st>>>(fine, coarse, nx, out + 1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  refine_total_kernel<<<1, kThreads, 0, st>>>(out + 1, ny / 2, out);
+  return cudaGetLastError();
+}
+
+bool refine_sizes_ok(int nx, int ny) { return nx >= 2 && ny >= 2 && nx % 2 == 0 && ny % 2 == 0; }
+
 size_t histogram_smem(int nbins) { return sizeof(int) * (size_t)(nbins + 2) * kPad; }
 
 cudaError_t launch_moments(const View& v, double* out, int* mismatch, cudaStream_t st) {
@@ -432,6 +486,38 @@ int ch_ensemble_histogram(ch_handle h, const int* members, int count, double lo,
   }
   if (n) *n = take;
   return CH_OK;
+}
+
+int ch_refinement_error(const double* fine, const double* coarse, int nx, int ny, double* out, void* stream) {
+  if (!chs::refine_sizes_ok(nx, ny) || !fine || !coarse || !out)
+    return chh::fail(CH_EINVAL, "nx, ny even and >= 2, non-NULL arrays");
+  CH_CHECK_CUDA(chs::launch_refinement(fine, coarse, nx, ny, out, static_cast<cudaStream_t>(stream)),
+                "refinement kernels");
+  return CH_OK;
+}
+
+int ch_ensemble_refinement_error(ch_handle fine, int fine_member, ch_handle coarse, int coarse_member,
+                                 double* out) {
+  if (int rc = chh::check_handle(fine)) return rc;
+  if (int rc = chh::check_handle(coarse)) return rc;
+  if (!out) return chh::fail(CH_EINVAL, "out is NULL");
+  if (fine_member < 0 || fine_member >= fine->m || !fine->has(fine_member) || coarse_member < 0 ||
+      coarse_member >= coarse->m || !coarse->has(coarse_member))
+    return chh::fail(CH_EINVAL, "member index out of range");
+  if (fine->precision != CH_FP64 || coarse->precision != CH_FP64)
+    return chh::fail(CH_EINVAL, "the refinement error compares FP64 fields");
+  const MemberParams& pf = fine->hp[fine_member];
+  const MemberParams& pc = coarse->hp[coarse_member];
+  if (!chs::refine_sizes_ok(pf.nx, pf.ny) || pc.nx * 2 != pf.nx || pc.ny * 2 != pf.ny)
+    return chh::fail(CH_EINVAL, "the coarse member must have half the points of the fine member per axis");
+  CH_CHECK_CUDA(cudaStreamSynchronize(coarse->stream), "synchronise the coarse handle");
+  chs::Scratch sc;
+  double* dout = nullptr;
+  if (cudaError_t e = sc.get(&dout, 1 + (size_t)pf.ny / 2)) return chh::cuda_fail(e, "refinement scratch");
+  const double* f = static_cast<const double*>(fine->C) + pf.offset;
+  const double* c = static_cast<const double*>(coarse->C) + pc.offset;
+  CH_CHECK_CUDA(chs::launch_refinement(f, c, pf.nx, pf.ny, dout, fine->stream), "refinement kernels");
+  return chh::copy_out(fine, out, dout, sizeof(double), "read refinement error");
 }
 
 int ch_ensemble_trend(ch_handle h, const int* members, int count, double t1, double t2, double tf1, double tf2,

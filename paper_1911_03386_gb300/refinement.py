@@ -1,0 +1,70 @@
+"""Grid-refinement study of Appendix A on the GPU path.
+
+The same single-droplet start (`workloads.droplet_field`) is run to the final time T on
+grids of n = 128, 256, ... points per axis with dt = 0.1 dx (rounded so every grid ends at
+T), in FP64.  E_n, the mean L1 distance between the n-grid field restricted by 2 x 2
+block means and the n/2-grid field, is computed on the device
+(`ch_ensemble_refinement_error`); log2(E_n / E_2n) is the observed order of convergence.
+Each grid is one handle; only two are alive at a time.
+
+    python -m paper_1911_03386_gb300.refinement --nmax 4096
+"""
+import argparse
+import json
+import math
+import time
+
+import paper_1911_03386_gb300 as ch
+from paper_1911_03386_gb300 import workloads as wl
+
+
+def run_grid(n, preset=wl.REFINEMENT, torch=None):
+    """A handle holding the droplet run on the n-grid after its steps; (handle, info)."""
+    steps, dt = wl.refinement_steps(n, preset)
+    e = ch.Ensemble.create(n, n, preset["L"], preset["gamma"], dt, [0.0], wl.BASE_SEED, ch.CH_FP64)
+    try:
+        e.set_field(0, wl.droplet_field(n, preset["L"], preset["gamma"]))
+        e.set_sampling(max(1, steps), 0.0, 0)  # no samples needed beyond the start
+        t0 = time.perf_counter()
+        e.step(steps)
+        e.synchronize()
+        wall = time.perf_counter() - t0
+        F, D, _ = e.observables()  # of the field at T
+    except Exception:
+        e.close()
+        raise
+    return e, {"n": n, "steps": steps, "dt": dt, "s": preset["gamma"] * dt / (preset["L"] / n) ** 4,
+               "run_s": wall, "grid_point_steps_per_s": n * n * steps / max(wall, 1e-12),
+               "F_T": float(F[0]), "dFdt_T": float(D[0])}
+
+
+def study(sizes=None, preset=wl.REFINEMENT):
+    """Rows {n, steps, dt, E_n (against n/2), order log2(E_n / E_2n)} for sizes[1:]."""
+    sizes = list(preset["sizes"] if sizes is None else sizes)
+    rows = []
+    prev, prev_info = run_grid(sizes[0], preset)
+    try:
+        for n in sizes[1:]:
+            cur, info = run_grid(n, preset)
+            info["E_n"] = ch.ch_ensemble_refinement_error(cur.h, 0, prev.h, 0)
+            prev.close()
+            prev, prev_info = cur, info
+            rows.append(info)
+    finally:
+        prev.close()
+    for a, b in zip(rows, rows[1:]):
+        a["order"] = math.log2(a["E_n"] / b["E_n"]) if a["E_n"] > 0 and b["E_n"] > 0 else None
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nmin", type=int, default=128)
+    ap.add_argument("--nmax", type=int, default=2048)
+    args = ap.parse_args()
+    sizes = [n for n in wl.REFINEMENT["sizes"] if args.nmin <= n <= args.nmax]
+    print(json.dumps(study(sizes)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

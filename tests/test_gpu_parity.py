@@ -711,3 +711,72 @@ def test_fine_grid_nyquist_mode_decays_as_the_scheme_says(prec):
     else:
         bound = nsteps * (dt / h ** 2) * 2.0 ** -24 * 8 * (8 * gamma * eps / h ** 2)
     assert np.max(np.abs(got - C0 - amp * phi)) <= bound
+
+
+# ------------------------------------------------------------------------------------------
+# FP64 split form: rows too long for a shared-memory band run the stencil in blocks of
+# rows x 256 columns (stencil_block_kernel)
+# ------------------------------------------------------------------------------------------
+# h_x = 0.1 on the long members (s_x = 0.1, 0.05): the standard FP64 bars apply
+LONG_ROWS = [dict(nx=4096, ny=24, L=409.6, gamma=0.01, dt=1e-3, C0=0.1),
+             dict(nx=8192, ny=10, L=819.2, gamma=0.005, dt=1e-3, C0=-0.2),
+             dict(nx=1000, ny=17, L=100.0, gamma=0.01, dt=1e-3, C0=0.3),    # ragged last block
+             dict(nx=64, ny=64, L=TWO_PI, gamma=0.01, dt=1e-3, C0=0.0)]     # whole rows, same launch
+# the same width on [0, 2 pi): s_x = 1.8e6, where the bars follow from the conditioning
+LONG_ROWS_STIFF = [dict(nx=4096, ny=24, L=TWO_PI, gamma=0.01, dt=1e-3, C0=0.1),
+                   dict(nx=64, ny=64, L=TWO_PI, gamma=0.01, dt=1e-3, C0=0.0)]
+
+
+@pytest.mark.parametrize("members", [LONG_ROWS, LONG_ROWS_STIFF], ids=["moderate_s", "stiff"])
+def test_long_rows_match_oracle(orc, members):
+    descs, base = [], 0
+    for k, d in enumerate(members):
+        descs.append(dict(d, seed=SEED + 11 * k, counter_base=base))
+        base += d["nx"] * d["ny"]
+    nsteps = 12
+    with ch.Ensemble.batch(descs, ch.CH_FP64) as e:
+        assert e.tuning()["split"] == 1
+        e.set_sampling(4, 0.0, capacity=8)
+        e.step(nsteps)
+        for k, d in enumerate(descs):
+            C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
+            ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps, every=4)
+            # round-off bound: each side's step is backward stable for the factorised
+            # operator, whose condition number is at most 1 + 16 s per axis, so a step adds
+            # at most ~2 u (1 + 16 s_max) max|dC| (s_x = 1.8e6 for the 4096-wide member)
+            s_max = d["gamma"] * d["dt"] / min(d["L"] / d["nx"], d["L"] / d["ny"]) ** 4
+            C, inc = C0.copy(), 0.0
+            for _ in range(nsteps):
+                prev = C.copy()
+                orc.step(C, d["L"], d["gamma"], d["dt"])
+                inc += np.max(np.abs(C - prev))
+            tol = max(1e-12, 2 * 2 * 2.0 ** -53 * (1 + 16 * s_max) * inc)
+            err = np.max(np.abs(e.field(k) - ref.C))
+            assert err <= tol, (k, err, tol)
+            if s_max < 1e3:
+                assert err <= 1e-12, (k, err)
+            ser = e.series(k, 8)
+            assert np.array_equal(ser[:, 0], ref.series[:, 0])
+            np.testing.assert_allclose(ser[:, 1], ref.series[:, 1], rtol=1e-11)
+            if s_max < 1e3:
+                # dF/dt = -h^2 sum |D+ mu|^2 with mu containing gamma lap_h C: at s_x ~ 1e6 the
+                # field's round-off above reaches it amplified by gamma / h^2, so only the
+                # moderate-s members are held to the 1e-9 series bar
+                np.testing.assert_allclose(ser[:, 2], ref.series[:, 2], rtol=1e-9)
+
+
+def test_stencil_blocks_equal_whole_rows():
+    """A band taller than the shared memory holds for whole rows switches the member to the
+    block stencil; mu and R' are formed in the same operation order, so the fields equal the
+    whole-row kernel's bit for bit (observables: the same sums grouped by block)."""
+    d = dict(nx=512, ny=70, L=TWO_PI, gamma=0.01, dt=1e-3, C0=0.2, seed=SEED, counter_base=0)
+    out = []
+    for band in (16, 64):  # 16: whole rows fit (155 KB); 64: block form
+        with ch.Ensemble.batch([d], ch.CH_FP64) as e:
+            e.set_tuning(split=1, rows_band=band)
+            e.set_sampling(5, 0.0, capacity=8)
+            e.step(30)
+            out.append((e.field(0), e.series(0, 8)))
+    assert np.array_equal(out[0][0], out[1][0])
+    np.testing.assert_allclose(out[1][1][:, 1], out[0][1][:, 1], rtol=1e-13)
+    np.testing.assert_allclose(out[1][1][:, 2], out[0][1][:, 2], rtol=1e-12)
