@@ -1208,16 +1208,18 @@ __global__ void __launch_bounds__(512) stencil_kernel(DevView v) {
 // side (periodic, both axes), mu on a 1-point halo; mu and R' are formed in exactly the
 // operation order of compute_mu and rprime_at, so W equals the whole-row kernel's bit for
 // bit.  Each block writes its own partial slot (index = band x blocks per band + block).
+// OBS: observables of the current field only (partials, no W, no step state), the block
+// counterpart of rows_kernel<T, true> for ch_observables.
 // Shared memory: Cs (nr+4) x (nc+4), Ms (nr+2) x (nc+2), then the FP64 reduction buffer.
 // -------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool OBS>
 __global__ void __launch_bounds__(512) stencil_block_kernel(DevView v, int tile_base) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Tile tl = v.row_tiles[tile_base + blockIdx.x];
   const MemberParams& P = v.mp[tl.member];
   MemberState* st = v.ms + tl.member;
   bool sample = true;
-  if (!stencil_prologue(tl, st, P, sample)) return;
+  if (!OBS && !stencil_prologue(tl, st, P, sample)) return;
   const int nx = P.nx, ny = P.ny, j0 = tl.start, nr = tl.count, i0 = tl.x0, nc = tl.xn;
   const int lc = nc + 4, lm = nc + 2;
   T* Cs = reinterpret_cast<T*>(smem);
@@ -1272,6 +1274,7 @@ __global__ void __launch_bounds__(512) stencil_block_kernel(DevView v, int tile_
     block_sum2(sF, sD, red);
     if (threadIdx.x == 0) v.partials[P.partial_base + tl.index] = make_double2(sF, sD);
   }
+  if (OBS) return;
   T* __restrict__ W = static_cast<T*>(v.W) + P.offset;
   const T rho = (T)P.rho, w0 = (T)P.w0;
   for (int r = warp; r < nr; r += nwarps) {
@@ -2013,7 +2016,7 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
         if (whole > 0) stencil_kernel<T><<<whole, sh.rows_threads, sh.rows_smem, st>>>(v);
         if (sh.rt_blk > 0) {
           if (sizeof(T) != sizeof(double)) return cudaErrorInvalidValue;  // FP64 only
-          stencil_block_kernel<T><<<sh.rt_blk, sh.rows_threads, sh.blk_smem, st>>>(v, whole);
+          stencil_block_kernel<T, false><<<sh.rt_blk, sh.rows_threads, sh.blk_smem, st>>>(v, whole);
         }
       } else
         seg_launch<T>(v, sh, st);
@@ -2061,9 +2064,17 @@ cudaError_t step_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) 
 
 template <typename T>
 cudaError_t observe_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
-  if (sh.n_row_tiles > 0) rows_kernel<T, true><<<sh.n_row_tiles, sh.rows_threads, sh.rows_smem, st>>>(v, 0);
+  // whole-row tiles through the observe mode of rows_kernel, stencil blocks of long rows
+  // (last in the list) through the observe mode of stencil_block_kernel
+  const int whole = sh.n_row_tiles - sh.rt_blk;
+  if (whole > 0) rows_kernel<T, true><<<whole, sh.rows_threads, sh.rows_smem, st>>>(v, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (sh.rt_blk > 0) {
+    if (sizeof(T) != sizeof(double)) return cudaErrorInvalidValue;  // FP64 only
+    stencil_block_kernel<T, true><<<sh.rt_blk, sh.rows_threads, sh.blk_smem, st>>>(v, whole);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   obs_finalize_kernel<<<(v.m + 127) / 128, 128, 0, st>>>(v);
   return cudaGetLastError();
 }
@@ -2078,7 +2089,10 @@ cudaError_t smem_limits_impl() {
     return e;
   if ((e = cudaFuncSetAttribute(stencil_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(stencil_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
+  if ((e = cudaFuncSetAttribute(stencil_block_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(stencil_block_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) !=
       cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(rowsT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)

@@ -61,9 +61,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--nmin", type=int, default=128)
     ap.add_argument("--nmax", type=int, default=2048)
+    ap.add_argument("--T", type=float, default=wl.REFINEMENT["T"], help="final time (the study's is 10)")
     args = ap.parse_args()
-    sizes = [n for n in wl.REFINEMENT["sizes"] if args.nmin <= n <= args.nmax]
-    print(json.dumps(study(sizes)), flush=True)
+    preset = dict(wl.REFINEMENT, T=args.T)
+    sizes = [n for n in preset["sizes"] if args.nmin <= n <= args.nmax]
+    print(json.dumps(study(sizes, preset)), flush=True)
 
 
 if __name__ == "__main__":

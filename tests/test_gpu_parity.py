@@ -738,7 +738,12 @@ def test_long_rows_match_oracle(orc, members):
         assert e.tuning()["split"] == 1
         e.set_sampling(4, 0.0, capacity=8)
         e.step(nsteps)
+        F, D, _ = e.observables()  # of the current fields (observe mode of both stencil forms)
         for k, d in enumerate(descs):
+            Fo, Do = orc.field_observables(e.field(k), d["L"], d["gamma"])
+            assert abs(F[k] - Fo) <= 1e-12 * abs(Fo), (k, F[k], Fo)
+            if d["gamma"] * d["dt"] / min(d["L"] / d["nx"], d["L"] / d["ny"]) ** 4 < 1e3:
+                assert abs(D[k] - Do) <= 1e-9 * abs(Do), (k, D[k], Do)
             C0 = orc.initial_field(d["nx"], d["ny"], d["C0"], d["seed"], d["counter_base"])
             ref = orc.run(C0, d["L"], d["gamma"], d["dt"], nsteps, every=4)
             # round-off bound: each side's step is backward stable for the factorised
@@ -776,7 +781,9 @@ def test_stencil_blocks_equal_whole_rows():
             e.set_tuning(split=1, rows_band=band)
             e.set_sampling(5, 0.0, capacity=8)
             e.step(30)
-            out.append((e.field(0), e.series(0, 8)))
+            out.append((e.field(0), e.series(0, 8), e.observables()))
     assert np.array_equal(out[0][0], out[1][0])
+    for q in range(2):
+        np.testing.assert_allclose(out[1][2][q], out[0][2][q], rtol=1e-12)
     np.testing.assert_allclose(out[1][1][:, 1], out[0][1][:, 1], rtol=1e-13)
     np.testing.assert_allclose(out[1][1][:, 2], out[0][1][:, 2], rtol=1e-12)
