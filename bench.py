@@ -469,6 +469,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=120)
     ap.add_argument("--no-batches", action="store_true", help="skip the uneven-batch and 1024^2 legs")
     ap.add_argument("--no-stats", action="store_true", help="skip the ensemble-statistics leg")
+    ap.add_argument("--campaign", action="store_true",
+                    help="also run the paper's L = 2 pi campaign ensemble (1024 x 256^2 to t = 100, FP32; "
+                         "about 75 s of GPU time) and report its Table 4 statistics")
     ap.add_argument("--refinement-nmax", type=int, default=1024,
                     help="largest grid of the Appendix-A refinement study leg (0: skip)")
     ap.add_argument("--long-beta", action="store_true",
@@ -617,6 +620,12 @@ def main():
         refine = {"workload": wl.REFINEMENT["name"], "gamma": wl.REFINEMENT["gamma"], "T": wl.REFINEMENT["T"],
                   "dt": "0.1 dx", "precision": "fp64", "rows": refinement.study(sizes)}
 
+    camp = None
+    if args.campaign and rank == 0:
+        from paper_1911_03386_gb300 import campaign
+        camp = campaign.run(2 * math.pi, wl.CAMPAIGN["M"], ch.CH_FP32)
+        camp["paper_table4"] = dict(zip(["beta0", "k"], wl.CAMPAIGN["table4"]["2pi"]))
+
     from paper_1911_03386_gb300 import replicas
     tdist = torch.distributed if dist else None
 
@@ -697,7 +706,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_line,
             "gpu_launches": r64["launches"], "clocks": r64["clocks"], "fp32": fp32,
             "beta_avg": beta_stats(avg64), "serving": serving, "batches": batches, "ensemble_stats": stats,
-            "refinement": refine,
+            "refinement": refine, "campaign": camp,
             "kernel_source": kernel_source_hash()}
     print(json.dumps(finite_or_none(line), allow_nan=False), flush=True)
     if dist:

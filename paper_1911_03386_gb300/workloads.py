@@ -113,3 +113,19 @@ def refinement_steps(n, preset=REFINEMENT):
     dx = preset["L"] / n
     steps = max(1, int(round(preset["T"] / (preset["cfl"] * dx))))
     return steps, preset["T"] / steps
+
+
+# The paper's Cahn-Hilliard campaign (Sec. 4.1-4.2, Tables 3-4): M = 1024 runs per domain
+# size L, gamma = 0.01, dt = 0.0012, dx = 2 pi / 256 (Sec. 4.1's resolution; Table 3's
+# caption says 2 pi / 512), t up to 100, asymmetric mixtures; Table 4 reports the window
+# mean of mu_1 over [20, 100] and k of mu_2 = k t fitted on the same window.
+CAMPAIGN = dict(name="paper-campaign-asymmetric", gamma=0.01, dt=0.0012, dx=TWO_PI / 256, T=100.0,
+                Ls=[TWO_PI, 2 * TWO_PI, 4 * TWO_PI, 8 * TWO_PI], M=1024, every=10, window=(20.0, 100.0),
+                table4={"2pi": (0.33, 0.036), "4pi": (0.28, 0.0056), "8pi": (0.28, 0.0013), "16pi": (0.28, 0.00031)})
+
+
+def asymmetric_field(n, seed, member):
+    """Sec. 4.1's asymmetric start on an n x n grid: C = 0.5 + 0.1 (r - 1), r i.i.d. uniform
+    on [0, 1) (numpy's generator, one stream per (seed, member))."""
+    rng = np.random.default_rng([seed, member])
+    return 0.5 + 0.1 * (rng.random((n, n)) - 1.0)
