@@ -21,7 +21,9 @@
  *   - statistics of beta across an ensemble: the moments of Sec. 3.3 Eqs. (41a,b) per
  *     sample time, histograms (the empirical p_beta(b, t) of Sec. 1 Eq. (7)), the window
  *     mean of mu_1 (Eq. (42)) and the slope k of the least-squares line mu_2 = k t;
- *   - the grid-refinement error E_n of Appendix A (2 x 2 restriction, L1 distance).
+ *   - the grid-refinement error E_n of Appendix A (2 x 2 restriction, L1 distance);
+ *   - Model 1, the mean-field droplet population of Secs. 2-3 (Eqs. (13), (14), (31),
+ *     (33), (36), (38), (39)), integrated by the Dormand-Prince 5(4) pair.
  * The discretisation (Sec. 4.1 names only a semi-implicit ADI finite-difference method
  * with periodic boundaries) is read as the delta-form approximate factorisation
  *     (I + s D_x^4)(I + s D_y^4)(C^{n+1} - C^n) = dt * lap_h( C^3 - C - gamma lap_h C )^n,
@@ -481,4 +483,203 @@ double or_refinement_error(int nx, int ny, const double* fine, const double* coa
     }
   }
   return sum / ((double)mx * (double)my);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Model 1: a population of N droplets under mean-field (LSW-type) dynamics.          */
+/*   dR_i/dt = H(R_i + eps) (-1/R_i^2 + u/R_i),   Sec. 2.1 Eq. (13), regularised as  */
+/*                                                 in Sec. 3.1 Eq. (39);              */
+/*   u = sum_i H(R_i) / sum_i H(R_i) R_i,          Sec. 2.1 Eq. (14);                 */
+/* H(s) = 1 for s > 0, else 0.  Observables (Sec. 2.4): F = 1/2 sum H(R_i) R_i^2      */
+/* (Eq. (31) with the volume constraint met), dF/dt = -sum H(R_i)/R_i (1 - u R_i)^2   */
+/* (Eq. (33)), beta = -(t/F) dF/dt (Eq. (36)).  Start: R_i(0) = r_i (Eq. (38)).       */
+/* Time stepping: the Dormand-Prince 5(4) Runge-Kutta pair (J. R. Dormand and P. J.   */
+/* Prince, J. Comput. Appl. Math. 6 (1980) 19-26), the method of Matlab's ODE45 that  */
+/* the paper names, on the whole N-vector with one step size.                         */
+/* ------------------------------------------------------------------------------ */
+
+/* Right-hand side of the droplet system at radii R: out_i = dR_i/dt; *u_out = u. */
+static void or_drop_rhs(int N, const double* R, double eps, double* out, double* u_out) {
+  double alive = 0.0, sum_r = 0.0;
+  for (int i = 0; i < N; ++i) {
+    if (R[i] > 0.0) {
+      alive += 1.0;
+      sum_r += R[i];
+    }
+  }
+  double u = sum_r > 0.0 ? alive / sum_r : 0.0;
+  for (int i = 0; i < N; ++i) out[i] = (R[i] + eps > 0.0) ? (-1.0 / (R[i] * R[i]) + u / R[i]) : 0.0;
+  if (u_out) *u_out = u;
+}
+
+/* F, dF/dt and the number of droplets with R > 0 (Eqs. (31), (33)). */
+void or_drop_observables(int N, const double* R, double* F, double* dFdt, double* alive) {
+  double cnt = 0.0, sum_r = 0.0;
+  for (int i = 0; i < N; ++i) {
+    if (R[i] > 0.0) {
+      cnt += 1.0;
+      sum_r += R[i];
+    }
+  }
+  double u = sum_r > 0.0 ? cnt / sum_r : 0.0;
+  double f = 0.0, d = 0.0;
+  for (int i = 0; i < N; ++i) {
+    if (R[i] > 0.0) {
+      f += 0.5 * R[i] * R[i];
+      double g = 1.0 - u * R[i];
+      d += g * g / R[i];
+    }
+  }
+  *F = f;
+  *dFdt = -d;
+  *alive = cnt;
+}
+
+/* The Dormand-Prince tableau: nodes c, stage weights a (lower triangle, row s holds the
+ * weights of stages 1..s-1 for stage s), the fifth-order weights b (= row 7 of a) and the
+ * embedded fourth-order weights bs. */
+static const double OR_DP_C[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
+static const double OR_DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
+static const double OR_DP_BS[7] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0,
+                                   -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
+
+/*
+ * One Dormand-Prince step of size h from y (n components) for a right-hand side f:
+ * k[0] must hold f(y) on entry (first-same-as-last); on return ynew holds the
+ * fifth-order solution, k[6] = f(ynew), and err[i] = ynew_i - (fourth-order solution)_i.
+ * k is 7 x n scratch, ys n scratch.
+ */
+typedef void (*or_rhs_fn)(int n, const double* y, double eps, double* out, double* u_out);
+
+static void or_dp_step(int n, const double* y, double h, double eps, or_rhs_fn f, double* k, double* ys,
+                       double* ynew, double* err) {
+  for (int s = 1; s < 7; ++s) {
+    for (int i = 0; i < n; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < s; ++j) acc += OR_DP_A[s][j] * k[(size_t)j * n + i];
+      ys[i] = y[i] + h * acc;
+    }
+    f(n, ys, eps, k + (size_t)s * n, NULL);
+  }
+  /* stage 7 is evaluated at the fifth-order solution itself (row 7 of a = b) */
+  for (int i = 0; i < n; ++i) {
+    ynew[i] = ys[i];
+    double lo = 0.0;
+    for (int j = 0; j < 7; ++j) lo += OR_DP_BS[j] * k[(size_t)j * n + i];
+    err[i] = ynew[i] - (y[i] + h * lo);
+  }
+}
+
+/*
+ * Integrate a droplet population from t = 0 to t_end.  R (n values) holds R(0) on entry
+ * and R(t_end) on return.  Step control (adaptive when rtol > 0): a step of size h is
+ * accepted when the scaled error norm
+ *     err = sqrt( (1/n) sum_i ( e_i / (atol + rtol * max(|R_i|, |Rnew_i|)) )^2 ) <= 1,
+ * and the next size is h * min(5, max(0.2, 0.9 err^(-1/5))) (at most h after a rejection;
+ * 5 h when err = 0); the first try is h0.  With rtol <= 0 every step has size h0 (fixed
+ * steps).  Steps are shortened to land exactly on each sample time ts[0 .. ns) (increasing,
+ * within [0, t_end]); at each, the sample (t, F, dF/dt, beta, alive) is written to
+ * series[5 s ..].  stats[0] = accepted steps, stats[1] = rejected steps.
+ * Returns OR_OK, OR_EINVAL (bad arguments; more than max_steps steps; h below 1e-300).
+ */
+int or_drop_run(int n, double* R, double t_end, int ns, const double* ts, double rtol, double atol, double h0,
+                double eps, int64_t max_steps, double* series, int64_t* stats) {
+  if (n < 1 || !(t_end >= 0.0) || !(h0 > 0.0) || ns < 0 || max_steps < 1) return OR_EINVAL;
+  double* k = (double*)malloc(sizeof(double) * 7 * (size_t)n);
+  double* ys = (double*)malloc(sizeof(double) * (size_t)n);
+  double* ynew = (double*)malloc(sizeof(double) * (size_t)n);
+  double* err = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!k || !ys || !ynew || !err) {
+    free(k); free(ys); free(ynew); free(err);
+    return OR_ENOMEM;
+  }
+  int rc = OR_OK;
+  double t = 0.0, h = h0;
+  int next = 0;
+  int64_t acc = 0, rej = 0;
+  or_drop_rhs(n, R, eps, k, NULL);
+  for (;;) {
+    while (next < ns && ts[next] <= t) { /* samples due at the current time */
+      double F, D, alive;
+      or_drop_observables(n, R, &F, &D, &alive);
+      double* row = series + 5 * (size_t)next;
+      row[0] = t;
+      row[1] = F;
+      row[2] = D;
+      row[3] = or_beta(t, F, D);
+      row[4] = alive;
+      ++next;
+    }
+    if (t >= t_end) break;
+    if (acc + rej >= max_steps || !(h > 1e-300)) {
+      rc = OR_EINVAL;
+      break;
+    }
+    double target = next < ns && ts[next] < t_end ? ts[next] : t_end;
+    int lands = h >= target - t;
+    double hs = lands ? target - t : h;
+    or_dp_step(n, R, hs, eps, or_drop_rhs, k, ys, ynew, err);
+    double e2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double sc = atol + rtol * fmax(fabs(R[i]), fabs(ynew[i]));
+      double q = err[i] / sc;
+      e2 += q * q;
+    }
+    double en = rtol > 0.0 ? sqrt(e2 / (double)n) : 0.0;
+    int accept = rtol <= 0.0 || en <= 1.0;
+    if (accept) {
+      memcpy(R, ynew, sizeof(double) * (size_t)n);
+      memcpy(k, k + (size_t)6 * n, sizeof(double) * (size_t)n);
+      t = lands ? target : t + hs;
+      ++acc;
+    } else {
+      ++rej;
+    }
+    if (rtol > 0.0) {
+      double fac = en > 0.0 ? 0.9 * pow(en, -0.2) : 5.0;
+      fac = fmin(5.0, fmax(0.2, fac));
+      if (!accept) fac = fmin(fac, 1.0);
+      h = hs * fac;
+    }
+  }
+  stats[0] = acc;
+  stats[1] = rej;
+  free(k); free(ys); free(ynew); free(err);
+  return rc;
+}
+
+/* One Dormand-Prince step of the scalar test equation y' = g(t) = t^p (time-only right-hand
+ * side) from (t, y) with step h: returns the fifth-order value, *err = fifth - fourth. */
+double or_dp_poly_step(int p, double t, double y, double h, double* err) {
+  double k[7];
+  for (int s = 0; s < 7; ++s) k[s] = pow(t + OR_DP_C[s] * h, (double)p);
+  double hi = 0.0, lo = 0.0;
+  for (int j = 0; j < 6; ++j) hi += OR_DP_A[6][j] * k[j];
+  for (int j = 0; j < 7; ++j) lo += OR_DP_BS[j] * k[j];
+  *err = h * (hi - lo);
+  return y + h * hi;
+}
+
+/* One Dormand-Prince step of the linear test equation y' = lam y from y with step h:
+ * returns the fifth-order value, *err = fifth - fourth. */
+double or_dp_lin_step(double lam, double y, double h, double* err) {
+  double k[7], ys = y;
+  k[0] = lam * y;
+  for (int s = 1; s < 7; ++s) {
+    double acc = 0.0;
+    for (int j = 0; j < s; ++j) acc += OR_DP_A[s][j] * k[j];
+    ys = y + h * acc;
+    k[s] = lam * ys;
+  }
+  double lo = 0.0;
+  for (int j = 0; j < 7; ++j) lo += OR_DP_BS[j] * k[j];
+  *err = ys - (y + h * lo);
+  return ys;
 }

@@ -31,6 +31,10 @@ _SIGS = {
     "or_beta_histogram": (_i, [_i64, _i64, _i64, _dp, _d, _d, _i, _i64p]),
     "or_beta_trend": (None, [_i64, _dp, _dp, _dp, _d, _d, _d, _d, _dp]),
     "or_refinement_error": (_d, [_i, _i, _dp, _dp]),
+    "or_drop_observables": (None, [_i, _dp, _dp, _dp, _dp]),
+    "or_drop_run": (_i, [_i, _dp, _d, _i, _dp, _d, _d, _d, _d, _i64, _dp, _i64p]),
+    "or_dp_poly_step": (_d, [_i, _d, _d, _d, _dp]),
+    "or_dp_lin_step": (_d, [_d, _d, _d, _dp]),
 }
 
 
@@ -180,6 +184,39 @@ class Oracle:
         ny, nx = fine.shape
         assert coarse.shape == (ny // 2, nx // 2)
         return float(self._L.or_refinement_error(nx, ny, _ptr(fine), _ptr(coarse)))
+
+    # ---- Model 1 droplet populations (Secs. 2-3) ----
+    def drop_observables(self, R):
+        """(F, dF/dt, droplets with R > 0) of radii R (Eqs. (31), (33))."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        F, D, A = _d(), _d(), _d()
+        self._L.or_drop_observables(R.size, _ptr(R), ctypes.byref(F), ctypes.byref(D), ctypes.byref(A))
+        return F.value, D.value, int(A.value)
+
+    def drop_run(self, R0, t_end, ts, rtol=1e-6, atol=1e-9, h0=1e-4, eps=1e-3, max_steps=10 ** 7):
+        """Integrate one population from R0 to t_end; returns (R(t_end), samples (len(ts), 5):
+        t, F, dF/dt, beta, alive; accepted steps, rejected steps)."""
+        R = np.array(R0, dtype=np.float64, order="C", copy=True)
+        ts = np.ascontiguousarray(ts, dtype=np.float64)
+        series = np.full((max(ts.size, 1), 5), np.nan)
+        stats = np.zeros(2, dtype=np.int64)
+        rc = self._L.or_drop_run(R.size, _ptr(R), t_end, ts.size, _ptr(ts), rtol, atol, h0, eps, max_steps,
+                                 _ptr(series), stats.ctypes.data_as(_i64p))
+        if rc != 0:
+            raise ValueError("or_drop_run rc=%d" % rc)
+        return R, series[: ts.size], int(stats[0]), int(stats[1])
+
+    def dp_poly_step(self, p, t, y, h):
+        """One Dormand-Prince step of y' = t^p: (fifth-order value, fifth - fourth)."""
+        e = _d()
+        v = self._L.or_dp_poly_step(p, t, y, h, ctypes.byref(e))
+        return v, e.value
+
+    def dp_lin_step(self, lam, y, h):
+        """One Dormand-Prince step of y' = lam y: (fifth-order value, fifth - fourth)."""
+        e = _d()
+        v = self._L.or_dp_lin_step(lam, y, h, ctypes.byref(e))
+        return v, e.value
 
 
 _default = None

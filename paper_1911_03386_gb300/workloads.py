@@ -129,3 +129,16 @@ def asymmetric_field(n, seed, member):
     on [0, 1) (numpy's generator, one stream per (seed, member))."""
     rng = np.random.default_rng([seed, member])
     return 0.5 + 0.1 * (rng.random((n, n)) - 1.0)
+
+
+# Model 1 (Secs. 2-3): ensembles of M = 100 droplet populations of N droplets each, radii
+# drawn uniformly from [0, 1) (Eq. (38)), N = 512 ... 8192 (Table 1), t up to 40, eps = 1e-3.
+DROPLETS = dict(name="model1-droplet-ensembles", M=100, Ns=[512, 1024, 2048, 4096, 8192], T=40.0, eps=1e-3,
+                rtol=1e-6, atol=1e-9, h0=1e-6, sample_dt=0.1, window=(20.0, 40.0), fit=(0.0, 40.0),
+                table2={512: (0.24, 0.0075), 1024: (0.2613, 0.0036), 2048: (0.2833, 0.0017),
+                        4096: (0.2908, 8.6e-4), 8192: (0.2995, 4.5e-4)})
+
+
+def droplet_radii(M, N, seed=BASE_SEED):
+    """Initial radii of M populations of N droplets, i.i.d. uniform on [0, 1): (M, N)."""
+    return np.random.default_rng([seed, N]).random((M, N))

@@ -473,6 +473,107 @@ def pin_refinement_fourier_mode(orc):
         assert abs(got - want) <= 1e-13 * want + 1e-16, (nx, ny, k, l, got, want)
 
 
+# ------------------------------------------------------------------------------------------
+# Model 1 droplet populations and the Dormand-Prince integrator
+# ------------------------------------------------------------------------------------------
+def pin_dp_quadrature_orders(orc):
+    """For y' = t^p the fifth-order solution is the method's quadrature: exact for p <= 4
+    (the order conditions sum b c^k = 1/(k+1), k <= 4) and wrong at p = 5, its error
+    scaling like h^6; the embedded fourth-order solution is exact for p <= 3, so the error
+    estimate vanishes there and scales like h^5 at p = 4."""
+    t0 = 0.3
+    for p in range(5):
+        for h in (0.7, 0.35):
+            v, e = orc.dp_poly_step(p, t0, 0.0, h)
+            want = ((t0 + h) ** (p + 1) - t0 ** (p + 1)) / (p + 1)
+            assert abs(v - want) <= 1e-15 * max(1.0, abs(want)), (p, h, v, want)
+            if p <= 3:
+                assert abs(e) <= 1e-15, (p, e)
+    e1 = orc.dp_poly_step(4, 0.0, 0.0, 0.2)[1]
+    e2 = orc.dp_poly_step(4, 0.0, 0.0, 0.1)[1]
+    assert e1 != 0.0 and abs(e1 / e2 - 32.0) < 1e-9
+    d1 = orc.dp_poly_step(5, 0.0, 0.0, 0.2)[0] - 0.2 ** 6 / 6
+    d2 = orc.dp_poly_step(5, 0.0, 0.0, 0.1)[0] - 0.1 ** 6 / 6
+    assert d1 != 0.0 and abs(d1 / d2 - 64.0) < 1e-6
+
+
+def pin_dp_linear_stability(orc):
+    """On y' = lam y one step multiplies y by the method's stability function, for the
+    Dormand-Prince pair R(z) = sum_{k <= 5} z^k / k! + z^6 / 600 (z = lam h); the error
+    estimate behaves like z^5."""
+    for lam, h in [(1.0, 0.5), (-3.0, 0.1), (-20.0, 0.1), (2.0, 0.01)]:
+        z = lam * h
+        R = sum(z ** k / math.factorial(k) for k in range(6)) + z ** 6 / 600.0
+        v, _ = orc.dp_lin_step(lam, 1.0, h)
+        assert abs(v - R) <= 4e-16 * max(1.0, abs(R)), (lam, h, v, R)
+    e1 = orc.dp_lin_step(-1.0, 1.0, 0.04)[1]
+    e2 = orc.dp_lin_step(-1.0, 1.0, 0.02)[1]
+    assert e1 != 0.0 and abs(e1 / e2 - 32.0) < 1.0
+
+
+def pin_drop_single_and_invariants(orc):
+    """One droplet is stationary (u = 1/R balances the curvature term).  Along a stretch
+    with no extinction the flow conserves the total volume sum R^3 (3 sum R^2 dR/dt =
+    3 sum (u R - 1) = 0 by the definition of u) and F decreases."""
+    R, ser, acc, rej = orc.drop_run([0.37], 5.0, [0.0, 5.0], rtol=1e-10, atol=1e-12)
+    assert abs(R[0] - 0.37) <= 1e-13
+    R0 = np.array([0.6, 0.7, 0.8, 0.95, 1.0])
+    R, ser, acc, rej = orc.drop_run(R0, 0.05, np.linspace(0, 0.05, 6), rtol=1e-11, atol=1e-13)
+    assert np.all(ser[:, 4] == 5)
+    assert abs(np.sum(R ** 3) - np.sum(R0 ** 3)) <= 1e-10
+    assert np.all(np.diff(ser[:, 1]) < 0)
+
+
+def pin_drop_observables_identity(orc):
+    """dF/dt of Eq. (33) equals -sum 1/R + u N over the live droplets (expand the square
+    and use u sum R = N); dead droplets (R <= 0) count in neither F nor dF/dt."""
+    rng = np.random.default_rng(9)
+    R = rng.uniform(0.05, 1.0, 40)
+    R[[3, 17]] = [-1e-3, 0.0]
+    live = R[R > 0]
+    u = live.size / live.sum()
+    F, D, A = orc.drop_observables(R)
+    assert A == live.size
+    assert abs(F - 0.5 * np.sum(live ** 2)) <= 1e-14 * F
+    assert abs(D - (-np.sum(1.0 / live) + u * live.size)) <= 1e-12 * abs(D)
+
+
+def pin_drop_dFdt_is_derivative(orc):
+    """The sampled dF/dt is the time derivative of the sampled F: central differences of
+    F at spacing delta agree to O(delta^2) (tight tolerances, no extinction)."""
+    R0 = np.array([0.5, 0.65, 0.8, 0.9, 1.0, 1.1])
+    d = 1e-3
+    ts = np.array([0.02 - d, 0.02, 0.02 + d])
+    _, ser, _, _ = orc.drop_run(R0, 0.03, ts, rtol=1e-12, atol=1e-14)
+    fd = (ser[2, 1] - ser[0, 1]) / (2 * d)
+    assert abs(fd - ser[1, 2]) <= 1e-4 * abs(ser[1, 2]), (fd, ser[1, 2])
+    assert abs(ser[1, 3] - (-(0.02 / ser[1, 1]) * ser[1, 2])) <= 1e-15 * abs(ser[1, 3])
+
+
+def pin_drop_convergence_order(orc):
+    """Fixed steps (rtol <= 0) converge at fifth order or better on a smooth stretch (no
+    extinction before t = 0.1): halving h from 0.025 divides the error by more than 2^4.5
+    (measured 44; a tableau that loses an order condition drops to 16 or below)."""
+    R0 = np.array([0.6, 0.8, 1.0])
+    ref = orc.drop_run(R0, 0.1, [], rtol=0.0, h0=0.1 / 1024)[0]
+    errs = [np.max(np.abs(orc.drop_run(R0, 0.1, [], rtol=0.0, h0=0.1 / m)[0] - ref)) for m in (4, 8)]
+    assert errs[0] / errs[1] > 2.0 ** 4.5 and errs[1] < 1e-9, errs
+
+
+def pin_drop_extinction(orc):
+    """A droplet much smaller than the others vanishes after about R^3/3 (dR/dt ~ -1/R^2),
+    then sits at or just below -eps, out of the live count; the adaptive integrator with
+    tight tolerances agrees with fine fixed steps."""
+    R0 = np.array([0.05, 1.0])
+    R, ser, _, _ = orc.drop_run(R0, 2e-4, [1e-5, 2e-4], rtol=1e-9, atol=1e-12, h0=1e-7, eps=1e-3)
+    assert ser[0, 4] == 2 and ser[1, 4] == 1
+    assert -2e-3 < R[0] <= -1e-3
+    R1 = np.array([0.6, 0.8, 1.0])
+    a = orc.drop_run(R1, 0.1, [], rtol=1e-11, atol=1e-13)[0]
+    b = orc.drop_run(R1, 0.1, [], rtol=0.0, h0=0.1 / 256)[0]
+    assert np.max(np.abs(a - b)) <= 1e-10
+
+
 ALL_PINS = [
     pin_splitmix_golden,
     pin_uniform_exact,
@@ -500,4 +601,11 @@ ALL_PINS = [
     pin_trend_closed_forms,
     pin_refinement_prolongation_and_linear,
     pin_refinement_fourier_mode,
+    pin_dp_quadrature_orders,
+    pin_dp_linear_stability,
+    pin_drop_single_and_invariants,
+    pin_drop_observables_identity,
+    pin_drop_dFdt_is_derivative,
+    pin_drop_convergence_order,
+    pin_drop_extinction,
 ]

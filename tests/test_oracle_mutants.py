@@ -62,6 +62,19 @@ MUTANTS = {
     "restrict_half": ("double r = 0.25 * (fine[", "double r = 0.5 * (fine["),
     "restrict_norm_fine": ("return sum / ((double)mx * (double)my);", "return sum / ((double)nx * (double)my);"),
     "restrict_transposed": ("sum += fabs(r - coarse[(size_t)j * mx + i]);", "sum += fabs(r - coarse[(size_t)i * my + j]);"),
+    "drop_rhs_sign": ("(-1.0 / (R[i] * R[i]) + u / R[i])", "(1.0 / (R[i] * R[i]) + u / R[i])"),
+    "drop_u_counts_twice": ("alive += 1.0;", "alive += 2.0;"),
+    "drop_heaviside_shift": ("(R[i] + eps > 0.0) ?", "(R[i] - eps > 0.0) ?"),
+    "drop_F_no_half": ("f += 0.5 * R[i] * R[i];", "f += R[i] * R[i];"),
+    "drop_dFdt_sign": ("*dFdt = -d;", "*dFdt = d;"),
+    "drop_dFdt_u_sign": ("double g = 1.0 - u * R[i];", "double g = 1.0 + u * R[i];"),
+    "dp_a53": ("64448.0 / 6561.0", "64448.0 / 6562.0"),
+    "dp_a32": ("{3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0}", "{3.0 / 40.0, 9.0 / 41.0, 0, 0, 0, 0}"),
+    "dp_b3": ("500.0 / 1113.0", "500.0 / 1112.0"),
+    "dp_bs3": ("7571.0 / 16695.0", "7571.0 / 16696.0"),
+    "dp_c5": ("8.0 / 9.0, 1.0, 1.0}", "7.0 / 9.0, 1.0, 1.0}"),
+    "dp_no_fsal": ("memcpy(k, k + (size_t)6 * n, sizeof(double) * (size_t)n);", ";"),
+    "dp_stage_h": ("ys[i] = y[i] + h * acc;", "ys[i] = y[i] + 0.5 * h * acc;"),
 }
 
 
