@@ -412,6 +412,36 @@ int ch_ensemble_refinement_error(ch_handle fine, int fine_member, ch_handle coar
                                  double* out);
 
 /* ------------------------------------------------------------------------------------ */
+/* Model 1: ensembles of mean-field droplet populations (Secs. 2-3).                      */
+/* ------------------------------------------------------------------------------------ */
+
+/*
+ * Integrate M populations of N droplets each from t = 0 to t_end on the device:
+ *   dR_i/dt = H(R_i + eps) (-1/R_i^2 + u/R_i),  u = sum H(R_i) / sum H(R_i) R_i
+ * (Sec. 2.1 Eqs. (13)-(14), regularised as in Sec. 3.1 Eq. (39); H(s) = 1 for s > 0, else
+ * 0), each population with its own Dormand-Prince 5(4) step size.  A step of size h is
+ * accepted when sqrt((1/N) sum_i (e_i / (atol + rtol max(|R_i|, |Rnew_i|)))^2) <= 1 (e the
+ * fifth- minus fourth-order solution); the next size is h min(5, max(0.2, 0.9 err^(-1/5)))
+ * (at most h after a rejection); the first try is h0.  rtol <= 0: fixed steps of h0.
+ * Steps are shortened to land on every sample time, where (t, F, dF/dt, beta, live
+ * droplets) is recorded, F = 1/2 sum H(R_i) R_i^2, dF/dt = -sum H(R_i)/R_i (1 - u R_i)^2,
+ * beta = -(t/F) dF/dt (Sec. 2.4 Eqs. (31), (33), (36)).
+ *   R          host, M x N (population-major): radii at t = 0 in, at t_end out
+ *   t_samples  host, nsamples increasing times (those above t_end are never reached)
+ *   series     host, M x nsamples x 5 doubles, or NULL; unreached samples are NaN
+ *   steps      host, M x 3 (accepted, rejected, status 0 ok / 1 step limit / 2 step
+ *              underflow), or NULL
+ * All buffers are the caller's; the call allocates device scratch (10 M N doubles, 2 M N
+ * ints) and
+ * synchronises `stream` (a cudaStream_t, NULL = legacy default stream).
+ * Errors: CH_EINVAL (arguments; a population reached max_steps steps or its step size
+ * underflowed, with R and steps still written), CH_ENOMEM, CH_ECUDA.
+ */
+int ch_droplets_run(int M, int N, double* R, double t_end, int nsamples, const double* t_samples, double rtol,
+                    double atol, double h0, double eps, int64_t max_steps, double* series, int64_t* steps,
+                    void* stream);
+
+/* ------------------------------------------------------------------------------------ */
 /* Serving: a stream of single-run requests with continuous batching.                    */
 /*                                                                                        */
 /* The paper (Sec. 4.1) ran its ensembles as M separate processes sharing the GPUs        */

@@ -21,6 +21,7 @@ __all__ = [
     "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_seg_tables", "ch_step_field_noalloc", "ch_last_error", "ch_version",
     "CH_MOMENTS", "CH_MAX_BINS", "ch_stats_moments", "ch_stats_histogram", "ch_stats_trend", "ch_ensemble_moments",
     "ch_ensemble_histogram", "ch_ensemble_trend", "ch_refinement_error", "ch_ensemble_refinement_error",
+    "ch_droplets_run",
     "Ensemble", "Server", "Request", "Result", "ServerStats", "ch_server_create", "ch_submit", "ch_poll",
     "ch_server_wait", "ch_server_stats", "ch_server_destroy",
 ]
@@ -129,6 +130,8 @@ _SIGS = {
     "ch_ensemble_trend": (_c_int, [_vp, _ip, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _dp]),
     "ch_refinement_error": (_c_int, [_vp, _vp, _c_int, _c_int, _vp, _vp]),
     "ch_ensemble_refinement_error": (_c_int, [_vp, _c_int, _vp, _c_int, _dp]),
+    "ch_droplets_run": (_c_int, [_c_int, _c_int, _dp, _c_dbl, _c_int, _dp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64,
+                                 _dp, _i64p, _vp]),
     "ch_server_create": (_c_int, [ctypes.c_size_t, _c_int, _c_int, ctypes.POINTER(_vp)]),
     "ch_submit": (_c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "ch_poll": (_c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result)]),
@@ -334,6 +337,22 @@ def ch_ensemble_refinement_error(fine_h, fine_member, coarse_h, coarse_member):
     out = ctypes.c_double()
     _check(lib().ch_ensemble_refinement_error(fine_h, fine_member, coarse_h, coarse_member, ctypes.byref(out)))
     return out.value
+
+
+def ch_droplets_run(R0, t_end, t_samples, rtol=1e-6, atol=1e-9, h0=1e-6, eps=1e-3, max_steps=10 ** 9,
+                    stream_ptr=None):
+    """Model 1 populations R0 (M, N) to t_end on the GPU: (R(t_end) (M, N), samples
+    (M, len(t_samples), 5): t, F, dF/dt, beta, live droplets; steps (M, 3))."""
+    R = np.array(R0, dtype=np.float64, order="C", copy=True)
+    if R.ndim != 2:
+        raise ValueError("R0 must be (M, N)")
+    M, N = R.shape
+    ts = np.ascontiguousarray(t_samples, dtype=np.float64)
+    series = np.zeros((M, max(ts.size, 1), 5))
+    steps = np.zeros((M, 3), dtype=np.int64)
+    _check(lib().ch_droplets_run(M, N, _ptr(R), t_end, ts.size, _ptr(ts), rtol, atol, h0, eps, max_steps,
+                                 _ptr(series), steps.ctypes.data_as(_i64p), stream_ptr))
+    return R, series[:, : ts.size].copy(), steps
 
 
 def ch_get_field(h, member):
