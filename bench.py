@@ -18,6 +18,8 @@ Reported:
   roofline       the dominant kernel against its bound (FP64 pipe for the FP64 path).
   ensemble_stats moments, histograms and trend statistics of beta across runs: kernel
                  times on a paper-size synthetic ensemble and the workload's own values.
+  droplets       Model 1: 100 droplet populations of 512 to t = 40 (adaptive Dormand-Prince
+                 on the GPU) and their Table 2 statistics.
   refinement     the Appendix-A grid-refinement study (E_n and observed order) up to
                  --refinement-nmax points per axis.
   cpu_baseline   the FP64 CPU oracle timed on this host's cores (bounded sample).
@@ -472,6 +474,8 @@ def main():
     ap.add_argument("--campaign", action="store_true",
                     help="also run the paper's L = 2 pi campaign ensemble (1024 x 256^2 to t = 100, FP32; "
                          "about 75 s of GPU time) and report its Table 4 statistics")
+    ap.add_argument("--no-droplets", action="store_true",
+                    help="skip the Model 1 leg (100 populations of 512 droplets to t = 40, about 10 s)")
     ap.add_argument("--refinement-nmax", type=int, default=1024,
                     help="largest grid of the Appendix-A refinement study leg (0: skip)")
     ap.add_argument("--long-beta", action="store_true",
@@ -620,6 +624,12 @@ def main():
         refine = {"workload": wl.REFINEMENT["name"], "gamma": wl.REFINEMENT["gamma"], "T": wl.REFINEMENT["T"],
                   "dt": "0.1 dx", "precision": "fp64", "rows": refinement.study(sizes)}
 
+    drops = None
+    if not args.no_droplets and rank == 0:
+        # Model 1 (Secs. 2-3): Table 1's M = 100 populations, N = 512, t to 40, with the
+        # window mean of mu_1 over [20, 40] and k of mu_2 = k t over [0, 40] (Table 2)
+        from paper_1911_03386_gb300 import droplets
+        drops = droplets.run(512)
     camp = None
     if args.campaign and rank == 0:
         from paper_1911_03386_gb300 import campaign
@@ -706,7 +716,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_line,
             "gpu_launches": r64["launches"], "clocks": r64["clocks"], "fp32": fp32,
             "beta_avg": beta_stats(avg64), "serving": serving, "batches": batches, "ensemble_stats": stats,
-            "refinement": refine, "campaign": camp,
+            "refinement": refine, "campaign": camp, "droplets": drops,
             "kernel_source": kernel_source_hash()}
     print(json.dumps(finite_or_none(line), allow_nan=False), flush=True)
     if dist:

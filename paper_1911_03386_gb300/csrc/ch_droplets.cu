@@ -28,6 +28,12 @@
 // (divisions above all), so the right-hand side takes one division, q = 1/R, and forms
 // q (u - q) = -1/R^2 + u/R.
 //
+// Working set: a population of up to kSmemDroplets droplets keeps its working arrays (R,
+// k_1..k_7, stage values, indices: 80 bytes a droplet) in shared memory, where a stage's
+// loads, stores and reductions cost tens of cycles instead of an L2 round trip each;
+// larger populations keep them in global memory (L2-resident).  The code is the same for
+// both (generic pointers).
+//
 // The step loop is bounded by max_steps; a population that reaches it, or whose step
 // size underflows, stops with a status code.
 #include <algorithm>
@@ -43,6 +49,8 @@
 namespace chd {
 
 constexpr int kMaxThreads = 1024;
+constexpr int kBytesPerDroplet = 9 * 8 + 2 * 4;             // R, k_1..k_7, stage value; two indices
+constexpr int kSmemDroplets = (227 * 1024 - 1024) / kBytesPerDroplet;  // 2892
 
 // Dormand-Prince nodes and weights (row s: weights of stages 1..s-1 for stage s; row 7 is
 // the fifth-order solution), and the embedded fourth-order weights.
@@ -71,6 +79,7 @@ struct View {
   int64_t max_steps;
   double* series;   // [M][ns][5] t, F, dF/dt, beta, live droplets
   int64_t* stats;   // [M][3] accepted, rejected, status (0 ok, 1 step limit, 2 step underflow)
+  int smem;         // 1: working arrays in dynamic shared memory (N <= kSmemDroplets)
 };
 
 // Sum of two values over the CTA, returned to every thread (fixed order).
@@ -188,13 +197,24 @@ __device__ void sample(const double* R, int N, double t, double* row, double2* r
 __global__ void __launch_bounds__(kMaxThreads) drop_kernel(View v) {
   __shared__ double2 red[kMaxThreads / 32];
   __shared__ int wsum[kMaxThreads / 32];
+  extern __shared__ __align__(16) double dsm[];
   const int m = blockIdx.x, N = v.N;
   double* Rout = v.R + (size_t)m * N;
-  double* R = v.Rc + (size_t)m * N;
-  int* idx = v.idx + (size_t)m * N;
-  int* idx2 = v.idx2 + (size_t)m * N;
-  double* K = v.K + (size_t)m * 7 * N;
-  double* Y = v.Y + (size_t)m * N;
+  double *R, *K, *Y;
+  int *idx, *idx2;
+  if (v.smem) {
+    R = dsm;
+    K = R + N;
+    Y = K + 7 * (size_t)N;
+    idx = reinterpret_cast<int*>(Y + N);
+    idx2 = idx + N;
+  } else {
+    R = v.Rc + (size_t)m * N;
+    K = v.K + (size_t)m * 7 * N;
+    Y = v.Y + (size_t)m * N;
+    idx = v.idx + (size_t)m * N;
+    idx2 = v.idx2 + (size_t)m * N;
+  }
   double* series = v.series ? v.series + (size_t)m * v.ns * 5 : nullptr;
   const double eps = v.eps, rtol = v.rtol, atol = v.atol;
 
@@ -345,8 +365,14 @@ int ch_droplets_run(int M, int N, double* R, double t_end, int nsamples, const d
     e = cudaMemsetAsync(v.series, 0xff, sizeof(double) * 5 * (size_t)M * nsamples, st);  // NaN until sampled
   if (e == cudaSuccess) {
     const int threads = N >= chd::kMaxThreads ? chd::kMaxThreads : ((N + 31) / 32) * 32;
-    chd::drop_kernel<<<M, threads, 0, st>>>(v);
-    e = cudaGetLastError();
+    v.smem = N <= chd::kSmemDroplets ? 1 : 0;
+    const size_t smem = v.smem ? (size_t)N * chd::kBytesPerDroplet : 0;
+    if (smem > 48 * 1024)
+      e = cudaFuncSetAttribute(chd::drop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      chd::drop_kernel<<<M, threads, smem, st>>>(v);
+      e = cudaGetLastError();
+    }
   }
   std::vector<int64_t> hst(3 * (size_t)M);
   if (e == cudaSuccess) e = cudaMemcpyAsync(R, v.R, sizeof(double) * nR, cudaMemcpyDeviceToHost, st);

@@ -33,7 +33,7 @@ def orc():
     return get_oracle()
 
 
-@pytest.mark.parametrize("M,N", [(3, 37), (2, 1), (1, 1500)])
+@pytest.mark.parametrize("M,N", [(3, 37), (2, 1), (1, 1500), (2, 3000)])  # 3000: global working arrays
 def test_fixed_steps_match_oracle(orc, M, N):
     rng = np.random.default_rng(N)
     R0 = 0.5 + 0.5 * rng.random((M, N))  # no extinction before t = 0.05
