@@ -38,7 +38,9 @@ def max_over_ranks(x, dist=None, device="cpu"):
 
 
 def gather_members(values, dist=None, device="cpu"):
-    """Concatenate every rank's per-member array (equal lengths), rank order."""
+    """Concatenate every rank's per-member array (equal shapes) along the member axis
+    (axis 0), rank order: per-member scalars, or per-member sample series (members x T)
+    whose ensemble moments are then taken over all ranks' members."""
     values = np.asarray(values, dtype=np.float64)
     if dist is None or not dist.is_initialized():
         return values

@@ -67,6 +67,37 @@ def test_two_gloo_ranks_gather_like_one_process(tmp_path):
         np.testing.assert_array_equal(np.load(tmp_path / ("all%d.npy" % r)), allb)
 
 
+def fake_series(rank, T=9):
+    """A rank's beta series (its members x T sample times), the input of the ensemble
+    moments of Sec. 3.3 Eqs. (41a,b) when the members are spread over ranks."""
+    rng = np.random.default_rng(300 + rank)
+    return 0.3 + 0.05 * rng.standard_normal((M_PER_RANK, T))
+
+
+def _series_worker(rank, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=WORLD)
+    allser = replicas.gather_members(fake_series(rank), dist)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "series.npy"), allser)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_series_gathered_over_ranks_give_the_ensemble_moments(tmp_path):
+    """Per-rank beta series gathered (rank order, members stacked) equal the series of the
+    whole ensemble, so the moments across members over all ranks are those of one process."""
+    from oracle.oracle import get as get_oracle
+
+    tmp.spawn(_series_worker, args=(_free_port(), str(tmp_path)), nprocs=WORLD, join=True)
+    got = np.load(tmp_path / "series.npy")
+    whole = np.concatenate([fake_series(r) for r in range(WORLD)], axis=0)
+    np.testing.assert_array_equal(got, whole)
+    orc = get_oracle()
+    np.testing.assert_array_equal(orc.beta_moments(got), orc.beta_moments(whole))
+
+
 def test_member_ranges_and_counter_bases():
     for m in [1, 5, 256, 1001]:
         for world in [1, 2, 3, 8]:
