@@ -197,6 +197,7 @@ __device__ void sample(const double* R, int N, double t, double* row, double2* r
 __global__ void __launch_bounds__(kMaxThreads) drop_kernel(View v) {
   __shared__ double2 red[kMaxThreads / 32];
   __shared__ int wsum[kMaxThreads / 32];
+  __shared__ double s_ctl[2];  // accept flag, next step size (written by thread 0)
   extern __shared__ __align__(16) double dsm[];
   const int m = blockIdx.x, N = v.N;
   double* Rout = v.R + (size_t)m * N;
@@ -277,8 +278,25 @@ __global__ void __launch_bounds__(kMaxThreads) drop_kernel(View v) {
         e2 += q * q;
       }
     }
-    const double en = rtol > 0.0 ? sqrt(block_sum(e2, 0.0, red).x / (double)N) : 0.0;
-    const bool accept = rtol <= 0.0 || en <= 1.0;
+    // the step controller runs on one thread (pow and sqrt are long FP64 sequences) and
+    // its decision is broadcast through shared memory
+    const double e2sum = rtol > 0.0 ? block_sum(e2, 0.0, red).x : 0.0;
+    if (threadIdx.x == 0) {
+      const double en = rtol > 0.0 ? sqrt(e2sum / (double)N) : 0.0;
+      const bool ok = rtol <= 0.0 || en <= 1.0;
+      double hn = h;
+      if (rtol > 0.0) {
+        double fac = en > 0.0 ? 0.9 * pow(en, -0.2) : 5.0;
+        fac = fmin(5.0, fmax(0.2, fac));
+        if (!ok) fac = fmin(fac, 1.0);
+        hn = hs * fac;
+      }
+      s_ctl[0] = ok ? 1.0 : 0.0;
+      s_ctl[1] = hn;
+    }
+    __syncthreads();
+    const bool accept = s_ctl[0] != 0.0;
+    h = s_ctl[1];
     if (accept) {
       const double* K7 = K + (size_t)6 * N;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -290,12 +308,6 @@ __global__ void __launch_bounds__(kMaxThreads) drop_kernel(View v) {
       if ((acc & 255) == 0) tidy = true;
     } else {
       ++rej;
-    }
-    if (rtol > 0.0) {
-      double fac = en > 0.0 ? 0.9 * pow(en, -0.2) : 5.0;
-      fac = fmin(5.0, fmax(0.2, fac));
-      if (!accept) fac = fmin(fac, 1.0);
-      h = hs * fac;
     }
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) Rout[idx[i]] = R[i];
