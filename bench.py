@@ -33,6 +33,7 @@ import multiprocessing as mp
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -111,8 +112,11 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index) if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/ch_clocks_%d_%d.csv" % (os.getpid(), index)
+        # the raw samples go to $CH_CLOCK_LOG_DIR when set (kept beside the run's outputs),
+        # else to a temporary file; the JSON line carries their summary either way
+        log_dir = os.environ.get("CH_CLOCK_LOG_DIR")
+        self.path = (os.path.join(log_dir, "clocks_rank%d.csv" % index) if log_dir and os.path.isdir(log_dir)
+                     else os.path.join(tempfile.gettempdir(), "ch_clocks_%d_%d.csv" % (os.getpid(), index)))
 
     def __enter__(self):
         try:
