@@ -95,9 +95,17 @@ def cpu_baseline(pool, p, cores, target_s=12.0):
     per_step = wall1 / 2
     nsteps = max(2, int(target_s / max(per_step, 1e-6)))
     pts, wall, _ = oracle_sample(pool, p, cores, nsteps)
-    return {"value": pts / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d members x %d steps of %dx%d (one member per process, FP64, single-threaded C "
-                      "oracle), %.1f s wall" % (cores, nsteps, p["nx"], p["ny"], wall)}
+    out = {"value": pts / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d members x %d steps of %dx%d (one member per process, FP64, single-threaded C "
+                     "oracle), %.1f s wall" % (cores, nsteps, p["nx"], p["ny"], wall)}
+    # the 64^2 single-run workload in full (2000 steps, one core)
+    from paper_1911_03386_gb300 import workloads as wl
+    s = wl.SINGLE_64
+    job = (s["nx"], s["ny"], s["L"], s["gamma"], s["dt"], s["C0"][0], wl.BASE_SEED, 0, s["steps"], None)
+    w = pool.apply(_oracle_worker, (job,))[0]
+    out["single_64_full"] = {"workload": s["name"], "time_steps": s["steps"], "wall_s": w, "cores": 1,
+                             "value": s["nx"] * s["ny"] * s["steps"] / w, "unit": UNIT}
+    return out
 
 
 # ------------------------------------------------------------------------------------------
