@@ -43,8 +43,19 @@ if ROOT not in sys.path:
 METRIC = "CH grid-point-steps/s per GB300 (FP32 vs FP64 path); served p50/p99 latency"
 UNIT = "grid-point-steps/s"
 STEPS_PER_BENCH_STEP = 100
-FP64_PIPE_PEAK = 1.25e12  # FLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
-HBM_PEAK = 6694.5e9       # B/s, MEASURED_PEAKS.json hbm_gbs
+FP64_PIPE_PEAK = 1.25e12  # FLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal; replaced by the measured rate)
+
+
+def _hbm_peak():
+    """Measured HBM copy bandwidth (B/s) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]) * 1e9, "measured hbm_gbs (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6.8e12, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+HBM_PEAK, HBM_PEAK_SOURCE = _hbm_peak()
 # Algorithmic work per grid point of one time step, per kernel (flop, field words moved):
 #   stencil  mu (9) + R' (6) flop; read C, write R'
 #   rowsweep forward/backward row recurrences (8); read R', write W
@@ -459,6 +470,74 @@ def run_serving_leg(ch, torch, n_requests, rate, seed, precision, budget_bytes=8
     return out
 
 
+def run_peak_leg(ch, torch):
+    """FMA throughput of the FP64 and FP32 pipes (ch_fma_peak), CUDA-event timed on one
+    stream over about a second of work each, with the SM clock sampled meanwhile: the
+    denominators of the FP64 path's "alu" roofline and of the on-chip FP32 kernels."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = torch.cuda.Stream()
+    out = {"sms": sms}
+    for prec, name, iters in ((ch.CH_FP64, "fp64", 400), (ch.CH_FP32, "fp32", 20000)):
+        blocks, threads, reps = 2 * sms, 1024, 40
+        for _ in range(2):
+            ch.ch_fma_peak(prec, blocks, threads, iters, sink.data_ptr(), st.cuda_stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            a.record(st)
+            flops = 0.0
+            for _ in range(reps):
+                flops += ch.ch_fma_peak(prec, blocks, threads, iters, sink.data_ptr(), st.cuda_stream)
+            b.record(st)
+            torch.cuda.synchronize()
+        s_ = a.elapsed_time(b) * 1e-3
+        c = clk.summary()
+        rate = flops / s_
+        r = {"flops_per_s": rate, "tflops": rate / 1e12, "seconds": s_, "clocks": c}
+        if c.get("sm_mhz"):
+            # FMAs per SM per clock at the sampled median clock (2 flop per FMA)
+            r["fma_per_sm_per_clk"] = rate / 2 / (sms * c["sm_mhz"] * 1e6)
+            r["at_max_clock_tflops"] = rate / 1e12 * c["sm_max_mhz"] / c["sm_mhz"]
+        out[name] = r
+    return out
+
+
+def run_beta_check(ch, torch, p):
+    """<beta> acceptance of the FP32 form on the workload itself: the whole horizon (20 000
+    steps, t = 20) in FP64 and FP32 from the same start, the window average of beta per
+    run (t >= t1), then per C0 group the mean and standard error over the runs and
+    whether |mean_32 - mean_64| <= SE_64 (within one standard error)."""
+    from paper_1911_03386_gb300 import workloads as wl
+    descs = [dict(nx=p["nx"], ny=p["ny"], L=p["L"], gamma=p["gamma"], dt=p["dt"], C0=c0, seed=wl.BASE_SEED,
+                  counter_base=k * p["nx"] * p["ny"]) for k, c0 in enumerate(p["C0"])]
+    labels = list(p["C0"])
+    res = {"workload": p["name"], "time_steps": p["steps"], "sample_every": p["every"], "window_t1": p["t1"],
+           "window": [p["t1"], p["steps"] * p["dt"]]}
+    stats = {}
+    for prec, name in ((ch.CH_FP64, "fp64"), (ch.CH_FP32, "fp32")):
+        stream = torch.cuda.Stream()
+        with ch.Ensemble.batch(descs, prec) as e:
+            e.set_stream(stream.cuda_stream)
+            e.set_sampling(p["every"], p["t1"], capacity=0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            e.step(p["steps"])
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            avg, cnt = e.beta_avg()
+        stats[name] = replicas_stats(avg, labels)
+        res[name] = {"seconds": ms * 1e-3, "value": len(descs) * p["nx"] * p["ny"] * p["steps"] / (ms * 1e-3),
+                     "unit": UNIT, "samples_in_window": int(min(cnt)), "beta_avg": stats[name]}
+    res["within_one_se"] = {k: abs(stats["fp32"][k]["mean"] - stats["fp64"][k]["mean"]) <= stats["fp64"][k]["se"]
+                            for k in stats["fp64"]}
+    res["diff_in_se"] = {k: abs(stats["fp32"][k]["mean"] - stats["fp64"][k]["mean"]) / stats["fp64"][k]["se"]
+                         for k in stats["fp64"]}
+    return res
+
+
 def replicas_stats(values, labels):
     """Mean, standard error and count of the window-averaged beta per initial mean C0."""
     from paper_1911_03386_gb300 import replicas
@@ -490,6 +569,9 @@ def main():
                     help="skip the Model 1 leg (100 populations of 512 droplets to t = 40, about 10 s)")
     ap.add_argument("--refinement-nmax", type=int, default=1024,
                     help="largest grid of the Appendix-A refinement study leg (0: skip)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA-throughput measurement")
+    ap.add_argument("--no-beta-check", action="store_true",
+                    help="skip the whole-horizon <beta> check of the FP32 form against FP64 (about 20 s)")
     ap.add_argument("--long-beta", action="store_true",
                     help="also run the 32 x 1024^2 coarsening ensemble over its whole horizon in both precisions "
                          "and compare <beta> (minutes of GPU time)")
@@ -546,6 +628,8 @@ def main():
     r64 = run_gpu_leg(ch, torch, p, ch.CH_FP64, K, W, rank, world, dist)
     r32 = None if args.no_fp32 else run_gpu_leg(ch, torch, p, ch.CH_FP32, K, W, rank, world, dist)
     e2e = None if args.no_e2e else run_e2e_leg(ch, torch, p, ch.CH_FP64, K, rank, dist)
+    peaks = None if args.no_peaks else run_peak_leg(ch, torch)
+    beta_check = None if (args.no_beta_check or rank != 0) else run_beta_check(ch, torch, p)
     serving = None
     if not args.no_serving and rank == 0:
         # the serving workload's own rate, then a rate the measured capacity sustains
@@ -698,19 +782,29 @@ def main():
         step_ms = sum(ks.values())
         if bound == "alu":
             ach = flops * npts / (ks[dom] * 1e-3)
-            rl = {"bound": "alu", "kernel": tname, "achieved": ach / 1e12, "peak": FP64_PIPE_PEAK / 1e12,
-                  "unit": "TFLOP/s", "frac": ach / FP64_PIPE_PEAK,
-                  "peak_source": "FP64 pipe, nominal 1.25 TFLOP/s of the recipe (152 SMs x 2 DFMA/clk x 2.07 GHz); "
-                                 "no measured FP64 peak in MEASURED_PEAKS.json"}
+            if peaks is not None:
+                pk = peaks["fp64"]["flops_per_s"]
+                src = ("measured: FP64 FMA throughput of this run (ch_fma_peak, %d CTAs x 1024 threads, CUDA events), "
+                       "the burst rate of a kernel timed alone" % peaks["fp64"].get("blocks", 2 * peaks["sms"]))
+            else:
+                pk = FP64_PIPE_PEAK
+                src = "nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz); FMA probe skipped"
+            rl = {"bound": "alu", "kernel": tname, "achieved": ach / 1e12, "peak": pk / 1e12,
+                  "unit": "TFLOP/s", "frac": ach / pk, "peak_source": src}
         else:
             ach = words * elt * npts / (ks[dom] * 1e-3)
             rl = {"bound": "hbm", "kernel": tname, "achieved": ach / 1e9, "peak": HBM_PEAK / 1e9, "unit": "GB/s",
-                  "frac": ach / HBM_PEAK, "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)"}
+                  "frac": ach / HBM_PEAK, "peak_source": HBM_PEAK_SOURCE}
         rl["traffic"] = ncu_traffic(tname, p["name"])
         rl["algorithmic_per_point"] = {"flop": flops, "bytes": words * elt}
         rl["per_kernel"] = per_launch
         rl["step_ms_sum_of_kernels"] = step_ms
-        rl["step_frac_of_16B_per_point"] = 2 * 2 * elt * npts / (step_ms * 1e-3) / HBM_PEAK
+        # the whole step against the HBM bound of any factorised ADI step: 2 reads + 2 writes
+        # of a field word per point (16 B FP32, 32 B FP64)
+        rl["fused_step_hbm"] = {"step_ms": step_ms, "algorithmic_bytes_per_point": 4 * elt,
+                                "achieved_gbs": 4 * elt * npts / (step_ms * 1e-3) / 1e9,
+                                "frac": 4 * elt * npts / (step_ms * 1e-3) / HBM_PEAK, "peak_gbs": HBM_PEAK / 1e9,
+                                "peak_source": HBM_PEAK_SOURCE}
         return rl
 
     roofline = kernel_roofline(r64, "alu", 8)
@@ -728,7 +822,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e_line,
             "gpu_launches": r64["launches"], "clocks": r64["clocks"], "fp32": fp32,
             "beta_avg": beta_stats(avg64), "serving": serving, "batches": batches, "ensemble_stats": stats,
-            "refinement": refine, "campaign": camp, "droplets": drops,
+            "refinement": refine, "campaign": camp, "droplets": drops, "peaks": peaks, "beta_check": beta_check,
             "kernel_source": kernel_source_hash()}
     print(json.dumps(finite_or_none(line), allow_nan=False), flush=True)
     if dist:

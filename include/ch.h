@@ -165,8 +165,10 @@ int ch_get_fields(ch_handle h, double* out);
  * 13-point stencil (observables on sample steps), fused with the row sweep in the fused
  * form; phase 1 = the row sweep in the split form (nothing in the fused form); phase 2 =
  * the column kernel (column sweep, update, sample finalisation, step counter).  Phases 0,
- * 1, 2 in order are exactly one ch_step(h, 1); they exist separately so callers can time
- * each kernel with events on the stream.  Errors: CH_EINVAL (phase), CH_ECUDA.
+ * 1, 2 in order are exactly one ch_step(h, 1) of every member outside the cluster-resident
+ * form (ch_tuning.resident), whose members the phases leave unchanged; they exist
+ * separately so callers can time each kernel with events on the stream.
+ * Errors: CH_EINVAL (phase), CH_ECUDA.
  */
 int ch_launch_phase(ch_handle h, int phase);
 
@@ -224,6 +226,16 @@ int ch_launch_phase(ch_handle h, int phase);
  *               else S = 16 in one CTA, else S = 32, else 16 over a CTA pair, else panels
  *               or streaming (CH_FP64 split form: streaming for every member); -1 = panels
  *               or streaming.
+ *   resident    cluster-resident form of CH_FP32 members with nx = 128 or 256 and
+ *               ny = 32 Q, Q = 1 .. 8: the member's field stays in the shared memory of a
+ *               cluster of Q CTAs (32 rows each, two halo rows per side) for a launch of
+ *               up to 4096 steps; the row recurrences are segment scans across 16 lanes
+ *               per row, the column recurrences combine their segment end states through
+ *               distributed shared memory, and neighbouring CTAs exchange halo rows by
+ *               remote shared-memory stores.  HBM then moves the field once per launch
+ *               instead of five words per point and step.  The phase launches
+ *               (ch_launch_phase, ch_debug_row_solve) do not touch such members.
+ *               0 or 1 = on for every member that fits (default), -1 = off.
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
  * size, lines too long for shared memory, a row_seg that some member's nx does not fit).
@@ -240,6 +252,7 @@ typedef struct {
   int persist;
   int row_seg;
   int col_seg;
+  int resident;
 } ch_tuning;
 int ch_set_tuning(ch_handle h, const ch_tuning* t); /* NULL restores the defaults */
 int ch_get_tuning(ch_handle h, ch_tuning* t);       /* shape in effect (member 0's values) */
@@ -314,14 +327,19 @@ int ch_seg_tables(double s, int seg, int groups, double* out);
  * until the process exits.  So nx*ny must be <= 1,048,576 (e.g. 1024 x 1024); larger
  * grids are rejected with CH_EINVAL and a message in ch_last_error().
  *
- * The first call on each device (with that device current) looks up the array's device
- * address (cudaGetSymbolAddress) and sets the kernels' shared-memory limits; make that
- * first call before any stream capture.  All calls on a device share the array, which
- * keeps the last call's contents; every step overwrites all of W before reading it, so
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, which allocates nothing) and sets the kernels' shared-memory
+ * limits, so a device reset or a switch to another context between calls is safe.  The
+ * first call on a device also loads the library's kernels there: make it before any
+ * stream capture on that device.  All calls on a device share the array, which keeps
+ * the last call's contents; every step overwrites all of W before reading it, so
  * nothing needs clearing.  Calls whose work overlaps on the GPU (other streams, other
  * host threads) race on the array: serialise them.
  * Errors: CH_EINVAL (NULL C, nx or ny < 5, nx*ny above the limit, L/gamma/dt not finite
- * and > 0, nsteps < 0), CH_ECUDA (set-up or launch failed).
+ * and > 0, nsteps < 0), CH_ECUDA (set-up or launch failed).  Launch errors are read
+ * without clearing the CUDA error state, so an error the caller left pending also gives
+ * CH_ECUDA (and stays pending).  After CH_ECUDA the field may have advanced by fewer than
+ * nsteps steps: the steps enqueued before the failure still run.
  */
 int ch_step_field_noalloc(double* C, int nx, int ny, double L, double gamma, double dt, int64_t nsteps,
                           void* stream);
@@ -502,6 +520,18 @@ int ch_server_wait(ch_server s, uint64_t id, double timeout_s, ch_result* out);
 int ch_server_stats(ch_server s, ch_server_stats_t* out);
 /* Stop the worker (runs in flight are abandoned) and release everything. */
 void ch_server_destroy(ch_server s);
+
+/*
+ * Measured fused multiply-add throughput (a measurement aid; the paper has no
+ * counterpart).  Enqueues on `stream` one kernel of `blocks` CTAs x `threads` threads
+ * (a multiple of 32, at most 1024) in which every thread runs 8 independent chains of
+ * 16 x iters FMAs in FP64 (precision CH_FP64) or FP32 (CH_FP32), with no memory traffic,
+ * and sets *flops (host) to the floating-point operations it performs (2 per FMA).  The
+ * caller times it (e.g. with CUDA events on `stream`) to get the pipe's peak rate.  `sink`
+ * is a device double the kernel never writes in practice (it keeps the work live).
+ * Errors: CH_EINVAL (shape, iters < 1, NULL pointer, precision), CH_ECUDA (launch).
+ */
+int ch_fma_peak(int precision, int blocks, int threads, int64_t iters, double* sink, void* stream, double* flops);
 
 /* Message of the last failure on this host thread ("" if none). */
 const char* ch_last_error(void);

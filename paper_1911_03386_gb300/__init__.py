@@ -82,7 +82,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("split", ctypes.c_int), ("rows_band", ctypes.c_int), ("rows_p", ctypes.c_int),
                 ("sweep_band", ctypes.c_int), ("cols_panel", ctypes.c_int), ("cols_p", ctypes.c_int),
                 ("threads", ctypes.c_int), ("stream", ctypes.c_int), ("persist", ctypes.c_int),
-                ("row_seg", ctypes.c_int), ("col_seg", ctypes.c_int)]
+                ("row_seg", ctypes.c_int), ("col_seg", ctypes.c_int), ("resident", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -138,6 +138,7 @@ _SIGS = {
     "ch_server_wait": (_c_int, [_vp, ctypes.c_uint64, _c_dbl, ctypes.POINTER(Result)]),
     "ch_server_stats": (_c_int, [_vp, ctypes.POINTER(ServerStats)]),
     "ch_server_destroy": (None, [_vp]),
+    "ch_fma_peak": (_c_int, [_c_int, _c_int, _c_int, _c_i64, _vp, _vp, _dp]),
     "ch_last_error": (ctypes.c_char_p, []),
     "ch_version": (ctypes.c_char_p, []),
 }
@@ -204,6 +205,13 @@ def ch_step_field_noalloc(C_ptr, nx, ny, L, gamma, dt, nsteps, stream_ptr=None):
     """Advance a caller-owned FP64 device field (address C_ptr) by nsteps steps without
     allocating anything (scratch in a static 8 MiB device array; nx*ny <= 1048576)."""
     _check(lib().ch_step_field_noalloc(C_ptr, nx, ny, L, gamma, dt, nsteps, stream_ptr or None))
+
+
+def ch_fma_peak(precision, blocks, threads, iters, sink_ptr, stream_ptr=None):
+    """Enqueue the FMA-throughput kernel (see include/ch.h); returns the flops it performs."""
+    flops = ctypes.c_double()
+    _check(lib().ch_fma_peak(precision, blocks, threads, iters, sink_ptr, stream_ptr or None, ctypes.byref(flops)))
+    return flops.value
 
 
 def ch_create_ensemble(nx, ny, L, gamma, dt, C0, seed, precision=CH_FP64):
@@ -388,8 +396,9 @@ def ch_launch_phase(h, phase):
 
 
 def ch_set_tuning(h, split=-1, rows_band=0, rows_p=0, sweep_band=0, cols_panel=0, cols_p=0, threads=0, stream=-1,
-                  persist=-1, row_seg=0, col_seg=0):
-    t = Tuning(split, rows_band, rows_p, sweep_band, cols_panel, cols_p, threads, stream, persist, row_seg, col_seg)
+                  persist=-1, row_seg=0, col_seg=0, resident=0):
+    t = Tuning(split, rows_band, rows_p, sweep_band, cols_panel, cols_p, threads, stream, persist, row_seg, col_seg,
+               resident)
     _check(lib().ch_set_tuning(h, ctypes.byref(t)))
 
 

@@ -165,6 +165,46 @@ void seg_tables(double p1, double p2, int S, int G, chk::SegTable* t) {
   for (int i = 0; i < 4; ++i) t->Pf[i] = (float)t->P[i];
 }
 
+// Closed-form segment responses of the recurrence y_i = r_i + p1 y_{i-1} + p2 y_{i-2} over
+// S <= 32 points (see SegTable::Hf), computed in FP64 and rounded to FP32.
+void seg_responses(double p1, double p2, int S, chk::SegTable* t) {
+  double h[2][32], g[2][32], k[2][32];
+  for (int j = 0; j < 2; ++j) {
+    // forward homogeneous response to (y_-1, y_-2) = e_j
+    double y1 = j == 0 ? 1.0 : 0.0, y2 = j == 0 ? 0.0 : 1.0;
+    for (int i = 0; i < S; ++i) {
+      const double yi = p1 * y1 + p2 * y2;
+      h[j][i] = yi;
+      y2 = y1;
+      y1 = yi;
+    }
+    // its backward pass from a zero state
+    double x1 = 0.0, x2 = 0.0;
+    for (int i = S - 1; i >= 0; --i) {
+      const double xi = h[j][i] + p1 * x1 + p2 * x2;
+      g[j][i] = xi;
+      x2 = x1;
+      x1 = xi;
+    }
+    // backward homogeneous response to (x_S, x_S+1) = e_j
+    x1 = j == 0 ? 1.0 : 0.0;
+    x2 = j == 0 ? 0.0 : 1.0;
+    for (int i = S - 1; i >= 0; --i) {
+      const double xi = p1 * x1 + p2 * x2;
+      k[j][i] = xi;
+      x2 = x1;
+      x1 = xi;
+    }
+  }
+  for (int u = 0; u < 32; ++u) {
+    const bool in = u < S;
+    t->Hf[u][0] = in ? (float)g[0][u] : 0.f;
+    t->Hf[u][1] = in ? (float)g[1][u] : 0.f;
+    t->Hf[u][2] = in ? (float)k[0][u] : 0.f;
+    t->Hf[u][3] = in ? (float)k[1][u] : 0.f;
+  }
+}
+
 bool is_pow2_upto32(int g) { return g >= 1 && g <= 32 && (g & (g - 1)) == 0; }
 
 }  // namespace chh
@@ -192,6 +232,7 @@ void free_device(ch_ensemble* h) {
   cudaFree(h->drt);
   cudaFree(h->dst);
   cudaFree(h->dct);
+  cudaFree(h->dres);
   cudaFree(h->dpart);
   cudaFree(h->dseries);
   cudaFree(h->dobs);
@@ -201,8 +242,8 @@ void free_device(ch_ensemble* h) {
   h->dseg = h->dsegy = nullptr;
   h->dcst = nullptr;
   h->cap_cst = 0;
-  h->drt = h->dst = h->dct = nullptr;
-  h->cap_rt = h->cap_st = h->cap_ct = h->cap_part = 0;
+  h->drt = h->dst = h->dct = h->dres = nullptr;
+  h->cap_rt = h->cap_st = h->cap_ct = h->cap_part = h->cap_res = 0;
   h->dpart = nullptr;
   h->dseries = h->dobs = nullptr;
 }
@@ -379,9 +420,14 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   };
   // class index of a segment-form member's columns: S = 16, 32 in one CTA, then over pairs
   auto col_index = [&](const MemberParams& p, int S) { return (S == 32 ? 1 : 0) + (col_pair(p, S) ? 2 : 0); };
+  // cluster-resident form (FP32): nx = 128 or 256, ny = 32 Q with Q <= 8 CTAs per cluster
+  auto resident = [&](const MemberParams& p) {
+    return !f64 && t.resident >= 0 && (p.nx == 128 || p.nx == 256) && p.ny % 32 == 0 && p.ny >= 32 &&
+           p.ny <= 256;
+  };
   int cwarps[4] = {8, 8, max_wp, max_wp};  // warps per CTA of each class
   for (int k = 0; k < h->m; ++k) {
-    if (!h->has(k)) continue;
+    if (!h->has(k) || resident(h->hp[k])) continue;
     const MemberParams& p = h->hp[k];
     if (t.row_seg == 1 && !split && !rowT_fits(p))
       return fail(CH_EINVAL, "row_seg 1: some member's nx is not 32 times at most 16");
@@ -394,6 +440,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   }
 
   std::vector<Tile> rts[3], csts[4], sts[3], ct;  // rows: S = 16, S = 32, chunked; columns: 4 classes
+  std::vector<Tile> rcl[chk::kResClasses];        // cluster-resident members by class
   std::vector<Tile> rtb;                          // stencil blocks of long rows (last)
   std::vector<Tile> rtT[17];                   // rows, transposed-block form, by nw
   chk::LaunchShape sh{};
@@ -408,6 +455,20 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     if (!h->has(k)) {
       p.nbands = 0;
       p.partial_base = part;
+      continue;
+    }
+    if (resident(p)) {
+      // one tile per member; one partial slot per CTA of its cluster.  Scan tables: rows
+      // of 16 segments of nx / 16 points, columns of ny / (nx / 8) segments of nx / 8
+      const int Q = p.ny / 32;
+      rcl[chk::res_class(p.nx, p.comp, Q)].push_back(Tile{k, 0, p.ny, 0, 0, 0});
+      p.seg_g = p.row_t = p.col_s = 0;
+      p.nbands = Q;
+      p.partial_base = part;
+      part += Q;
+      seg_tables(p.p1x, p.p2x, p.nx / 16, 16, &h->hseg[k]);
+      seg_tables(p.p1y, p.p2y, p.nx / 8, p.ny / (p.nx / 8), &h->hsegy[k]);
+      seg_responses(p.p1y, p.p2y, p.nx / 8, &h->hsegy[k]);
       continue;
     }
     const int rc = row_class(p), cc = col_class(p), ri = rc == 16 ? 0 : rc == 32 ? 1 : 2;
@@ -532,9 +593,15 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   sh.rt_blk = (int)rtb.size();
   rt.insert(rt.end(), rtb.begin(), rtb.end());
   for (int c = 0; c < 4; ++c) cst.insert(cst.end(), csts[c].begin(), csts[c].end());
+  std::vector<Tile> rest;
+  for (int c = 0; c < chk::kResClasses; ++c) {
+    sh.res_n[c] = (int)rcl[c].size();
+    rest.insert(rest.end(), rcl[c].begin(), rcl[c].end());
+  }
   sh.n_row_tiles = (int)rt.size();
   sh.n_sweep_tiles = (int)st.size();
   sh.n_col_tiles = (int)ct.size();
+  h->rest.swap(rest);
   h->rt.swap(rt);
   h->st.swap(st);
   h->ct.swap(ct);
@@ -563,6 +630,7 @@ int upload_tiles(ch_ensemble* h) {
       (e = ensure((void**)&h->dst, h->cap_st, h->st.size(), sizeof(Tile))) != cudaSuccess ||
       (e = ensure((void**)&h->dct, h->cap_ct, h->ct.size(), sizeof(Tile))) != cudaSuccess ||
       (e = ensure((void**)&h->dcst, h->cap_cst, h->cst.size(), sizeof(Tile))) != cudaSuccess ||
+      (e = ensure((void**)&h->dres, h->cap_res, h->rest.size(), sizeof(Tile))) != cudaSuccess ||
       (e = ensure((void**)&h->dpart, h->cap_part, (size_t)h->total_bands, sizeof(double2))) != cudaSuccess) {
     cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? CH_ENOMEM : CH_ECUDA, std::string("tile tables: ") + cudaGetErrorString(e));
@@ -576,12 +644,16 @@ int upload_tiles(ch_ensemble* h) {
           "upload member parameters");
   int n_rowT = 0;
   for (int nw = 1; nw <= 16; ++nw) n_rowT += h->shape.rtT_n[nw];
-  if (h->shape.rt_seg[0] + h->shape.rt_seg[1] + h->shape.st_seg[0] + h->shape.st_seg[1] + n_rowT)
+  if (!h->rest.empty())
+    CH_CUDA(cudaMemcpyAsync(h->dres, h->rest.data(), sizeof(Tile) * h->rest.size(), cudaMemcpyHostToDevice, h->stream),
+            "tiles");
+  if (h->shape.rt_seg[0] + h->shape.rt_seg[1] + h->shape.st_seg[0] + h->shape.st_seg[1] + n_rowT + h->rest.size())
     CH_CUDA(cudaMemcpyAsync(h->dseg, h->hseg.data(), sizeof(chk::SegTable) * h->m, cudaMemcpyHostToDevice, h->stream),
             "upload scan tables");
-  if (!h->cst.empty()) {
+  if (!h->cst.empty())
     CH_CUDA(cudaMemcpyAsync(h->dcst, h->cst.data(), sizeof(Tile) * h->cst.size(), cudaMemcpyHostToDevice, h->stream),
             "tiles");
+  if (!h->cst.empty() || !h->rest.empty()) {
     CH_CUDA(cudaMemcpyAsync(h->dsegy, h->hsegy.data(), sizeof(chk::SegTable) * h->m, cudaMemcpyHostToDevice,
                             h->stream),
             "upload scan tables");
@@ -699,13 +771,20 @@ int check_member(ch_handle h, int member) {
   return CH_OK;
 }
 
-int launch_steps_direct(ch_ensemble* h, int64_t n) {
+// n single steps of the tiled kernels (every member outside the cluster-resident form).
+int launch_tiled_direct(ch_ensemble* h, int64_t n) {
   const chk::DevView v = h->view();
+  if (h->shape.n_row_tiles == 0) return CH_OK;
   for (int64_t i = 0; i < n; ++i) {
     cudaError_t e = chk::launch_step(v, h->precision, h->shape, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
   }
   return CH_OK;
+}
+
+int launch_steps_direct(ch_ensemble* h, int64_t n) {
+  CH_CUDA(chk::launch_resident(h->view(), h->precision, h->shape, n, h->stream), "resident step launch");
+  return launch_tiled_direct(h, n);
 }
 
 int ensure_graph(ch_ensemble* h) {
@@ -752,6 +831,7 @@ ch_tuning default_tuning() {
   t.persist = -1;
   t.row_seg = 0;
   t.col_seg = 0;
+  t.resident = 0;
   return t;
 }
 
@@ -847,6 +927,10 @@ int ch_step(ch_handle h, int64_t nsteps) {
   if (nsteps < 0) return fail(CH_EINVAL, "nsteps must be >= 0");
   // The legacy default stream cannot be captured: launch directly there.
   const bool can_graph = h->stream != nullptr && h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
+  // cluster-resident members first (their own launches of many steps each), then the
+  // other members' single steps, replayed from a captured graph where possible
+  CH_CUDA(chk::launch_resident(h->view(), h->precision, h->shape, nsteps, h->stream), "resident step launch");
+  if (h->shape.n_row_tiles == 0) return CH_OK;
   int64_t left = nsteps;
   if (can_graph && left >= kGraphSteps) {
     if (int rc = ensure_graph(h)) return rc;
@@ -855,7 +939,7 @@ int ch_step(ch_handle h, int64_t nsteps) {
       left -= h->graph_steps;
     }
   }
-  return launch_steps_direct(h, left);
+  return launch_tiled_direct(h, left);
 }
 
 int ch_synchronize(ch_handle h) {
@@ -1037,6 +1121,7 @@ int ch_set_tuning(ch_handle h, const ch_tuning* t) {
     return fail(CH_EINVAL, "row_seg must be -1, 0, 1, 16 or 32");
   if (req.col_seg != -1 && req.col_seg != 0 && req.col_seg != 16 && req.col_seg != 32)
     return fail(CH_EINVAL, "col_seg must be -1, 0, 16 or 32");
+  if (req.resident < -1 || req.resident > 1) return fail(CH_EINVAL, "resident must be -1, 0 or 1");
   CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
   const std::vector<MemberParams> saved = h->hp;
   const ch_tuning old = h->tuning;
@@ -1065,6 +1150,9 @@ int ch_get_tuning(ch_handle h, ch_tuning* t) {
   // kernel classes of member 0
   t->row_seg = h->hp[0].row_t ? 1 : (h->hp[0].seg_g ? h->hp[0].nx / h->hp[0].seg_g : (h->shape.split ? 0 : -1));
   t->col_seg = h->hp[0].col_s ? h->hp[0].col_s : -1;
+  t->resident = h->rest.empty() ? -1 : 1;
+  for (const Tile& r : h->rest)
+    if (r.member == 0) t->row_seg = t->col_seg = 0;  // member 0 runs in the resident form
   return CH_OK;
 }
 
@@ -1100,6 +1188,10 @@ int ch_member_shape(ch_handle h, int member, int* nx, int* ny) {
 int ch_debug_row_solve(ch_handle h, int member, double* out) {
   if (int rc = check_member(h, member)) return rc;
   if (!out) return fail(CH_EINVAL, "out is NULL");
+  for (const Tile& r : h->rest)
+    if (r.member == member)
+      return fail(CH_EINVAL, "member runs in the cluster-resident form: its row solve has no phase of its own "
+                             "(set_tuning resident = -1 to use the tiled kernels)");
   // phases 0 and 1 only touch W, the band partials and the members' active flags
   CH_CUDA(chk::launch_phase(h->view(), h->precision, 0, h->shape, h->stream), "row phase");
   CH_CUDA(chk::launch_phase(h->view(), h->precision, 1, h->shape, h->stream), "row phase");

@@ -27,6 +27,7 @@ struct ch_ensemble {
   std::vector<chk::SegTable> hsegy; // scan tables of the segment column kernel, per member
   std::vector<Tile> cst;            // CTAs of the segment column kernel
   std::vector<Tile> rt, st, ct;   // stencil/fused bands, row-sweep bands, column panels
+  std::vector<Tile> rest;         // members of the cluster-resident form (FP32), by class
   chk::LaunchShape shape{};
   ch_tuning tuning{};             // as requested (0 / -1 = default)
   int64_t total_points = 0, max_points = 0;
@@ -47,7 +48,8 @@ struct ch_ensemble {
   Tile* drt = nullptr;
   Tile* dst = nullptr;
   Tile* dct = nullptr;
-  size_t cap_rt = 0, cap_st = 0, cap_ct = 0, cap_part = 0;  // device array capacities
+  Tile* dres = nullptr;
+  size_t cap_rt = 0, cap_st = 0, cap_ct = 0, cap_part = 0, cap_res = 0;  // device array capacities
   double2* dpart = nullptr;
   double* dseries = nullptr;
   double* dobs = nullptr;
@@ -74,6 +76,7 @@ struct ch_ensemble {
     v.seg = dseg;
     v.segy = dsegy;
     v.colseg_tiles = dcst;
+    v.res_tiles = dres;
     v.m = m;
     return v;
   }
@@ -100,6 +103,8 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t);
 // Upload tile tables, partial slots and member parameters (synchronises the stream).
 int upload_tiles(ch_ensemble* h);
 void drop_graph(ch_ensemble* h);
+// n steps of every member: the cluster-resident members' launches, then n single steps
+// of the tiled kernels.
 int launch_steps_direct(ch_ensemble* h, int64_t n);
 int copy_out(ch_ensemble* h, void* dst, const void* src, size_t bytes, const char* what);
 int read_states(ch_ensemble* h, std::vector<MemberState>& s);

@@ -67,6 +67,13 @@ struct SegTable {
   float Af[5][4];        // the same rounded to FP32
   float Bf[64][4];
   float Pf[4];
+  // Closed-form responses of one segment of S <= 32 points (cluster-resident column
+  // kernel), FP32: Hf[u] = (g1_u, g2_u, k1_u, k2_u) where, on a segment with start states
+  // s = (y_-1, y_-2) of the forward and t = (x_S, x_S+1) of the backward recurrence,
+  // x_u = G0(F0(r))_u + g1_u s_0 + g2_u s_1 + k1_u t_0 + k2_u t_1 (F0, G0: the forward and
+  // backward recurrences from zero states; g = G0 of the forward homogeneous responses,
+  // k = the backward homogeneous responses).
+  float Hf[32][4];
 };
 
 struct MemberState {
@@ -102,8 +109,17 @@ struct DevView {
   const SegTable* seg;   // [m] scan tables (segment form of the row sweep)
   const SegTable* segy;  // [m] scan tables of the y recurrence (segment form of the column kernel)
   const Tile* colseg_tiles;  // CTAs of the segment-form column kernel
+  const Tile* res_tiles;     // one per member of the cluster-resident form (FP32)
   int m;
 };
+
+// Cluster-resident form (FP32): a member with nx = 128 or 256 and ny = 32 Q, Q = 1 .. 8,
+// is stepped by a cluster of Q CTAs that keep its field in shared memory for a whole
+// chunk of steps.  Its tiles are ordered by class (nx, compensated, Q):
+// class index = ((nx == 256) * 2 + comp) * 8 + Q - 1.
+constexpr int kResClasses = 32;
+constexpr int64_t kResChunk = 4096;  // steps per launch of the resident kernel
+inline int res_class(int nx, int comp, int Q) { return ((nx == 256 ? 2 : 0) + (comp ? 1 : 0)) * 8 + Q - 1; }
 
 // Launch shapes chosen on the host per handle (see ch_api.cu).
 struct LaunchShape {
@@ -140,6 +156,8 @@ struct LaunchShape {
   int cst_n[4];
   int colseg_threads[4];
   size_t colseg_smem[4];
+  // cluster-resident members (FP32): tiles per class (see res_class)
+  int res_n[kResClasses];
 };
 
 // Kernel launchers (ch_kernels.cu).  Each returns the launch status.
@@ -151,6 +169,11 @@ cudaError_t launch_init_members(const DevView& v, int precision, const int* list
 cudaError_t launch_step(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st);
 cudaError_t launch_phase(const DevView& v, int precision, int phase, const LaunchShape& sh, cudaStream_t st);
 cudaError_t launch_observe(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st);
+// nsteps steps of every cluster-resident member (no-op when there are none), in launches
+// of at most kResChunk steps.
+cudaError_t launch_resident(const DevView& v, int precision, const LaunchShape& sh, int64_t nsteps, cudaStream_t st);
+// Dynamic shared memory of the cluster-resident kernel for rows of nx floats.
+size_t resident_smem_bytes(int nx, int comp);
 cudaError_t set_kernel_smem_limits(int precision);
 // Resident CTAs per SM of the column kernel for a launch shape (0 on error).
 int cols_blocks_per_sm(int precision, int persist, int threads, size_t smem);

@@ -534,18 +534,12 @@ __device__ __forceinline__ double* red_buffer(unsigned char* smem, size_t tile_b
   return reinterpret_cast<double*>(smem + ((tile_bytes + 15) & ~(size_t)15));
 }
 
-// Sample finalisation of one member (called once per member and step by the column phase,
-// after the stencil phase wrote the band partials): F, dF/dt, beta, series, window
-// average; then the step counter and horizon advance.
-__device__ __forceinline__ void finalize_sample(const DevView& v, int member, MemberState* st, const MemberParams& P) {
+// The sample itself from the member's summed partials (sF, sD): F, dF/dt, beta, the series
+// ring and the window average; then the step counter and horizon advance.
+__device__ __forceinline__ void finalize_sums(const DevView& v, int member, MemberState* st, const MemberParams& P,
+                                              double sF, double sD) {
   const int64_t n = st->step;
   if (n % P.every == 0) {
-    double sF = 0.0, sD = 0.0;
-    for (int b = 0; b < P.nbands; ++b) {
-      const double2 pr = v.partials[P.partial_base + b];
-      sF += pr.x;
-      sD += pr.y;
-    }
     const double hh = P.hx * P.hy;
     const double F = hh * sF;
     const double dFdt = -(hh * sD);
@@ -570,6 +564,21 @@ __device__ __forceinline__ void finalize_sample(const DevView& v, int member, Me
   }
   st->step = n + 1;
   if (st->remaining != kUnbounded) st->remaining -= 1;
+}
+
+// Sample finalisation of one member (called once per member and step by the column phase,
+// after the stencil phase wrote the band partials): the partials summed in band order, then
+// finalize_sums.
+__device__ __forceinline__ void finalize_sample(const DevView& v, int member, MemberState* st, const MemberParams& P) {
+  double sF = 0.0, sD = 0.0;
+  if (st->step % P.every == 0) {
+    for (int b = 0; b < P.nbands; ++b) {
+      const double2 pr = v.partials[P.partial_base + b];
+      sF += pr.x;
+      sD += pr.y;
+    }
+  }
+  finalize_sums(v, member, st, P, sF, sD);
 }
 
 // -------------------------------------------------------------------------------------
@@ -1749,6 +1758,439 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(sizeof(T) == 4 ? 102
 }
 
 // -------------------------------------------------------------------------------------
+// Cluster-resident form (FP32).  A member with nx = 128 or 256 and ny = 32 Q (Q <= 8)
+// keeps its whole field in the shared memory of a cluster of Q CTAs for a chunk of steps:
+// CTA q holds rows 32q .. 32q+31 plus two halo rows on each side, so HBM sees one load and
+// one store of the field per launch instead of five words per point and step.  One step:
+//   mu      34 rows (own rows and one halo row each side) from the C tile, 4 points per
+//           thread, into the mu/W tile;
+//   rows    R' in registers, both row recurrences as segment scans across 16 lanes per
+//           row (S = nx / 16 points per lane), W back into the mu/W tile;
+//   columns a thread owns SC = nx / 8 rows of one column: the forward recurrence from a
+//           zero state over its W, then the backward recurrence from a zero state over that
+//           result; both end states go to shared memory, and after the step's only cluster
+//           barrier every thread combines the end states of all segments of its column in
+//           recurrence order (read through distributed shared memory), which gives every
+//           segment's forward start state s_k and backward start state t_k.  The solution
+//           is then closed-form, x = G0(F0(W)) + g s_k + k t_k with the segment responses
+//           g, k (SegTable::Hf), except the two first and two last rows of a segment, which
+//           are taken from the combination (t_{k-1}, and the first two backward steps from
+//           t_k over s_{k+1}).  Every CTA computes the same s_k, t_k with the same
+//           operations, so it updates its halo rows -- its neighbours' boundary rows --
+//           itself, bit for bit as the neighbours update them: no halo exchange.
+// The end states are double-buffered by step parity (a CTA may start the next step while
+// others still read this step's).  Sample steps add the FP64 partial sums of the F and
+// dF/dt densities (mu recomputed in FP64 from the stored field, as in the other FP32
+// kernels); rank 0 sums the CTAs' partials in rank order and finalises the sample.  mu and
+// R' are formed in the operation order of the segment-form kernels.
+// -------------------------------------------------------------------------------------
+constexpr int kResRows = 32;      // rows of the field per CTA
+constexpr int kResThreads = 256;  // threads per CTA
+#ifndef CH_RES_MIN_BLOCKS
+#define CH_RES_MIN_BLOCKS 2
+#endif
+// CTAs per SM the register budget is sized for (two plain 256-column CTAs fit the shared
+// memory of an SM)
+constexpr int kResMinBlocks = CH_RES_MIN_BLOCKS;
+
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// Four FP32 values from distributed shared memory.  No memory clobber: the loads of a
+// combination are issued back to back and wait only where their values are used (the
+// cluster barrier before them carries the ordering).
+__device__ __forceinline__ float4 ld_peer4(unsigned addr) {
+  float4 x;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w)
+               : "r"(addr));
+  return x;
+}
+
+__device__ __forceinline__ void st_peer2d(unsigned addr, double2 x) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(x.x), "d"(x.y) : "memory");
+}
+
+// Element (r, i) of the mu/W tile (pitch NX floats).  The 16-byte quad of column i is
+// XOR-ed with bits 3..5 of its quad index: the row phase's 16-byte reads of 16 lanes S
+// points apart, the mu phase's consecutive quads and the column phase's consecutive
+// columns all fall in distinct banks.
+template <int NX>
+__device__ __forceinline__ int res_swz(int r, int i) {
+  const int q = i >> 2;
+  return r * NX + (((q ^ ((q >> 3) & 7)) << 2) | (i & 3));
+}
+
+// 2 x 2 matrix (row-major, 4 floats) times a state.
+__device__ __forceinline__ float2 mat2v(const float* A, float2 v) {
+  return make_float2(fmaf(A[0], v.x, A[1] * v.y), fmaf(A[2], v.x, A[3] * v.y));
+}
+__device__ __forceinline__ float2 mat2v_add(const float* A, float2 v, float2 w) {
+  return make_float2(fmaf(A[0], v.x, fmaf(A[1], v.y, w.x)), fmaf(A[2], v.x, fmaf(A[3], v.y, w.y)));
+}
+
+// FP64 partial sums of the F and dF/dt densities over the CTA's own rows (C tile rows
+// 2 .. 33; hi + lo for compensated members), mu recomputed in FP64 from the stored field.
+// Thread = column i of a block of 32 NX / 256 rows, walking down with three field rows in
+// registers; x neighbours by shuffles (lanes hold consecutive columns), the ends of a warp's
+// run loaded.  Fixed work split and order.  Result in thread 0.
+template <int NX, bool COMP>
+__device__ __forceinline__ void res_partials(const float* Ct, const float* Lt, const MemberParams& P, double* red,
+                                             double& sF, double& sD) {
+  constexpr int RB = kResRows * NX / kResThreads;  // rows per thread
+  const int lane = threadIdx.x & 31;
+  const int i = threadIdx.x % NX, r0 = (threadIdx.x / NX) * RB;
+  const int ie = i + 1 == NX ? 0 : i + 1, iw = i == 0 ? NX - 1 : i - 1, iee = ie + 1 == NX ? 0 : ie + 1;
+  const double a = P.a, bx = P.bx, by = P.by;
+  auto at = [&](int r, int ii) {  // own row r (-2 .. 33) at column ii, in FP64
+    const int k = (r + 2) * NX + ii;
+    return COMP ? (double)Ct[k] + (double)Lt[k] : (double)Ct[k];
+  };
+  auto mu_of = [&](double c, double e, double w, double n, double s) {
+    return c * (c * c - a) - bx * (e + w) - by * (n + s);
+  };
+  // west / east neighbours of the field at row r (value cv of this lane's column)
+  auto nbrs = [&](double cv, int r, double& w, double& e) {
+    w = __shfl_up_sync(kFull, cv, 1);
+    e = __shfl_down_sync(kFull, cv, 1);
+    if (lane == 0) w = at(r, iw);
+    if (lane == 31) e = at(r, ie);
+  };
+  double sw = 0.0, sdx = 0.0, sdy = 0.0, smx = 0.0, smy = 0.0;
+  double cm = at(r0 - 1, i), c0 = at(r0, i), c1 = at(r0 + 1, i);
+  double w0, e0;
+  nbrs(c0, r0, w0, e0);
+  double mu0 = mu_of(c0, e0, w0, c1, cm);
+  for (int r = r0; r < r0 + RB; ++r) {
+    const double c2 = at(r + 2, i);
+    double w1, e1;
+    nbrs(c1, r + 1, w1, e1);
+    const double mu1 = mu_of(c1, e1, w1, c2, c0);
+    double mue = __shfl_down_sync(kFull, mu0, 1);
+    if (lane == 31) mue = mu_of(e0, at(r, iee), c0, at(r + 1, ie), at(r - 1, ie));
+    const double w = c0 * c0 - 1.0, gx = e0 - c0, gy = c1 - c0, mx = mue - mu0, my = mu1 - mu0;
+    sw += w * w;
+    sdx += gx * gx;
+    sdy += gy * gy;
+    smx += mx * mx;
+    smy += my * my;
+    cm = c0;
+    c0 = c1;
+    c1 = c2;
+    e0 = e1;
+    mu0 = mu1;
+  }
+  (void)cm;
+  const double hxi2 = 1.0 / (P.hx * P.hx), hyi2 = 1.0 / (P.hy * P.hy);
+  sF = 0.25 * sw + 0.5 * P.gamma * (hxi2 * sdx + hyi2 * sdy);
+  sD = hxi2 * smx + hyi2 * smy;
+  block_sum2(sF, sD, red);
+}
+
+// Shared memory of the resident kernel (bytes): C tile (and lo tile), mu/W tile, the
+// column end states (two step parities), the scan tables, the FP64 reduction buffer, the
+// per-rank partial slots (two step parities) and the member's state (rank 0).
+constexpr int kResConsts = 288;  // row A, P (24); column A, P (8); row B (16 x 4); column B (16 x 4); H (32 x 4)
+__host__ __device__ constexpr size_t res_smem_bytes(int nx, bool comp) {
+  return (size_t)((comp ? 2 : 1) * (kResRows + 4) + (kResRows + 2)) * nx * sizeof(float) +
+         (size_t)2 * kResThreads * sizeof(float4) + kResConsts * sizeof(float) + 16 * sizeof(double) +
+         16 * sizeof(double2) + (sizeof(MemberState) + 15) / 16 * 16;
+}
+
+template <int NX, bool COMP, bool OBS>
+__global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView v, int tile_base, int64_t nsteps) {
+  constexpr int S = NX / 16;                       // row points per lane
+  constexpr int SC = kResRows * NX / kResThreads;  // column points per thread
+  constexpr int NSEG = kResRows / SC;              // column segments per CTA
+  constexpr int KMAX = 8 * NSEG;                   // column segments at most (Q <= 8)
+  constexpr int NQ = NX / 4;                       // 16-byte quads per row
+  constexpr int CT = kResRows + 4, MT = kResRows + 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Ct = reinterpret_cast<float*>(smem);
+  float* Lt = Ct + CT * NX;
+  float* Mw = Lt + (COMP ? CT * NX : 0);
+  float4* xs = reinterpret_cast<float4*>(Mw + MT * NX);  // [2][kResThreads]
+  float* Ks = reinterpret_cast<float*>(xs + 2 * kResThreads);  // see kResConsts
+  double* red = reinterpret_cast<double*>(Ks + kResConsts);
+  double2* part = reinterpret_cast<double2*>(red + 16);  // [2][8]: by step parity, then rank
+  MemberState* lst = reinterpret_cast<MemberState*>(part + 16);
+
+  const unsigned Q = cluster_size(), rank = cluster_rank();
+  const Tile tl = v.res_tiles[tile_base + blockIdx.x / Q];
+  const int m = tl.member;
+  const MemberParams& P = v.mp[m];
+  MemberState* st = v.ms + m;
+  const int ny = P.ny, j0 = (int)rank * kResRows;
+  const int tid = threadIdx.x, lane = tid & 31;
+  float* __restrict__ Cg = static_cast<float*>(v.C) + P.offset;
+  float* __restrict__ Lg = COMP ? static_cast<float*>(v.C) + P.lo_offset : nullptr;
+
+  // the steps of this launch, read before any CTA of the cluster changes the state (rank 0
+  // writes it back only at the end)
+  const int64_t n0 = st->step, rem = st->remaining;
+  const int64_t nrun = OBS ? 0 : (rem < nsteps ? rem : nsteps);
+  if (!OBS && nrun <= 0) return;  // the same decision in every CTA of the cluster
+
+  // C (and lo) rows j0 - 2 .. j0 + 33, periodic
+  for (int k = tid; k < CT * NQ; k += kResThreads) {
+    const int r = k / NQ, q = k - r * NQ;
+    int j = j0 - 2 + r;
+    j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
+    reinterpret_cast<float4*>(Ct + r * NX)[q] = reinterpret_cast<const float4*>(Cg + (int64_t)j * NX)[q];
+    if (COMP) reinterpret_cast<float4*>(Lt + r * NX)[q] = reinterpret_cast<const float4*>(Lg + (int64_t)j * NX)[q];
+  }
+  if (OBS) {
+    __syncthreads();
+    double sF, sD;
+    res_partials<NX, COMP>(Ct, Lt, P, red, sF, sD);
+    if (tid == 0) v.partials[P.partial_base + rank] = make_double2(sF, sD);
+    return;
+  }
+  // column phase: column c, rows g SC .. g SC + SC - 1 of this CTA = segment gs of ns
+  const int c = tid % NX, g = tid / NX;
+  const int ns = (int)Q * NSEG, gs = (int)rank * NSEG + g;
+  {
+    const SegTable& tx = v.seg[m];
+    const SegTable& ty = v.segy[m];
+    for (int k = tid; k < kResConsts; k += kResThreads) {
+      float x = 0.f;
+      if (k < 20)
+        x = tx.Af[k >> 2][k & 3];
+      else if (k < 24)
+        x = tx.Pf[k - 20];
+      else if (k < 28)
+        x = ty.Af[0][k - 24];
+      else if (k < 32)
+        x = ty.Pf[k - 28];
+      else if (k < 96)
+        x = tx.Bf[(k - 32) >> 2][k & 3];
+      else if (k < 160)
+        x = (k - 96) >> 2 < ns ? ty.Bf[(k - 96) >> 2][k & 3] : 0.f;
+      else
+        x = ty.Hf[(k - 160) >> 2][k & 3];
+      Ks[k] = x;
+    }
+  }
+  const float* KB = Ks + 32;   // row start-state matrices M^(S l), l = 0 .. 15
+  const float* KC = Ks + 96;   // column powers M^(SC k), k = 0 .. ns - 1
+  const float* KH = Ks + 160;  // column segment responses (g1, g2, k1, k2) per row
+  // row phase: 16 lanes per row, rows grp and grp + 16
+  const int l = tid & 15, grp = tid >> 4;
+  const float a = P.fa, bx = P.fbx, by = P.fby, rho = P.frho, w0 = P.fw0;
+  const float p1x = P.fp1x, p2x = P.fp2x, p1y = P.fp1y, p2y = P.fp2y, kap = P.fkappa;
+  // the member's state lives in shared memory of rank 0 for the launch
+  const bool keeper = rank == 0 && tid == 0;
+  if (keeper) *lst = *st;
+  cluster_sync();  // every CTA of the cluster runs and has its tile and constants
+
+  for (int64_t s = 0; s < nrun; ++s) {
+    const bool sample = ((n0 + s) % P.every) == 0;
+    if (sample) {
+      double sF, sD;
+      res_partials<NX, COMP>(Ct, Lt, P, red, sF, sD);
+      if (tid == 0) st_peer2d(peer_addr(part + 8 * (s & 1) + rank, 0), make_double2(sF, sD));
+    }
+    // mu of own rows -1 .. 32 (tile row r + 1 of C) into mu/W tile row r
+    {
+      const int q = tid % NQ;
+      for (int r = tid / NQ; r < MT; r += kResThreads / NQ) {  // warp-uniform (NQ >= 32)
+        const float* c0 = Ct + (r + 1) * NX;
+        float cc[4], nn[4], so[4];
+        ld4(c0 + 4 * q, cc);
+        ld4(c0 - NX + 4 * q, nn);
+        ld4(c0 + NX + 4 * q, so);
+        float w = __shfl_up_sync(kFull, cc[3], 1), e = __shfl_down_sync(kFull, cc[0], 1);
+        if (lane == 0) w = c0[q == 0 ? NX - 1 : 4 * q - 1];
+        if (lane == 31) e = c0[q == NQ - 1 ? 0 : 4 * q + 4];
+        float out[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float ce = k < 3 ? cc[k + 1] : e;
+          const float cw = k > 0 ? cc[k - 1] : w;
+          const float u = cc[k] * fmaf(cc[k], cc[k], -a);
+          out[k] = fmaf(-by, so[k] + nn[k], fmaf(-bx, ce + cw, u));
+        }
+        st4(Mw + res_swz<NX>(r, 4 * q), out);
+      }
+    }
+    __syncthreads();
+    // R' and the row recurrences of own rows grp, grp + 16 (mu/W tile rows + 1)
+    {
+      float y[2][S];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int r = grp + 16 * t + 1;
+#pragma unroll
+        for (int k = 0; k < S / 4; ++k) ld4(Mw + res_swz<NX>(r, l * S + 4 * k), &y[t][4 * k]);
+        const float left = __shfl_sync(kFull, y[t][S - 1], (l + 15) & 15, 16);
+        const float right = __shfl_sync(kFull, y[t][0], (l + 1) & 15, 16);
+        float prv = left;
+#pragma unroll
+        for (int k = 0; k < S / 4; ++k) {
+          float up[4], dn[4];
+          ld4(Mw + res_swz<NX>(r - 1, l * S + 4 * k), up);
+          ld4(Mw + res_swz<NX>(r + 1, l * S + 4 * k), dn);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int u = 4 * k + q;
+            const float cur = y[t][u];
+            const float e = u + 1 < S ? y[t][u + 1] : right;
+            y[t][u] = fmaf(w0, cur, fmaf(rho, dn[q] + up[q], e + prv));
+            prv = cur;
+          }
+        }
+      }
+      {
+        float B[4];
+        ld4(KB + 4 * l, B);
+        seg_sweep<float, S, 2, false>(y, p1x, p2x, l, 16, 4, Ks, B);
+        ld4(KB + 4 * (15 - l), B);
+        seg_sweep<float, S, 2, true>(y, p1x, p2x, l, 16, 4, Ks, B);
+      }
+      __syncthreads();  // every mu read of this step is done: W replaces mu
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int k = 0; k < S / 4; ++k) st4(Mw + res_swz<NX>(grp + 16 * t + 1, l * S + 4 * k), &y[t][4 * k]);
+    }
+    __syncthreads();
+    // columns
+    {
+      float4* xsb = xs + (s & 1) * kResThreads;
+      float y[SC];
+#pragma unroll
+      for (int u = 0; u < SC; ++u) y[u] = Mw[res_swz<NX>(g * SC + u + 1, c)];
+      // forward recurrence from a zero state, then the backward one over its result
+      float fa = 0.f, fb = 0.f;
+#pragma unroll
+      for (int u = 0; u < SC; ++u) {
+        const float t = fmaf(p1y, fa, fmaf(p2y, fb, y[u]));
+        y[u] = t;
+        fb = fa;
+        fa = t;
+      }
+      float ba = 0.f, bb = 0.f;
+#pragma unroll
+      for (int u = SC - 1; u >= 0; --u) {
+        const float t = fmaf(p1y, ba, fmaf(p2y, bb, y[u]));
+        y[u] = t;
+        bb = ba;
+        ba = t;
+      }
+      xsb[tid] = make_float4(fa, fb, ba, bb);  // (y_SC-1, y_SC-2), (x_0, x_1)
+      cluster_sync();
+      if (keeper) {
+        // the sample (partials of every CTA, summed in rank order) and the step counter
+        double sF = 0.0, sD = 0.0;
+        if (sample)
+          for (unsigned k = 0; k < Q; ++k) {
+            sF += part[8 * (s & 1) + k].x;
+            sD += part[8 * (s & 1) + k].y;
+          }
+        finalize_sums(v, m, lst, P, sF, sD);
+      }
+      // the end states of the column's ns segments (k in recurrence order of the forward
+      // pass), then the combination -- the same operations in every thread of the column
+      float4 E[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        if (k < ns) {
+          const unsigned owner = (unsigned)(k / NSEG);
+          const int slot = (k - (int)owner * NSEG) * NX + c;
+          E[k] = owner == rank ? xsb[slot] : ld_peer4(peer_addr(xsb + slot, owner));
+        }
+      }
+      const float* A = Ks + 24;  // M^SC: one segment, either direction
+      const float* PP = Ks + 28; // (I - M^ny)^-1
+      const float Eb[4] = {KH[0], KH[1], KH[4], KH[5]};  // (x_0, x_1) per unit start state s
+      // forward: the total from zero, the periodic start x0, then s_k = M^(SC k) x0 + Y_k-1;
+      // backward end states with their true start: e_k + Eb s_k (kept in E[k].z, .w)
+      float2 Y = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < ns) Y = mat2v_add(A, Y, make_float2(E[k].x, E[k].y));
+      const float2 x0 = mat2v(PP, Y);
+      float2 s_own = x0, s_next = x0;
+      Y = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        if (k < ns) {
+          const float2 sk = mat2v_add(KC + 4 * k, x0, Y);
+          if (k == gs) s_own = sk;
+          if (k == (gs + 1 == ns ? 0 : gs + 1)) s_next = sk;
+          const float2 eb = mat2v_add(Eb, sk, make_float2(E[k].z, E[k].w));
+          E[k].z = eb.x;
+          E[k].w = eb.y;
+          Y = mat2v_add(A, Y, make_float2(E[k].x, E[k].y));
+        }
+      }
+      // backward, segments from the last: the total, the periodic start of the last
+      // segment, then t_k = M^(SC (ns-1-k)) t_last + Z_k+1
+      // (k runs down from KMAX - 1 so that E is indexed by constants and stays in registers)
+      float2 Z = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = KMAX - 1; k >= 0; --k)
+        if (k < ns) Z = mat2v_add(A, Z, make_float2(E[k].z, E[k].w));
+      const float2 tl0 = mat2v(PP, Z);
+      float2 t_own = tl0, t_prev = tl0;
+      Z = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = KMAX - 1; k >= 0; --k) {
+        if (k < ns) {
+          const float2 tk = mat2v_add(KC + 4 * (ns - 1 - k), tl0, Z);
+          if (k == gs) t_own = tk;
+          if (k == (gs == 0 ? ns - 1 : gs - 1)) t_prev = tk;
+          Z = mat2v_add(A, Z, make_float2(E[k].z, E[k].w));
+        }
+      }
+      // the solution of this segment: closed form inside, the combination at its ends
+#pragma unroll
+      for (int u = 2; u < SC - 2; ++u) {
+        float H[4];
+        ld4(KH + 4 * u, H);
+        y[u] = fmaf(H[3], t_own.y, fmaf(H[2], t_own.x, fmaf(H[1], s_own.y, fmaf(H[0], s_own.x, y[u]))));
+      }
+      y[0] = t_prev.x;
+      y[1] = t_prev.y;
+      y[SC - 1] = fmaf(p1y, t_own.x, fmaf(p2y, t_own.y, s_next.x));
+      y[SC - 2] = fmaf(p1y, y[SC - 1], fmaf(p2y, t_own.x, s_next.y));
+#pragma unroll
+      for (int u = 0; u < SC; ++u) {
+        const int k = (g * SC + u + 2) * NX + c;
+        Ct[k] = c_update<float>(Ct[k], kap, y[u], COMP ? Lt + k : nullptr);
+      }
+      // halo rows: the previous segment's last two rows (above the first segment of this
+      // CTA) and the next segment's first two rows (below the last), as their owners
+      // compute them
+      if (g == 0) {
+        const float h1 = fmaf(p1y, t_prev.x, fmaf(p2y, t_prev.y, s_own.x));
+        const float h0 = fmaf(p1y, h1, fmaf(p2y, t_prev.x, s_own.y));
+        Ct[NX + c] = c_update<float>(Ct[NX + c], kap, h1, COMP ? Lt + NX + c : nullptr);
+        Ct[c] = c_update<float>(Ct[c], kap, h0, COMP ? Lt + c : nullptr);
+      }
+      if (g == NSEG - 1) {
+        const int k34 = (kResRows + 2) * NX + c, k35 = k34 + NX;
+        Ct[k34] = c_update<float>(Ct[k34], kap, t_own.x, COMP ? Lt + k34 : nullptr);
+        Ct[k35] = c_update<float>(Ct[k35], kap, t_own.y, COMP ? Lt + k35 : nullptr);
+      }
+    }
+    __syncthreads();
+  }
+  cluster_sync();  // no CTA leaves while others may still read its end states
+  if (keeper) *st = *lst;
+  // own rows back to HBM
+  for (int k = tid; k < kResRows * NQ; k += kResThreads) {
+    const int r = k / NQ, q = k - r * NQ;
+    reinterpret_cast<float4*>(Cg + (int64_t)(j0 + r) * NX)[q] = reinterpret_cast<const float4*>(Ct + (r + 2) * NX)[q];
+    if (COMP)
+      reinterpret_cast<float4*>(Lg + (int64_t)(j0 + r) * NX)[q] = reinterpret_cast<const float4*>(Lt + (r + 2) * NX)[q];
+  }
+}
+
+// -------------------------------------------------------------------------------------
 // Streaming sweeps (split form).  Lines are not held on chip: each warp owns 32 lines (one
 // per lane) and streams them, so the number of recurrences in flight per SM is bounded by
 // registers rather than by shared memory.  The intermediate y of the two-pass solve lives
@@ -2053,6 +2495,51 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
   return cudaGetLastError();
 }
 
+// One launch of the resident kernel over the n tiles of one class (clusters of Q CTAs).
+template <int NX, bool COMP, bool OBS>
+cudaError_t res_launch(const DevView& v, int base, int n, int Q, int64_t nsteps, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n * Q), 1, 1);
+  cfg.blockDim = dim3(kResThreads, 1, 1);
+  cfg.dynamicSmemBytes = res_smem_bytes(NX, COMP);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)Q;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, res_kernel<NX, COMP, OBS>, v, base, nsteps);
+}
+
+template <bool OBS>
+cudaError_t res_all(const DevView& v, const LaunchShape& sh, int64_t nsteps, cudaStream_t st) {
+  int base = 0;
+  for (int ci = 0; ci < kResClasses; ++ci) {
+    const int n = sh.res_n[ci];
+    if (n <= 0) continue;
+    const int Q = ci % 8 + 1;
+    const bool comp = (ci / 8) & 1, wide = ci >= 16;
+    cudaError_t e;
+    if (wide)
+      e = comp ? res_launch<256, true, OBS>(v, base, n, Q, nsteps, st) : res_launch<256, false, OBS>(v, base, n, Q, nsteps, st);
+    else
+      e = comp ? res_launch<128, true, OBS>(v, base, n, Q, nsteps, st) : res_launch<128, false, OBS>(v, base, n, Q, nsteps, st);
+    if (e != cudaSuccess) return e;
+    base += n;
+  }
+  return cudaSuccess;
+}
+
+template <int NX, bool COMP>
+cudaError_t res_smem_limit() {
+  const int b = (int)res_smem_bytes(NX, COMP);
+  cudaError_t e = cudaFuncSetAttribute(res_kernel<NX, COMP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(res_kernel<NX, COMP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
 template <typename T>
 cudaError_t step_impl(const DevView& v, const LaunchShape& sh, cudaStream_t st) {
   for (int ph = 0; ph < 3; ++ph) {
@@ -2075,6 +2562,7 @@ cudaError_t observe_impl(const DevView& v, const LaunchShape& sh, cudaStream_t s
     stencil_block_kernel<T, true><<<sh.rt_blk, sh.rows_threads, sh.blk_smem, st>>>(v, whole);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if (sizeof(T) == sizeof(float) && (e = res_all<true>(v, sh, 0, st)) != cudaSuccess) return e;
   obs_finalize_kernel<<<(v.m + 127) / 128, 128, 0, st>>>(v);
   return cudaGetLastError();
 }
@@ -2122,7 +2610,24 @@ cudaError_t smem_limits_impl() {
 }  // namespace
 
 cudaError_t set_kernel_smem_limits(int precision) {
-  return precision == 0 ? smem_limits_impl<double>() : smem_limits_impl<float>();
+  if (precision == 0) return smem_limits_impl<double>();
+  cudaError_t e;
+  if ((e = smem_limits_impl<float>()) != cudaSuccess || (e = res_smem_limit<128, false>()) != cudaSuccess ||
+      (e = res_smem_limit<128, true>()) != cudaSuccess || (e = res_smem_limit<256, false>()) != cudaSuccess)
+    return e;
+  return res_smem_limit<256, true>();
+}
+
+size_t resident_smem_bytes(int nx, int comp) { return res_smem_bytes(nx, comp != 0); }
+
+cudaError_t launch_resident(const DevView& v, int precision, const LaunchShape& sh, int64_t nsteps, cudaStream_t st) {
+  if (precision == 0 || nsteps <= 0) return cudaSuccess;
+  for (int64_t done = 0; done < nsteps; done += kResChunk) {
+    const int64_t n = nsteps - done < kResChunk ? nsteps - done : kResChunk;
+    cudaError_t e = res_all<false>(v, sh, n, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_init_members(const DevView& v, int precision, const int* list, int count, int64_t max_points,

@@ -16,7 +16,6 @@
 // with the member constants passed by value instead of from device tables.
 #include <cstdint>
 #include <cstdio>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -34,10 +33,6 @@ constexpr int64_t kNoAllocMaxPoints = (int64_t)1 << 20;
 // The scratch.  In host code this name is only a stand-in for the device array: host code
 // must use the address returned by cudaGetSymbolAddress, never the name itself.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxPoints];
-
-constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mutex;
 
 constexpr size_t kSmemMax = 227 * 1024;
 constexpr int kThreads = 256;
@@ -165,24 +160,20 @@ int na_fail(int code, const char* msg) {
   return code;
 }
 
-// Device address of the scratch on the current device (looked up once per device).
+// Device address of the scratch in the current context, and the kernels' shared-memory
+// limit, set up on every call.  Neither allocates.  The address belongs to the module as
+// loaded in the current context, so it is not cached: after a device reset, or when the
+// caller switches to another context of the same device, the module is loaded again at
+// another address, and a cached pointer would then point at freed or unmapped memory.
 cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(noalloc_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(noalloc_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  e = cudaFuncSetAttribute(noalloc_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(noalloc_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -224,10 +215,12 @@ extern "C" int ch_step_field_noalloc(double* C, int nx, int ny, double L, double
   if (scratch_address(&W) != cudaSuccess) return na_fail(CH_ECUDA, "scratch set-up failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int row_blocks = (ny + br - 1) / br, col_blocks = (nx + bc - 1) / bc;
+  // Launch errors are read with cudaPeekAtLastError, which leaves the error state as it
+  // is for the caller.  A failure here returns with the steps before it already enqueued.
   for (int64_t s = 0; s < nsteps; ++s) {
     noalloc_rows<<<row_blocks, kThreads, rows_smem, st>>>(C, W, P);
     noalloc_cols<<<col_blocks, kThreads, cols_smem, st>>>(C, W, P);
-    if (cudaGetLastError() != cudaSuccess) return na_fail(CH_ECUDA, "ch_step_field_noalloc: launch failed");
+    if (cudaPeekAtLastError() != cudaSuccess) return na_fail(CH_ECUDA, "ch_step_field_noalloc: launch failed");
   }
   return CH_OK;
 }

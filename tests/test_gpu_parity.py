@@ -367,12 +367,12 @@ def test_ensemble_256_full_size_sampled_members(orc):
 
 
 def test_ensemble_256_fp32_full_size_sampled_members(orc):
-    # the FP32 leg of the benchmark: default kernel classes (segment rows and columns)
+    # the FP32 leg of the benchmark: default kernel classes (the cluster-resident form)
     p = wl.ENSEMBLE_256
     nsteps = 200
     with ens(p["nx"], p["ny"], p["C0"], p["gamma"], p["dt"], p["L"], prec=ch.CH_FP32) as e:
         t = e.tuning()
-        assert t["row_seg"] == 16 and t["col_seg"] == 32
+        assert t["resident"] == 1
         e.set_sampling(p["every"], p["t1"], capacity=4)
         e.step(nsteps)
         F, D, B = e.observables()
