@@ -61,7 +61,14 @@ HBM_PEAK, HBM_PEAK_SOURCE = _hbm_peak()
 #   rowsweep forward/backward row recurrences (8); read R', write W
 #   rows     (fused) stencil + row recurrences (23); read C, write W
 #   cols     column recurrences (8) + update (2); read W, read C, write C
-KERNEL_WORK = {"stencil": (15.0, 2), "rowsweep": (8.0, 2), "rows": (23.0, 2), "cols": (10.0, 3)}
+#   resident (cluster-resident FP32 form) the whole step on chip: mu (9) + R' (6) + row
+#            recurrences (8) + column recurrences (8) + update (2) flop; the field crosses HBM
+#            once per launch (read and written: 2 words per point per launch, not per step)
+KERNEL_WORK = {"stencil": (15.0, 2), "rowsweep": (8.0, 2), "rows": (23.0, 2), "cols": (10.0, 3), "resident": (33.0, 0)}
+# The same work in FP64 pipe operations (an ADD or MUL takes a pipe slot like an FMA):
+#   stencil  mu 6 (3 FMA, 1 MUL, 2 ADD) + R' 4 (2 FMA, 2 ADD); rowsweep 4 (2 FMA per
+#   recurrence); cols 5 (4 FMA + the update FMA)
+KERNEL_OPS = {"stencil": 10.0, "rowsweep": 4.0, "rows": 14.0, "cols": 5.0}
 
 
 # ------------------------------------------------------------------------------------------
@@ -214,9 +221,11 @@ def ncu_traffic(kernel, workload):
     return None
 
 
-def kernel_name(phase, t, elt):
+def kernel_name(phase, t, elt, nx=256):
     """Kernel that runs a phase under tuning t (member 0's kernel classes)."""
     ty = "double" if elt == 8 else "float"
+    if phase == "resident":
+        return "res_kernel<%d, false, false>" % nx
     if phase == "stencil":
         return "stencil_kernel<%s>" % ty
     if phase == "rowsweep":
@@ -280,7 +289,21 @@ def run_gpu_leg(ch, torch, p, prec, K, W, rank, world, dist, profile_kernels=Tru
            }
     out["tuning"] = e.tuning()
     out["launches"] = K * STEPS_PER_BENCH_STEP * (3 if out["tuning"]["split"] else 2)
-    if profile_kernels:
+    if profile_kernels and out["tuning"]["resident"] == 1:
+        # The cluster-resident form runs a sampling interval (100 steps) as one launch of its
+        # kernel: events around each launch, over 4 intervals after the timed region.
+        out["launches"] = K
+        reps = 4
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+        evs[0].record(stream)
+        for r in range(reps):
+            e.step(STEPS_PER_BENCH_STEP)
+            evs[r + 1].record(stream)
+        torch.cuda.synchronize()
+        out["kernels"] = {"resident": sum(evs[r].elapsed_time(evs[r + 1]) for r in range(reps)) / reps /
+                          STEPS_PER_BENCH_STEP}
+        out["resident_launch_ms"] = evs[0].elapsed_time(evs[reps]) / reps
+    elif profile_kernels:
         # Per-kernel durations: events around each phase launch on the engine's stream,
         # over 2 sampling intervals of the same state after the timed region.
         split = out["tuning"]["split"]
@@ -549,6 +572,40 @@ def value_estimate(res):
     return res["pts"] / (res["ms"] * 1e-3)
 
 
+# Small cases for profiler captures (one kernel, few launches, a few hundred MB at most):
+# 32 members of the 256 x 256 ensemble (inputs above the L2 for FP64), stepped 200 times to
+# leave the start transient, then one more sampling interval of 100 steps.
+#   resident32  FP32, cluster-resident form: one res_kernel launch per 100 steps
+#   stream64    FP64 split form: stencil_kernel, rowstream_kernel, colstream_kernel per step
+#   segment32   FP32 with the resident form off: rows_seg_kernel, colseg_kernel per step
+KERNEL_CASES = {"resident32": ("fp32", 0), "stream64": ("fp64", -1), "segment32": ("fp32", -1)}
+
+
+def kernel_case(name):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1911_03386_gb300 as ch
+    from paper_1911_03386_gb300 import workloads as wl
+    prec, res = KERNEL_CASES[name]
+    p = wl.ENSEMBLE_256
+    descs = [dict(nx=p["nx"], ny=p["ny"], L=p["L"], gamma=p["gamma"], dt=p["dt"], C0=p["C0"][8 * k], seed=wl.BASE_SEED,
+                  counter_base=k * p["nx"] * p["ny"]) for k in range(32)]
+    with ch.Ensemble.batch(descs, ch.CH_FP32 if prec == "fp32" else ch.CH_FP64) as e:
+        e.set_tuning(resident=res)
+        stream = torch.cuda.Stream()
+        e.set_stream(stream.cuda_stream)
+        e.set_sampling(p["every"], p["t1"], capacity=0)
+        e.step(200)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e.step(STEPS_PER_BENCH_STEP)
+        b.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": name, "members": len(descs), "time_steps": STEPS_PER_BENCH_STEP,
+                          "ms": a.elapsed_time(b), "tuning": e.tuning()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -560,6 +617,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serving legs of 1000 requests each: the workload's 50/s, the highest rate at which "
+                         "the measured load stays below 0.8 of capacity, and 200 requests FP32 vs FP64 "
+                         "(several minutes of GPU time)")
     ap.add_argument("--no-batches", action="store_true", help="skip the uneven-batch and 1024^2 legs")
     ap.add_argument("--no-stats", action="store_true", help="skip the ensemble-statistics leg")
     ap.add_argument("--campaign", action="store_true",
@@ -575,7 +636,12 @@ def main():
     ap.add_argument("--long-beta", action="store_true",
                     help="also run the 32 x 1024^2 coarsening ensemble over its whole horizon in both precisions "
                          "and compare <beta> (minutes of GPU time)")
+    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES),
+                    help="run one small profiling case (for ncu) and exit; see kernel_case()")
     args = ap.parse_args()
+    if args.kernel_case:
+        kernel_case(args.kernel_case)
+        return
     K, W = args.steps, args.warmup
     if W < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -633,14 +699,24 @@ def main():
     serving = None
     if not args.no_serving and rank == 0:
         # the serving workload's own rate, then a rate the measured capacity sustains
-        nreq = args.serving_requests
+        nreq = 1000 if args.serving_full else args.serving_requests
         at_rate = run_serving_leg(ch, torch, nreq, wl.SERVING["rate"], wl.BASE_SEED, ch.CH_FP32)
-        mean_work = at_rate["offered"] / wl.SERVING["rate"]
-        steady_rate = 0.5 * at_rate["capacity"] / mean_work
+        # mean work of a request from the generator itself (not from one leg's sample)
+        probe = wl.request_stream(count=20000, rate=1.0, seed=wl.BASE_SEED + 99)
+        mean_work = sum(r["nx"] * r["ny"] * r["steps"] for r in probe) / len(probe)
+        # a steady leg: a rate below capacity (busy-time throughput of the loaded leg); with
+        # the full legs, lowered until the measured load is at most 0.8
+        frac = 0.7 if args.serving_full else 0.5
+        steady_rate = frac * at_rate["capacity"] / mean_work
         steady = run_serving_leg(ch, torch, nreq, steady_rate, wl.BASE_SEED + 1, ch.CH_FP32)
+        tries = 0
+        while args.serving_full and steady["rho"] > 0.8 and tries < 2:
+            steady_rate *= 0.75 / steady["rho"]
+            steady = run_serving_leg(ch, torch, nreq, steady_rate, wl.BASE_SEED + 1, ch.CH_FP32)
+            tries += 1
         # the served FP32 form against the plain FP64 GPU path: the same requests at a rate
         # the FP64 ensemble throughput sustains, with paired <beta> differences
-        ncmp = max(10, nreq // 3)
+        ncmp = 200 if args.serving_full else max(10, nreq // 3)
         cmp_rate = 0.5 * value_estimate(r64) / mean_work
         c32 = run_serving_leg(ch, torch, ncmp, cmp_rate, wl.BASE_SEED + 2, ch.CH_FP32, keep=True)
         c64 = run_serving_leg(ch, torch, ncmp, cmp_rate, wl.BASE_SEED + 2, ch.CH_FP64, keep=True)
@@ -655,7 +731,8 @@ def main():
         d = np.array([x - y for x, y, n in pairs if n <= 256])
         serving = {"workload": wl.SERVING["name"], "precision": "fp32",
                    "sample": "%d requests per leg (n in {64..1024}^2, horizons U[1000, 50000], C0 ~ U[0, 0.5])"
-                             % nreq, "at_workload_rate": at_rate, "at_0.5_capacity": steady,
+                             % nreq, "mean_work_per_request": mean_work, "at_workload_rate": at_rate,
+                   "workload_rate_over_capacity": at_rate["rho"] > 1.0, "steady": steady,
                    "fp32_vs_fp64_same_requests": {
                        "requests": ncmp, "rate_per_s": cmp_rate, "fp32": c32, "fp64": c64,
                        "p99_ratio_fp64_over_fp32": c64["p99_s"] / c32["p99_s"],
@@ -730,7 +807,7 @@ def main():
     if args.campaign and rank == 0:
         from paper_1911_03386_gb300 import campaign
         camp = campaign.run(2 * math.pi, wl.CAMPAIGN["M"], ch.CH_FP32)
-        camp["paper_table4"] = dict(zip(["beta0", "k"], wl.CAMPAIGN["table4"]["2pi"]))
+        camp["paper_table"] = dict(zip(["beta0", "k"], wl.CAMPAIGN["table4"]["2pi"]))
 
     from paper_1911_03386_gb300 import replicas
     tdist = torch.distributed if dist else None
@@ -776,21 +853,30 @@ def main():
         ks = res["kernels"]
         dom = max(ks, key=ks.get)
         flops, words = KERNEL_WORK[dom]
-        tname = kernel_name(dom, res["tuning"], elt)
+        tname = kernel_name(dom, res["tuning"], elt, p["nx"])
+        if dom == "resident":
+            return resident_roofline(res, tname, ks[dom], elt)
         per_launch = {k: {"ms": v, "achieved_tflops": KERNEL_WORK[k][0] * npts / (v * 1e-3) / 1e12,
                           "achieved_gbs": KERNEL_WORK[k][1] * elt * npts / (v * 1e-3) / 1e9} for k, v in ks.items()}
         step_ms = sum(ks.values())
         if bound == "alu":
-            ach = flops * npts / (ks[dom] * 1e-3)
+            # the FP64 pipe issues an ADD or MUL in a slot an FMA would take: achieved is
+            # counted in FMA-equivalent flops (2 per pipe operation) against the measured FMA
+            # rate, i.e. the fraction of pipe slots the kernel's minimal operations fill; the
+            # plain flop count and its fraction are given beside it
+            ach = 2.0 * KERNEL_OPS[dom] * npts / (ks[dom] * 1e-3)
+            ach_flop = flops * npts / (ks[dom] * 1e-3)
             if peaks is not None:
                 pk = peaks["fp64"]["flops_per_s"]
                 src = ("measured: FP64 FMA throughput of this run (ch_fma_peak, %d CTAs x 1024 threads, CUDA events), "
-                       "the burst rate of a kernel timed alone" % peaks["fp64"].get("blocks", 2 * peaks["sms"]))
+                       "the burst rate of a kernel timed alone" % (2 * peaks["sms"]))
             else:
                 pk = FP64_PIPE_PEAK
                 src = "nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz); FMA probe skipped"
             rl = {"bound": "alu", "kernel": tname, "achieved": ach / 1e12, "peak": pk / 1e12,
-                  "unit": "TFLOP/s", "frac": ach / pk, "peak_source": src}
+                  "unit": "TFLOP/s (FMA-equivalent: 2 x FP64 pipe operations)", "frac": ach / pk, "peak_source": src,
+                  "pipe_ops_per_point": KERNEL_OPS[dom], "achieved_flop_tflops": ach_flop / 1e12,
+                  "frac_flop": ach_flop / pk}
         else:
             ach = words * elt * npts / (ks[dom] * 1e-3)
             rl = {"bound": "hbm", "kernel": tname, "achieved": ach / 1e9, "peak": HBM_PEAK / 1e9, "unit": "GB/s",
@@ -805,6 +891,31 @@ def main():
                                 "achieved_gbs": 4 * elt * npts / (step_ms * 1e-3) / 1e9,
                                 "frac": 4 * elt * npts / (step_ms * 1e-3) / HBM_PEAK, "peak_gbs": HBM_PEAK / 1e9,
                                 "peak_source": HBM_PEAK_SOURCE}
+        return rl
+
+    def resident_roofline(res, tname, step_ms, elt):
+        # The cluster-resident kernel keeps the field on chip: its bound is the SM (FP32
+        # issue and shared-memory latency), so it is stated against the measured FP32 FMA
+        # rate with its minimal 33 flop per point and step.  Beside it: the HBM rate a
+        # streaming step would need for the same throughput at the 16 B per point minimum
+        # of any factorised ADI step, and the traffic it actually needs (one read and one
+        # write of the field per launch of 100 steps).
+        flops = KERNEL_WORK["resident"][0]
+        ach = flops * npts / (step_ms * 1e-3)
+        pk = peaks["fp32"]["flops_per_s"] if peaks is not None else None
+        rl = {"bound": "alu", "kernel": tname, "achieved": ach / 1e12, "peak": pk / 1e12 if pk else None,
+              "unit": "TFLOP/s", "frac": ach / pk if pk else None,
+              "peak_source": "measured: FP32 FMA throughput of this run (ch_fma_peak)" if pk else "FMA probe skipped",
+              "traffic": ncu_traffic(tname, p["name"]), "traffic_per": "launch of 100 steps",
+              "algorithmic_per_point": {"flop": flops, "bytes_per_launch": 2 * elt},
+              "step_ms": step_ms, "launch_ms": res.get("resident_launch_ms"),
+              "hbm_needed_per_launch_gbs": 2 * elt * npts / (res["resident_launch_ms"] * 1e-3) / 1e9}
+        rl["fused_step_hbm"] = {"step_ms": step_ms, "algorithmic_bytes_per_point": 4 * elt,
+                                "equivalent_gbs": 4 * elt * npts / (step_ms * 1e-3) / 1e9,
+                                "frac": 4 * elt * npts / (step_ms * 1e-3) / HBM_PEAK, "peak_gbs": HBM_PEAK / 1e9,
+                                "peak_source": HBM_PEAK_SOURCE,
+                                "note": "equivalent rate: the resident form moves the field through HBM once per "
+                                        "launch, not per step"}
         return rl
 
     roofline = kernel_roofline(r64, "alu", 8)

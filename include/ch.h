@@ -533,6 +533,25 @@ void ch_server_destroy(ch_server s);
  */
 int ch_fma_peak(int precision, int blocks, int threads, int64_t iters, double* sink, void* stream, double* flops);
 
+/*
+ * Host-side fault injection, for testing callers' error handling (the paper has no
+ * counterpart).  Arms one fault, process-wide, that fires once:
+ *   "alloc[:N]"     the N-th device allocation of the library from now (default the next)
+ *                   reports failure without allocating: the call that made it returns
+ *                   CH_ENOMEM, releases what it had allocated and leaves no handle;
+ *   "nan[:M]"       the next ch_step first writes a NaN into the first grid point of
+ *                   member M (default 0) of its handle with a host-to-device copy; the
+ *                   member's next sample (and ch_observables) reports CH_ENONFINITE;
+ *   "timeout[:MS]"  the next chunk of a server's worker thread starts MS milliseconds
+ *                   late (default 2000): ch_server_wait with a shorter timeout returns
+ *                   CH_ETIMEOUT, a later wait the result;
+ *   "none", "" or NULL disarms.
+ * The environment variable CH_FAULT, read at the library's first allocation or first
+ * ch_set_fault, arms the same specs.  No fault touches device code: nothing faults, traps
+ * or hangs a GPU.  Errors: CH_EINVAL (malformed spec).
+ */
+int ch_set_fault(const char* spec);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char* ch_last_error(void);
 

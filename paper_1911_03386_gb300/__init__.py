@@ -139,6 +139,7 @@ _SIGS = {
     "ch_server_stats": (_c_int, [_vp, ctypes.POINTER(ServerStats)]),
     "ch_server_destroy": (None, [_vp]),
     "ch_fma_peak": (_c_int, [_c_int, _c_int, _c_int, _c_i64, _vp, _vp, _dp]),
+    "ch_set_fault": (_c_int, [ctypes.c_char_p]),
     "ch_last_error": (ctypes.c_char_p, []),
     "ch_version": (ctypes.c_char_p, []),
 }
@@ -205,6 +206,11 @@ def ch_step_field_noalloc(C_ptr, nx, ny, L, gamma, dt, nsteps, stream_ptr=None):
     """Advance a caller-owned FP64 device field (address C_ptr) by nsteps steps without
     allocating anything (scratch in a static 8 MiB device array; nx*ny <= 1048576)."""
     _check(lib().ch_step_field_noalloc(C_ptr, nx, ny, L, gamma, dt, nsteps, stream_ptr or None))
+
+
+def ch_set_fault(spec):
+    """Arm one host-side fault ("alloc[:N]", "nan[:member]", "timeout[:ms]"; None disarms)."""
+    _check(lib().ch_set_fault(None if spec is None else spec.encode()))
 
 
 def ch_fma_peak(precision, blocks, threads, iters, sink_ptr, stream_ptr=None):

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libch.so")
-SOURCES = ["ch_kernels.cu", "ch_api.cu", "ch_serve.cu", "ch_noalloc.cu", "ch_stats.cu", "ch_droplets.cu", "ch_peak.cu"]
+SOURCES = ["ch_kernels.cu", "ch_api.cu", "ch_serve.cu", "ch_noalloc.cu", "ch_stats.cu", "ch_droplets.cu", "ch_peak.cu", "ch_fault.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "-I" + INCLUDE, "-I" + CSRC]

@@ -621,7 +621,7 @@ int upload_tiles(ch_ensemble* h) {
     cudaFree(*p);
     *p = nullptr;
     cap = 0;
-    cudaError_t e = cudaMalloc(p, need * elt);
+    cudaError_t e = chk::dev_malloc(p, need * elt);
     if (e == cudaSuccess) cap = need;
     return e;
   };
@@ -729,7 +729,7 @@ int create_common(int m, const ch_member_desc* d, int precision, ch_handle* out)
     return cuda_fail(e, "cudaStreamCreate");
   }
   h->stream = h->own;
-  auto alloc = [&](void** p, size_t bytes) -> cudaError_t { return cudaMalloc(p, bytes == 0 ? 16 : bytes); };
+  auto alloc = [&](void** p, size_t bytes) -> cudaError_t { return chk::dev_malloc(p, bytes == 0 ? 16 : bytes); };
   if ((e = alloc(&h->C, h->elt * h->c_points)) != cudaSuccess ||
       (e = alloc(&h->W, h->elt * h->total_points)) != cudaSuccess ||
       (e = alloc((void**)&h->dmp, sizeof(MemberParams) * m)) != cudaSuccess ||
@@ -890,7 +890,7 @@ int ch_set_sampling(ch_handle h, int every, double t1, int64_t capacity) {
     h->dseries = nullptr;
     h->series_cap = 0;
     if (capacity > 0) {
-      cudaError_t e = cudaMalloc(&h->dseries, sizeof(double) * 4 * capacity * h->m);
+      cudaError_t e = chk::dev_malloc(&h->dseries, sizeof(double) * 4 * capacity * h->m);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(CH_ENOMEM, "series allocation");
@@ -927,6 +927,7 @@ int ch_step(ch_handle h, int64_t nsteps) {
   if (nsteps < 0) return fail(CH_EINVAL, "nsteps must be >= 0");
   // The legacy default stream cannot be captured: launch directly there.
   const bool can_graph = h->stream != nullptr && h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
+  CH_CUDA(chk::inject_nan(h->C, h->precision, h->hp.data(), h->m, h->stream), "injected NaN");
   // cluster-resident members first (their own launches of many steps each), then the
   // other members' single steps, replayed from a captured graph where possible
   CH_CUDA(chk::launch_resident(h->view(), h->precision, h->shape, nsteps, h->stream), "resident step launch");

@@ -340,7 +340,7 @@ int ch_droplets_run(int M, int N, double* R, double t_end, int nsamples, const d
   };
   auto get = [&](size_t bytes) -> void* {
     void* p = nullptr;
-    if (cudaMalloc(&p, bytes > 0 ? bytes : 1) != cudaSuccess) {
+    if (chk::dev_malloc(&p, bytes > 0 ? bytes : 1) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }

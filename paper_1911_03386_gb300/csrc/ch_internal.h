@@ -160,6 +160,23 @@ struct LaunchShape {
   int res_n[kResClasses];
 };
 
+// Host-side fault injection (ch_fault.cu; armed by ch_set_fault or CH_FAULT).
+enum { kFaultNone = 0, kFaultAlloc = 1, kFaultNan = 2, kFaultTimeout = 3 };
+// Every device allocation of the library goes through here: an armed alloc fault makes
+// the N-th one report cudaErrorMemoryAllocation without allocating.
+cudaError_t dev_malloc(void** p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+// 1 (and the fault's argument) if a fault of this kind is armed, disarming it.
+int take_fault(int kind, int64_t* arg);
+// An armed nan fault writes a NaN into the first grid point of member arg (host-to-device
+// copy on st); mp: the host copy of the member constants.
+cudaError_t inject_nan(void* C, int precision, const MemberParams* mp, int m, cudaStream_t st);
+// An armed timeout fault stalls the calling host thread for its milliseconds.
+void stall_if_armed();
+
 // Kernel launchers (ch_kernels.cu).  Each returns the launch status.
 cudaError_t launch_init_fields(const DevView& v, int precision, int64_t max_points, cudaStream_t st);
 // Initial fields of the members listed in `list` (device array of count member indices).

@@ -225,6 +225,7 @@ void worker_main(ch_server_s* S) {
         }
     }
     chunk = std::max<int64_t>(chunk, 1);
+    chk::stall_if_armed();  // injected stall of this host thread (fault injection)
     if (int rc = chh::launch_steps_direct(h, chunk)) {
       server_fail_all(S, rc, "step launch failed");
       return;
@@ -371,13 +372,13 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
   if ((e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking)) != cudaSuccess)
     return cleanup(CH_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
   h->stream = h->own;
-  if ((e = cudaMalloc(&h->C, elt * elems)) != cudaSuccess || (e = cudaMalloc(&h->W, elt * elems)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&h->dmp, sizeof(MemberParams) * max_members)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&h->dms, sizeof(MemberState) * max_members)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&h->dseg, sizeof(chk::SegTable) * max_members)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&h->dsegy, sizeof(chk::SegTable) * max_members)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&h->dobs, sizeof(double) * 3 * max_members)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&S->dlist, sizeof(int) * max_members)) != cudaSuccess)
+  if ((e = chk::dev_malloc(&h->C, elt * elems)) != cudaSuccess || (e = chk::dev_malloc(&h->W, elt * elems)) != cudaSuccess ||
+      (e = chk::dev_malloc((void**)&h->dmp, sizeof(MemberParams) * max_members)) != cudaSuccess ||
+      (e = chk::dev_malloc((void**)&h->dms, sizeof(MemberState) * max_members)) != cudaSuccess ||
+      (e = chk::dev_malloc((void**)&h->dseg, sizeof(chk::SegTable) * max_members)) != cudaSuccess ||
+      (e = chk::dev_malloc((void**)&h->dsegy, sizeof(chk::SegTable) * max_members)) != cudaSuccess ||
+      (e = chk::dev_malloc((void**)&h->dobs, sizeof(double) * 3 * max_members)) != cudaSuccess ||
+      (e = chk::dev_malloc((void**)&S->dlist, sizeof(int) * max_members)) != cudaSuccess)
     return cleanup(e == cudaErrorMemoryAllocation ? CH_ENOMEM : CH_ECUDA,
                    std::string("server allocation: ") + cudaGetErrorString(e));
   if ((e = chk::set_kernel_smem_limits(precision)) != cudaSuccess ||

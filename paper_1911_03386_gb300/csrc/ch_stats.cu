@@ -344,7 +344,7 @@ struct Scratch {
   template <class T>
   cudaError_t get(T** out, size_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count > 0 ? count : 1));
+    cudaError_t e = chk::dev_malloc(&q, sizeof(T) * (count > 0 ? count : 1));
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e;

@@ -121,7 +121,9 @@ def refinement_steps(n, preset=REFINEMENT):
 # mean of mu_1 over [20, 100] and k of mu_2 = k t fitted on the same window.
 CAMPAIGN = dict(name="paper-campaign-asymmetric", gamma=0.01, dt=0.0012, dx=TWO_PI / 256, T=100.0,
                 Ls=[TWO_PI, 2 * TWO_PI, 4 * TWO_PI, 8 * TWO_PI], M=1024, every=10, window=(20.0, 100.0),
-                table4={"2pi": (0.33, 0.036), "4pi": (0.28, 0.0056), "8pi": (0.28, 0.0013), "16pi": (0.28, 0.00031)})
+                table4={"2pi": (0.33, 0.036), "4pi": (0.28, 0.0056), "8pi": (0.28, 0.0013), "16pi": (0.28, 0.00031)},
+                # Sec. 4.3, Table 5 (symmetric mixtures; the paper discards L = 2 pi)
+                table5={"4pi": (0.356, 0.0011), "8pi": (0.346, 0.00025), "16pi": (0.346, 0.00062)})
 
 
 def asymmetric_field(n, seed, member):

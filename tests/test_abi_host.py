@@ -199,3 +199,16 @@ def test_segment_tables_are_matrix_powers():
         with pytest.raises(ch.ChError) as e:
             ch.ch_seg_tables(*bad)
         assert e.value.code == ch.CH_EINVAL
+
+
+def test_fault_specs_parse_without_gpu_work():
+    # arming and disarming touch only host state
+    for spec in ["alloc", "alloc:3", "nan", "nan:2", "timeout", "timeout:10", "none", ""]:
+        ch.ch_set_fault(spec)
+    ch.ch_set_fault(None)
+    for bad in ["alloc:0", "alloc:-1", "nan:x", "boom", "timeout:", "alloc:2x"]:
+        with pytest.raises(ch.ChError) as e:
+            ch.ch_set_fault(bad)
+        assert e.value.code == ch.CH_EINVAL
+        assert "ch_set_fault" in ch.ch_last_error()
+    ch.ch_set_fault(None)

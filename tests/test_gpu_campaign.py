@@ -42,8 +42,28 @@ def test_host_start_runs_match_oracle(prec, tol):
             assert np.max(np.abs(e.field(k) - ref.C)) <= tol
 
 
-def test_campaign_driver_small():
-    out = campaign.run(2 * math.pi, 6, ch.CH_FP64, preset=SMALL)
-    assert out["n"] == 32 and out["steps"] == 50 and out["samples"] == 10
+@pytest.mark.parametrize("start", ["asymmetric", "symmetric"])
+def test_campaign_driver_small(start):
+    out = campaign.run(2 * math.pi, 6, ch.CH_FP64, preset=SMALL, start=start)
+    assert out["n"] == 32 and out["steps"] == 50 and out["samples"] == 10 and out["start"] == start
     assert out["runs_finite"] == 6 and out["runs_counted_last_sample"] == 6
     assert math.isfinite(out["beta0_window_mean_mu1"]) and math.isfinite(out["k_fit_mu2"])
+
+
+def test_symmetric_start_is_the_library_start_about_zero():
+    # Sec. 4.3's symmetric mixture: mean zero, the device start C = 0.1 (2u - 1); runs match
+    # the oracle from the oracle's own start
+    orc = get_oracle()
+    n, M, L = 32, 2, 2 * math.pi
+    steps = int(round(SMALL["T"] / SMALL["dt"]))
+    descs = [dict(nx=n, ny=n, L=L, gamma=SMALL["gamma"], dt=SMALL["dt"], C0=0.0, seed=wl.BASE_SEED,
+                  counter_base=k * n * n) for k in range(M)]
+    with ch.Ensemble.batch(descs, ch.CH_FP64) as e:
+        for k in range(M):
+            start = orc.initial_field(n, n, 0.0, wl.BASE_SEED, k * n * n)
+            assert abs(start.mean()) < 0.01 and np.max(np.abs(start)) <= 0.1
+            assert np.array_equal(e.field(k), start)
+        e.step(steps)
+        for k in range(M):
+            ref = orc.run(orc.initial_field(n, n, 0.0, wl.BASE_SEED, k * n * n), L, SMALL["gamma"], SMALL["dt"], steps)
+            assert np.max(np.abs(e.field(k) - ref.C)) <= 1e-12

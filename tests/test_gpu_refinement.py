@@ -126,3 +126,24 @@ def test_small_study_converges():
     es = [r["E_n"] for r in rows]
     assert all(math.isfinite(x) and x > 0 for x in es)
     assert es[-1] < es[-2]
+
+
+def test_tuned_grid_equals_default_shapes():
+    """The study's autotuned launch shape (a single grid: usually the fused segment forms)
+    and the library's default (split form, one thread per line) give the same field to
+    FP64 rounding, and so the same E_n."""
+    n = 256
+    a, ia = refinement.run_grid(n, SMALL, tune=True)
+    b, ib = refinement.run_grid(n, SMALL, tune=False)
+    c, _ = refinement.run_grid(n // 2, SMALL, tune=False)
+    try:
+        assert ib["tuning"]["split"] == 1
+        fa, fb = a.field(0), b.field(0)
+        assert np.max(np.abs(fa - fb)) <= 1e-12 * max(1.0, np.max(np.abs(fb)))
+        ea = ch.ch_ensemble_refinement_error(a.h, 0, c.h, 0)
+        eb = ch.ch_ensemble_refinement_error(b.h, 0, c.h, 0)
+        assert abs(ea - eb) <= 1e-9 * eb
+    finally:
+        a.close()
+        b.close()
+        c.close()
