@@ -572,13 +572,17 @@ def value_estimate(res):
     return res["pts"] / (res["ms"] * 1e-3)
 
 
-# Small cases for profiler captures (one kernel, few launches, a few hundred MB at most):
-# 32 members of the 256 x 256 ensemble (inputs above the L2 for FP64), stepped 200 times to
-# leave the start transient, then one more sampling interval of 100 steps.
-#   resident32  FP32, cluster-resident form: one res_kernel launch per 100 steps
-#   stream64    FP64 split form: stencil_kernel, rowstream_kernel, colstream_kernel per step
-#   segment32   FP32 with the resident form off: rows_seg_kernel, colseg_kernel per step
-KERNEL_CASES = {"resident32": ("fp32", 0), "stream64": ("fp64", -1), "segment32": ("fp32", -1)}
+# Cases for profiler captures (one kernel, few launches, a few hundred MB at most), stepped
+# 200 times to leave the start transient, then one more sampling interval of 100 steps
+# (steps 200 and 300 are sample steps; step 250 is not).  The suffixes 64 and 32 are the
+# precision (resident32: FP32 and 32 members):
+#   resident32  FP32, cluster-resident form, 32 members of the 256 x 256 ensemble (one wave
+#               of clusters): one res_kernel launch per 100 steps
+#   stream64    FP64 split form, the whole 256-member ensemble (256 MB, above the L2):
+#               stencil_kernel, rowstream_kernel, colstream_kernel per step
+#   segment32   FP32 with the resident form off, the whole ensemble (134 MB):
+#               rows_seg_kernel, colseg_kernel per step
+KERNEL_CASES = {"resident32": ("fp32", 0, 32), "stream64": ("fp64", -1, 256), "segment32": ("fp32", -1, 256)}
 
 
 def kernel_case(name):
@@ -587,10 +591,11 @@ def kernel_case(name):
     __graft_entry__.build()
     import paper_1911_03386_gb300 as ch
     from paper_1911_03386_gb300 import workloads as wl
-    prec, res = KERNEL_CASES[name]
+    prec, res, members = KERNEL_CASES[name]
     p = wl.ENSEMBLE_256
-    descs = [dict(nx=p["nx"], ny=p["ny"], L=p["L"], gamma=p["gamma"], dt=p["dt"], C0=p["C0"][8 * k], seed=wl.BASE_SEED,
-                  counter_base=k * p["nx"] * p["ny"]) for k in range(32)]
+    stride = len(p["C0"]) // members
+    descs = [dict(nx=p["nx"], ny=p["ny"], L=p["L"], gamma=p["gamma"], dt=p["dt"], C0=p["C0"][stride * k],
+                  seed=wl.BASE_SEED, counter_base=k * p["nx"] * p["ny"]) for k in range(members)]
     with ch.Ensemble.batch(descs, ch.CH_FP32 if prec == "fp32" else ch.CH_FP64) as e:
         e.set_tuning(resident=res)
         stream = torch.cuda.Stream()
@@ -710,7 +715,7 @@ def main():
         steady_rate = frac * at_rate["capacity"] / mean_work
         steady = run_serving_leg(ch, torch, nreq, steady_rate, wl.BASE_SEED + 1, ch.CH_FP32)
         tries = 0
-        while args.serving_full and steady["rho"] > 0.8 and tries < 2:
+        while args.serving_full and steady["rho"] > 0.8 and tries < 4:
             steady_rate *= 0.75 / steady["rho"]
             steady = run_serving_leg(ch, torch, nreq, steady_rate, wl.BASE_SEED + 1, ch.CH_FP32)
             tries += 1
@@ -866,17 +871,20 @@ def main():
             # plain flop count and its fraction are given beside it
             ach = 2.0 * KERNEL_OPS[dom] * npts / (ks[dom] * 1e-3)
             ach_flop = flops * npts / (ks[dom] * 1e-3)
-            if peaks is not None:
-                pk = peaks["fp64"]["flops_per_s"]
-                src = ("measured: FP64 FMA throughput of this run (ch_fma_peak, %d CTAs x 1024 threads, CUDA events), "
-                       "the burst rate of a kernel timed alone" % (2 * peaks["sms"]))
-            else:
-                pk = FP64_PIPE_PEAK
-                src = "nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz); FMA probe skipped"
+            # peak from the unit counts and the clock sampled during the timed region: 152 SMs x
+            # 2 FP64 pipe operations per clock x 2 flop; the FMA probe's measured rate beside it
+            sms = peaks["sms"] if peaks is not None else 152
+            mhz = (res.get("clocks") or {}).get("sm_mhz") or 2070.0
+            pk = sms * 2 * 2 * mhz * 1e6
             rl = {"bound": "alu", "kernel": tname, "achieved": ach / 1e12, "peak": pk / 1e12,
-                  "unit": "TFLOP/s (FMA-equivalent: 2 x FP64 pipe operations)", "frac": ach / pk, "peak_source": src,
+                  "unit": "TFLOP/s (FMA-equivalent: 2 x FP64 pipe operations)", "frac": ach / pk,
+                  "peak_source": "derived: %d SMs x 2 FP64 pipe operations per clock x 2 flop x %.0f MHz "
+                                 "(median SM clock of the timed region)" % (sms, mhz),
                   "pipe_ops_per_point": KERNEL_OPS[dom], "achieved_flop_tflops": ach_flop / 1e12,
                   "frac_flop": ach_flop / pk}
+            if peaks is not None:
+                rl["probe_fma_tflops"] = peaks["fp64"]["tflops"]
+                rl["frac_of_probe"] = ach / peaks["fp64"]["flops_per_s"]
         else:
             ach = words * elt * npts / (ks[dom] * 1e-3)
             rl = {"bound": "hbm", "kernel": tname, "achieved": ach / 1e9, "peak": HBM_PEAK / 1e9, "unit": "GB/s",
@@ -902,10 +910,13 @@ def main():
         # write of the field per launch of 100 steps).
         flops = KERNEL_WORK["resident"][0]
         ach = flops * npts / (step_ms * 1e-3)
-        pk = peaks["fp32"]["flops_per_s"] if peaks is not None else None
-        rl = {"bound": "alu", "kernel": tname, "achieved": ach / 1e12, "peak": pk / 1e12 if pk else None,
-              "unit": "TFLOP/s", "frac": ach / pk if pk else None,
-              "peak_source": "measured: FP32 FMA throughput of this run (ch_fma_peak)" if pk else "FMA probe skipped",
+        sms = peaks["sms"] if peaks is not None else 152
+        mhz = (res.get("clocks") or {}).get("sm_mhz") or 2070.0
+        pk = sms * 128 * 2 * mhz * 1e6  # 128 FP32 FMA lanes per SM
+        rl = {"bound": "alu", "kernel": tname, "achieved": ach / 1e12, "peak": pk / 1e12,
+              "unit": "TFLOP/s", "frac": ach / pk,
+              "peak_source": "derived: %d SMs x 128 FP32 FMA per clock x 2 flop x %.0f MHz; FMA probe measured %s"
+                             % (sms, mhz, "%.1f TFLOP/s" % peaks["fp32"]["tflops"] if peaks is not None else "-"),
               "traffic": ncu_traffic(tname, p["name"]), "traffic_per": "launch of 100 steps",
               "algorithmic_per_point": {"flop": flops, "bytes_per_launch": 2 * elt},
               "step_ms": step_ms, "launch_ms": res.get("resident_launch_ms"),

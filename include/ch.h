@@ -235,7 +235,10 @@ int ch_launch_phase(ch_handle h, int phase);
  *               remote shared-memory stores.  HBM then moves the field once per launch
  *               instead of five words per point and step.  The phase launches
  *               (ch_launch_phase, ch_debug_row_solve) do not touch such members.
- *               0 or 1 = on for every member that fits (default), -1 = off.
+ *               0 = on for every member that fits except compensated members 256 wide
+ *               (their tiles need 118 KB of shared memory per CTA, one CTA per SM, and
+ *               the tiled kernels are faster there) (default); 1 = on for every member
+ *               that fits; -1 = off.
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
  * size, lines too long for shared memory, a row_seg that some member's nx does not fit).

@@ -18,11 +18,15 @@ def candidates(precision):
     """Candidate tunings (dicts of ch_tuning fields) for a precision."""
     out = []
     if precision == ch.CH_FP32:
+        # members that fit the cluster-resident form use it in all of these (resident = 0);
+        # the shapes vary the tiled kernels of the others, and the last two turn it off
         for row_seg in (0, -1):
             for band in (8, 16, 32):
                 for threads in (128, 256):
                     for col_seg in (0, -1):
                         out.append(dict(split=0, row_seg=row_seg, rows_band=band, threads=threads, col_seg=col_seg))
+        out.append(dict(split=0, resident=-1))
+        out.append(dict(split=0, rows_band=8, threads=128, resident=-1))
     else:
         out.append(dict(split=1, stream=1))
         for band in (8, 16):

@@ -420,10 +420,12 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
   };
   // class index of a segment-form member's columns: S = 16, 32 in one CTA, then over pairs
   auto col_index = [&](const MemberParams& p, int S) { return (S == 32 ? 1 : 0) + (col_pair(p, S) ? 2 : 0); };
-  // cluster-resident form (FP32): nx = 128 or 256, ny = 32 Q with Q <= 8 CTAs per cluster
+  // cluster-resident form (FP32): nx = 128 or 256, ny = 32 Q with Q <= 8 CTAs per cluster.
+  // By default not for compensated 256-wide members: their C, lo and mu/W tiles take 118 KB
+  // of shared memory, one CTA per SM, and the tiled kernels step them faster
   auto resident = [&](const MemberParams& p) {
-    return !f64 && t.resident >= 0 && (p.nx == 128 || p.nx == 256) && p.ny % 32 == 0 && p.ny >= 32 &&
-           p.ny <= 256;
+    const bool fits = (p.nx == 128 || p.nx == 256) && p.ny % 32 == 0 && p.ny >= 32 && p.ny <= 256;
+    return !f64 && fits && (t.resident == 1 || (t.resident == 0 && !(p.comp && p.nx == 256)));
   };
   int cwarps[4] = {8, 8, max_wp, max_wp};  // warps per CTA of each class
   for (int k = 0; k < h->m; ++k) {

@@ -67,6 +67,10 @@ def s_max(d):
 def test_members_run_resident():
     with ch.Ensemble.batch(descs_of(MEMBERS), ch.CH_FP32) as e:
         assert e.tuning()["resident"] == 1
+    with ch.Ensemble.batch(descs_of(MEMBERS[8:9]), ch.CH_FP32) as e:
+        assert e.tuning()["resident"] == -1  # compensated 256-wide: tiled unless asked
+        e.set_tuning(resident=1)
+        assert e.tuning()["resident"] == 1
     with ch.Ensemble.batch(descs_of(MEMBERS), ch.CH_FP64) as e:
         assert e.tuning()["resident"] == -1  # FP32 only
 
@@ -75,6 +79,7 @@ def test_resident_members_match_oracle(orc):
     descs = descs_of(MEMBERS)
     nsteps, every = 120, 20
     with ch.Ensemble.batch(descs, ch.CH_FP32) as e:
+        e.set_tuning(resident=1)  # every member, compensated 256-wide ones included
         e.set_sampling(every, 0.0, capacity=16)
         e.step(nsteps)
         F, D, B = e.observables()
@@ -105,15 +110,15 @@ def test_resident_agrees_with_tiled_kernels(orc):
     descs = descs_of(MEMBERS)
     nsteps = 60
     fields = {}
-    for res in (0, -1):
+    for res in (1, -1):
         with ch.Ensemble.batch(descs, ch.CH_FP32) as e:
             e.set_tuning(resident=res)
-            assert e.tuning()["resident"] == (1 if res == 0 else -1)
+            assert e.tuning()["resident"] == res
             e.set_sampling(10, 0.0, capacity=8)
             e.step(nsteps)
             fields[res] = [(e.field(k), e.series(k, 8)) for k in range(len(descs))]
     for k, d in enumerate(descs):
-        (a, sa), (b, sb) = fields[0][k], fields[-1][k]
+        (a, sa), (b, sb) = fields[1][k], fields[-1][k]
         # two FP32 evaluations of the same steps, each within 2 u (1 + 16 s) of the step's
         # size per step (the solve's conditioning; the first step is the largest) plus the
         # rounding of the stored field: their difference is within twice that
