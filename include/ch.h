@@ -239,6 +239,10 @@ int ch_launch_phase(ch_handle h, int phase);
  *               (their tiles need 118 KB of shared memory per CTA, one CTA per SM, and
  *               the tiled kernels are faster there) (default); 1 = on for every member
  *               that fits; -1 = off.
+ *   resident_rows  rows of a resident member per CTA: 32 (clusters of ny/32 CTAs of 256
+ *               threads, two per SM) or 64 (256-column members with ny a multiple of 64:
+ *               clusters of ny/64 CTAs of 512 threads, one per SM, half the CTAs per
+ *               member); 0 = default.
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
  * size, lines too long for shared memory, a row_seg that some member's nx does not fit).
@@ -256,6 +260,7 @@ typedef struct {
   int row_seg;
   int col_seg;
   int resident;
+  int resident_rows;
 } ch_tuning;
 int ch_set_tuning(ch_handle h, const ch_tuning* t); /* NULL restores the defaults */
 int ch_get_tuning(ch_handle h, ch_tuning* t);       /* shape in effect (member 0's values) */

@@ -82,7 +82,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("split", ctypes.c_int), ("rows_band", ctypes.c_int), ("rows_p", ctypes.c_int),
                 ("sweep_band", ctypes.c_int), ("cols_panel", ctypes.c_int), ("cols_p", ctypes.c_int),
                 ("threads", ctypes.c_int), ("stream", ctypes.c_int), ("persist", ctypes.c_int),
-                ("row_seg", ctypes.c_int), ("col_seg", ctypes.c_int), ("resident", ctypes.c_int)]
+                ("row_seg", ctypes.c_int), ("col_seg", ctypes.c_int), ("resident", ctypes.c_int),
+                ("resident_rows", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -402,9 +403,9 @@ def ch_launch_phase(h, phase):
 
 
 def ch_set_tuning(h, split=-1, rows_band=0, rows_p=0, sweep_band=0, cols_panel=0, cols_p=0, threads=0, stream=-1,
-                  persist=-1, row_seg=0, col_seg=0, resident=0):
+                  persist=-1, row_seg=0, col_seg=0, resident=0, resident_rows=0):
     t = Tuning(split, rows_band, rows_p, sweep_band, cols_panel, cols_p, threads, stream, persist, row_seg, col_seg,
-               resident)
+               resident, resident_rows)
     _check(lib().ch_set_tuning(h, ctypes.byref(t)))
 
 

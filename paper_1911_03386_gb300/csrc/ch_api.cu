@@ -427,6 +427,11 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     const bool fits = (p.nx == 128 || p.nx == 256) && p.ny % 32 == 0 && p.ny >= 32 && p.ny <= 256;
     return !f64 && fits && (t.resident == 1 || (t.resident == 0 && !(p.comp && p.nx == 256)));
   };
+  // rows per CTA of a resident member: 64 (one 512-thread CTA per SM, half the CTAs per
+  // member) for 256-column members whose ny is a multiple of 64 when asked for, else 32
+  auto resident_rows = [&](const MemberParams& p) {
+    return (t.resident_rows == 64 && p.nx == 256 && p.ny % 64 == 0) ? 64 : 32;
+  };
   int cwarps[4] = {8, 8, max_wp, max_wp};  // warps per CTA of each class
   for (int k = 0; k < h->m; ++k) {
     if (!h->has(k) || resident(h->hp[k])) continue;
@@ -461,9 +466,10 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
     }
     if (resident(p)) {
       // one tile per member; one partial slot per CTA of its cluster.  Scan tables: rows
-      // of 16 segments of nx / 16 points, columns of ny / (nx / 8) segments of nx / 8
-      const int Q = p.ny / 32;
-      rcl[chk::res_class(p.nx, p.comp, Q)].push_back(Tile{k, 0, p.ny, 0, 0, 0});
+      // of 16 segments of nx / 16 points, columns of ny / (nx / 8) segments of nx / 8 (the
+      // same for both CTA heights)
+      const int nr = resident_rows(p), Q = p.ny / nr;
+      rcl[chk::res_class(p.nx, nr, p.comp, Q)].push_back(Tile{k, 0, p.ny, 0, 0, 0});
       p.seg_g = p.row_t = p.col_s = 0;
       p.nbands = Q;
       p.partial_base = part;
@@ -784,9 +790,52 @@ int launch_tiled_direct(ch_ensemble* h, int64_t n) {
   return CH_OK;
 }
 
+void free_aux(ch_ensemble* h) {
+  for (int i = 0; i < ch_ensemble::kAux; ++i) {
+    if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
+    if (h->aux_done[i]) cudaEventDestroy(h->aux_done[i]);
+    h->aux[i] = nullptr;
+    h->aux_done[i] = nullptr;
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
+  h->fork = nullptr;
+  h->aux_used = 0;
+}
+
+int fork_resident(ch_ensemble* h, int64_t n) {
+  h->aux_used = 0;
+  const int nc = chk::resident_classes(h->shape);
+  if (nc == 0 || n <= 0) return CH_OK;
+  if (nc == 1 && h->shape.n_row_tiles == 0) {  // nothing to overlap with
+    CH_CUDA(chk::launch_resident(h->view(), h->precision, h->shape, n, &h->stream, 1), "resident step launch");
+    return CH_OK;
+  }
+  if (!h->fork) {
+    for (int i = 0; i < ch_ensemble::kAux; ++i) {
+      CH_CUDA(cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking), "auxiliary stream");
+      CH_CUDA(cudaEventCreateWithFlags(&h->aux_done[i], cudaEventDisableTiming), "auxiliary event");
+    }
+    CH_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming), "fork event");
+  }
+  const int na = std::min(nc, (int)ch_ensemble::kAux);
+  CH_CUDA(cudaEventRecord(h->fork, h->stream), "fork");
+  for (int i = 0; i < na; ++i) CH_CUDA(cudaStreamWaitEvent(h->aux[i], h->fork, 0), "fork");
+  CH_CUDA(chk::launch_resident(h->view(), h->precision, h->shape, n, h->aux, na), "resident step launch");
+  for (int i = 0; i < na; ++i) CH_CUDA(cudaEventRecord(h->aux_done[i], h->aux[i]), "join");
+  h->aux_used = na;
+  return CH_OK;
+}
+
+int join_resident(ch_ensemble* h) {
+  for (int i = 0; i < h->aux_used; ++i) CH_CUDA(cudaStreamWaitEvent(h->stream, h->aux_done[i], 0), "join");
+  h->aux_used = 0;
+  return CH_OK;
+}
+
 int launch_steps_direct(ch_ensemble* h, int64_t n) {
-  CH_CUDA(chk::launch_resident(h->view(), h->precision, h->shape, n, h->stream), "resident step launch");
-  return launch_tiled_direct(h, n);
+  if (int rc = fork_resident(h, n)) return rc;
+  if (int rc = launch_tiled_direct(h, n)) return rc;
+  return join_resident(h);
 }
 
 int ensure_graph(ch_ensemble* h) {
@@ -834,6 +883,7 @@ ch_tuning default_tuning() {
   t.row_seg = 0;
   t.col_seg = 0;
   t.resident = 0;
+  t.resident_rows = 0;
   return t;
 }
 
@@ -868,6 +918,7 @@ void ch_destroy(ch_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_device(h);
+  free_aux(h);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }
@@ -930,19 +981,22 @@ int ch_step(ch_handle h, int64_t nsteps) {
   // The legacy default stream cannot be captured: launch directly there.
   const bool can_graph = h->stream != nullptr && h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
   CH_CUDA(chk::inject_nan(h->C, h->precision, h->hp.data(), h->m, h->stream), "injected NaN");
-  // cluster-resident members first (their own launches of many steps each), then the
-  // other members' single steps, replayed from a captured graph where possible
-  CH_CUDA(chk::launch_resident(h->view(), h->precision, h->shape, nsteps, h->stream), "resident step launch");
-  if (h->shape.n_row_tiles == 0) return CH_OK;
-  int64_t left = nsteps;
-  if (can_graph && left >= kGraphSteps) {
-    if (int rc = ensure_graph(h)) return rc;
-    while (left >= h->graph_steps) {
-      CH_CUDA(cudaGraphLaunch(h->graph, h->stream), "graph launch");
-      left -= h->graph_steps;
+  // cluster-resident members on their own streams (launches of many steps each), beside
+  // the other members' single steps on the handle's stream, replayed from a captured graph
+  // where possible; the handle's stream then waits for both
+  if (int rc = fork_resident(h, nsteps)) return rc;
+  if (h->shape.n_row_tiles > 0) {
+    int64_t left = nsteps;
+    if (can_graph && left >= kGraphSteps) {
+      if (int rc = ensure_graph(h)) return rc;
+      while (left >= h->graph_steps) {
+        CH_CUDA(cudaGraphLaunch(h->graph, h->stream), "graph launch");
+        left -= h->graph_steps;
+      }
     }
+    if (int rc = launch_tiled_direct(h, left)) return rc;
   }
-  return launch_tiled_direct(h, left);
+  return join_resident(h);
 }
 
 int ch_synchronize(ch_handle h) {
@@ -1125,6 +1179,8 @@ int ch_set_tuning(ch_handle h, const ch_tuning* t) {
   if (req.col_seg != -1 && req.col_seg != 0 && req.col_seg != 16 && req.col_seg != 32)
     return fail(CH_EINVAL, "col_seg must be -1, 0, 16 or 32");
   if (req.resident < -1 || req.resident > 1) return fail(CH_EINVAL, "resident must be -1, 0 or 1");
+  if (req.resident_rows != 0 && req.resident_rows != 32 && req.resident_rows != 64)
+    return fail(CH_EINVAL, "resident_rows must be 0, 32 or 64");
   CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
   const std::vector<MemberParams> saved = h->hp;
   const ch_tuning old = h->tuning;
@@ -1154,8 +1210,12 @@ int ch_get_tuning(ch_handle h, ch_tuning* t) {
   t->row_seg = h->hp[0].row_t ? 1 : (h->hp[0].seg_g ? h->hp[0].nx / h->hp[0].seg_g : (h->shape.split ? 0 : -1));
   t->col_seg = h->hp[0].col_s ? h->hp[0].col_s : -1;
   t->resident = h->rest.empty() ? -1 : 1;
+  t->resident_rows = 0;
   for (const Tile& r : h->rest)
-    if (r.member == 0) t->row_seg = t->col_seg = 0;  // member 0 runs in the resident form
+    if (r.member == 0) {  // member 0 runs in the resident form
+      t->row_seg = t->col_seg = 0;
+      t->resident_rows = h->hp[0].nbands > 0 ? h->hp[0].ny / h->hp[0].nbands : 32;
+    }
   return CH_OK;
 }
 

@@ -58,6 +58,13 @@ struct ch_ensemble {
   bool external_stream = false;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  // streams on which the resident classes run beside the tiled kernels (created on first
+  // use), the fork event recorded on `stream` and one join event per auxiliary stream
+  static constexpr int kAux = 4;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t aux_done[kAux] = {};
+  cudaEvent_t fork = nullptr;
+  int aux_used = 0;
 
   bool has(int k) const { return present.empty() || present[k]; }
 
@@ -106,6 +113,13 @@ void drop_graph(ch_ensemble* h);
 // n steps of every member: the cluster-resident members' launches, then n single steps
 // of the tiled kernels.
 int launch_steps_direct(ch_ensemble* h, int64_t n);
+// The resident members' n steps, forked from h->stream onto auxiliary streams when there
+// are tiled members or several resident classes to overlap with (then join_resident makes
+// h->stream wait for them).
+int fork_resident(ch_ensemble* h, int64_t n);
+int join_resident(ch_ensemble* h);
+// Release the auxiliary streams and events.
+void free_aux(ch_ensemble* h);
 int copy_out(ch_ensemble* h, void* dst, const void* src, size_t bytes, const char* what);
 int read_states(ch_ensemble* h, std::vector<MemberState>& s);
 // Member k's field to / from FP64 host values (FP32 compensated members: hi + lo).

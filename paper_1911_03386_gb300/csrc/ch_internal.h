@@ -113,13 +113,17 @@ struct DevView {
   int m;
 };
 
-// Cluster-resident form (FP32): a member with nx = 128 or 256 and ny = 32 Q, Q = 1 .. 8,
-// is stepped by a cluster of Q CTAs that keep its field in shared memory for a whole
-// chunk of steps.  Its tiles are ordered by class (nx, compensated, Q):
-// class index = ((nx == 256) * 2 + comp) * 8 + Q - 1.
-constexpr int kResClasses = 32;
+// Cluster-resident form (FP32): a member with nx = 128 or 256 and ny = NR Q (NR = 32 rows per
+// CTA, Q = 1 .. 8; or NR = 64, nx = 256, Q = 1 .. 4) is stepped by a cluster of Q CTAs that
+// keep its field in shared memory for a whole chunk of steps.  Its tiles are ordered by
+// class (form, compensated, Q) with form 0: nx = 128, NR = 32; 1: nx = 256, NR = 32;
+// 2: nx = 256, NR = 64 -- class index = (form * 2 + comp) * 8 + Q - 1.
+constexpr int kResClasses = 48;
 constexpr int64_t kResChunk = 4096;  // steps per launch of the resident kernel
-inline int res_class(int nx, int comp, int Q) { return ((nx == 256 ? 2 : 0) + (comp ? 1 : 0)) * 8 + Q - 1; }
+inline int res_class(int nx, int nr, int comp, int Q) {
+  const int form = nx == 128 ? 0 : (nr == 32 ? 1 : 2);
+  return (form * 2 + (comp ? 1 : 0)) * 8 + Q - 1;
+}
 
 // Launch shapes chosen on the host per handle (see ch_api.cu).
 struct LaunchShape {
@@ -187,10 +191,13 @@ cudaError_t launch_step(const DevView& v, int precision, const LaunchShape& sh, 
 cudaError_t launch_phase(const DevView& v, int precision, int phase, const LaunchShape& sh, cudaStream_t st);
 cudaError_t launch_observe(const DevView& v, int precision, const LaunchShape& sh, cudaStream_t st);
 // nsteps steps of every cluster-resident member (no-op when there are none), in launches
-// of at most kResChunk steps.
-cudaError_t launch_resident(const DevView& v, int precision, const LaunchShape& sh, int64_t nsteps, cudaStream_t st);
-// Dynamic shared memory of the cluster-resident kernel for rows of nx floats.
-size_t resident_smem_bytes(int nx, int comp);
+// of at most kResChunk steps; each class present goes to streams[i % nstreams].
+cudaError_t launch_resident(const DevView& v, int precision, const LaunchShape& sh, int64_t nsteps,
+                            const cudaStream_t* streams, int nstreams);
+// Number of resident classes present in a launch shape.
+int resident_classes(const LaunchShape& sh);
+// Dynamic shared memory of the cluster-resident kernel for rows of nx floats, nr per CTA.
+size_t resident_smem_bytes(int nx, int nr, int comp);
 cudaError_t set_kernel_smem_limits(int precision);
 // Resident CTAs per SM of the column kernel for a launch shape (0 on error).
 int cols_blocks_per_sm(int precision, int persist, int threads, size_t smem);

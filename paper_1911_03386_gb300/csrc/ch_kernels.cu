@@ -1758,11 +1758,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(sizeof(T) == 4 ? 102
 }
 
 // -------------------------------------------------------------------------------------
-// Cluster-resident form (FP32).  A member with nx = 128 or 256 and ny = 32 Q (Q <= 8)
-// keeps its whole field in the shared memory of a cluster of Q CTAs for a chunk of steps:
-// CTA q holds rows 32q .. 32q+31 plus two halo rows on each side, so HBM sees one load and
-// one store of the field per launch instead of five words per point and step.  One step:
-//   mu      34 rows (own rows and one halo row each side) from the C tile, 4 points per
+// Cluster-resident form (FP32).  A member with nx = 128 or 256 and ny = NR Q keeps its whole
+// field in the shared memory of a cluster of Q CTAs for a chunk of steps: CTA q holds rows
+// NR q .. NR q + NR - 1 (NR = 32, Q <= 8; or NR = 64 for nx = 256, Q <= 4) plus two halo rows
+// on each side, so HBM sees one load and one store of the field per launch instead of five
+// words per point and step.  One step:
+//   mu      NR + 2 rows (own rows and one halo row each side) from the C tile, 4 points per
 //           thread, into the mu/W tile;
 //   rows    R' in registers, both row recurrences as segment scans across 16 lanes per
 //           row (S = nx / 16 points per lane), W back into the mu/W tile;
@@ -1784,14 +1785,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(sizeof(T) == 4 ? 102
 // kernels); rank 0 sums the CTAs' partials in rank order and finalises the sample.  mu and
 // R' are formed in the operation order of the segment-form kernels.
 // -------------------------------------------------------------------------------------
-constexpr int kResRows = 32;      // rows of the field per CTA
-constexpr int kResThreads = 256;  // threads per CTA
-#ifndef CH_RES_MIN_BLOCKS
-#define CH_RES_MIN_BLOCKS 2
-#endif
-// CTAs per SM the register budget is sized for (two plain 256-column CTAs fit the shared
-// memory of an SM)
-constexpr int kResMinBlocks = CH_RES_MIN_BLOCKS;
+// NR rows of the field per CTA (32 or 64) with 8 NR threads: every thread owns 2 rows in the
+// row phase and NX / 8 rows of one column in the column phase.  NR = 32: two CTAs per SM (the
+// register and shared-memory budgets of a plain 256-column CTA); NR = 64: one CTA of 512
+// threads per SM, half as many CTAs per member.
 
 __device__ __forceinline__ unsigned cluster_size() {
   unsigned r;
@@ -1837,10 +1834,10 @@ __device__ __forceinline__ float2 mat2v_add(const float* A, float2 v, float2 w) 
 // Thread = column i of a block of 32 NX / 256 rows, walking down with three field rows in
 // registers; x neighbours by shuffles (lanes hold consecutive columns), the ends of a warp's
 // run loaded.  Fixed work split and order.  Result in thread 0.
-template <int NX, bool COMP>
+template <int NX, int NR, bool COMP>
 __device__ __forceinline__ void res_partials(const float* Ct, const float* Lt, const MemberParams& P, double* red,
                                              double& sF, double& sD) {
-  constexpr int RB = kResRows * NX / kResThreads;  // rows per thread
+  constexpr int RB = NX / 8;  // rows per thread (NR NX points over 8 NR threads)
   const int lane = threadIdx.x & 31;
   const int i = threadIdx.x % NX, r0 = (threadIdx.x / NX) * RB;
   const int ie = i + 1 == NX ? 0 : i + 1, iw = i == 0 ? NX - 1 : i - 1, iee = ie + 1 == NX ? 0 : ie + 1;
@@ -1894,28 +1891,29 @@ __device__ __forceinline__ void res_partials(const float* Ct, const float* Lt, c
 // column end states (two step parities), the scan tables, the FP64 reduction buffer, the
 // per-rank partial slots (two step parities) and the member's state (rank 0).
 constexpr int kResConsts = 288;  // row A, P (24); column A, P (8); row B (16 x 4); column B (16 x 4); H (32 x 4)
-__host__ __device__ constexpr size_t res_smem_bytes(int nx, bool comp) {
-  return (size_t)((comp ? 2 : 1) * (kResRows + 4) + (kResRows + 2)) * nx * sizeof(float) +
-         (size_t)2 * kResThreads * sizeof(float4) + kResConsts * sizeof(float) + 16 * sizeof(double) +
+__host__ __device__ constexpr size_t res_smem_bytes(int nx, int nr, bool comp) {
+  return (size_t)((comp ? 2 : 1) * (nr + 4) + (nr + 2)) * nx * sizeof(float) +
+         (size_t)2 * 8 * nr * sizeof(float4) + kResConsts * sizeof(float) + (size_t)(nr / 2) * sizeof(double) +
          16 * sizeof(double2) + (sizeof(MemberState) + 15) / 16 * 16;
 }
 
-template <int NX, bool COMP, bool OBS>
-__global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView v, int tile_base, int64_t nsteps) {
-  constexpr int S = NX / 16;                       // row points per lane
-  constexpr int SC = kResRows * NX / kResThreads;  // column points per thread
-  constexpr int NSEG = kResRows / SC;              // column segments per CTA
-  constexpr int KMAX = 8 * NSEG;                   // column segments at most (Q <= 8)
-  constexpr int NQ = NX / 4;                       // 16-byte quads per row
-  constexpr int CT = kResRows + 4, MT = kResRows + 2;
+template <int NX, int NR, bool COMP, bool OBS>
+__global__ void __launch_bounds__(8 * NR, NR == 32 ? 2 : 1) res_kernel(DevView v, int tile_base, int64_t nsteps) {
+  constexpr int TH = 8 * NR;      // threads per CTA
+  constexpr int S = NX / 16;      // row points per lane
+  constexpr int SC = NX / 8;      // column points per thread
+  constexpr int NSEG = NR / SC;   // column segments per CTA
+  constexpr int KMAX = 256 / SC;  // column segments at most (ny <= 256)
+  constexpr int NQ = NX / 4;      // 16-byte quads per row
+  constexpr int CT = NR + 4, MT = NR + 2;
   extern __shared__ __align__(16) unsigned char smem[];
   float* Ct = reinterpret_cast<float*>(smem);
   float* Lt = Ct + CT * NX;
   float* Mw = Lt + (COMP ? CT * NX : 0);
-  float4* xs = reinterpret_cast<float4*>(Mw + MT * NX);  // [2][kResThreads]
-  float* Ks = reinterpret_cast<float*>(xs + 2 * kResThreads);  // see kResConsts
-  double* red = reinterpret_cast<double*>(Ks + kResConsts);
-  double2* part = reinterpret_cast<double2*>(red + 16);  // [2][8]: by step parity, then rank
+  float4* xs = reinterpret_cast<float4*>(Mw + MT * NX);  // [2][TH]
+  float* Ks = reinterpret_cast<float*>(xs + 2 * TH);       // see kResConsts
+  double* red = reinterpret_cast<double*>(Ks + kResConsts);  // 2 per warp
+  double2* part = reinterpret_cast<double2*>(red + NR / 2);  // [2][8]: by step parity, then rank
   MemberState* lst = reinterpret_cast<MemberState*>(part + 16);
 
   const unsigned Q = cluster_size(), rank = cluster_rank();
@@ -1923,7 +1921,7 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
   const int m = tl.member;
   const MemberParams& P = v.mp[m];
   MemberState* st = v.ms + m;
-  const int ny = P.ny, j0 = (int)rank * kResRows;
+  const int ny = P.ny, j0 = (int)rank * NR;
   const int tid = threadIdx.x, lane = tid & 31;
   float* __restrict__ Cg = static_cast<float*>(v.C) + P.offset;
   float* __restrict__ Lg = COMP ? static_cast<float*>(v.C) + P.lo_offset : nullptr;
@@ -1935,7 +1933,7 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
   if (!OBS && nrun <= 0) return;  // the same decision in every CTA of the cluster
 
   // C (and lo) rows j0 - 2 .. j0 + 33, periodic
-  for (int k = tid; k < CT * NQ; k += kResThreads) {
+  for (int k = tid; k < CT * NQ; k += TH) {
     const int r = k / NQ, q = k - r * NQ;
     int j = j0 - 2 + r;
     j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
@@ -1945,7 +1943,7 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
   if (OBS) {
     __syncthreads();
     double sF, sD;
-    res_partials<NX, COMP>(Ct, Lt, P, red, sF, sD);
+    res_partials<NX, NR, COMP>(Ct, Lt, P, red, sF, sD);
     if (tid == 0) v.partials[P.partial_base + rank] = make_double2(sF, sD);
     return;
   }
@@ -1955,7 +1953,7 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
   {
     const SegTable& tx = v.seg[m];
     const SegTable& ty = v.segy[m];
-    for (int k = tid; k < kResConsts; k += kResThreads) {
+    for (int k = tid; k < kResConsts; k += TH) {
       float x = 0.f;
       if (k < 20)
         x = tx.Af[k >> 2][k & 3];
@@ -1977,7 +1975,7 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
   const float* KB = Ks + 32;   // row start-state matrices M^(S l), l = 0 .. 15
   const float* KC = Ks + 96;   // column powers M^(SC k), k = 0 .. ns - 1
   const float* KH = Ks + 160;  // column segment responses (g1, g2, k1, k2) per row
-  // row phase: 16 lanes per row, rows grp and grp + 16
+  // row phase: 16 lanes per row, rows grp and grp + NR / 2
   const int l = tid & 15, grp = tid >> 4;
   const float a = P.fa, bx = P.fbx, by = P.fby, rho = P.frho, w0 = P.fw0;
   const float p1x = P.fp1x, p2x = P.fp2x, p1y = P.fp1y, p2y = P.fp2y, kap = P.fkappa;
@@ -1990,13 +1988,13 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
     const bool sample = ((n0 + s) % P.every) == 0;
     if (sample) {
       double sF, sD;
-      res_partials<NX, COMP>(Ct, Lt, P, red, sF, sD);
+      res_partials<NX, NR, COMP>(Ct, Lt, P, red, sF, sD);
       if (tid == 0) st_peer2d(peer_addr(part + 8 * (s & 1) + rank, 0), make_double2(sF, sD));
     }
     // mu of own rows -1 .. 32 (tile row r + 1 of C) into mu/W tile row r
     {
       const int q = tid % NQ;
-      for (int r = tid / NQ; r < MT; r += kResThreads / NQ) {  // warp-uniform (NQ >= 32)
+      for (int r = tid / NQ; r < MT; r += TH / NQ) {  // warp-uniform (NQ >= 32)
         const float* c0 = Ct + (r + 1) * NX;
         float cc[4], nn[4], so[4];
         ld4(c0 + 4 * q, cc);
@@ -2017,12 +2015,12 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
       }
     }
     __syncthreads();
-    // R' and the row recurrences of own rows grp, grp + 16 (mu/W tile rows + 1)
+    // R' and the row recurrences of own rows grp, grp + NR / 2 (mu/W tile rows + 1)
     {
       float y[2][S];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        const int r = grp + 16 * t + 1;
+        const int r = grp + (NR / 2) * t + 1;
 #pragma unroll
         for (int k = 0; k < S / 4; ++k) ld4(Mw + res_swz<NX>(r, l * S + 4 * k), &y[t][4 * k]);
         const float left = __shfl_sync(kFull, y[t][S - 1], (l + 15) & 15, 16);
@@ -2054,12 +2052,12 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
 #pragma unroll
       for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int k = 0; k < S / 4; ++k) st4(Mw + res_swz<NX>(grp + 16 * t + 1, l * S + 4 * k), &y[t][4 * k]);
+        for (int k = 0; k < S / 4; ++k) st4(Mw + res_swz<NX>(grp + (NR / 2) * t + 1, l * S + 4 * k), &y[t][4 * k]);
     }
     __syncthreads();
     // columns
     {
-      float4* xsb = xs + (s & 1) * kResThreads;
+      float4* xsb = xs + (s & 1) * TH;
       float y[SC];
 #pragma unroll
       for (int u = 0; u < SC; ++u) y[u] = Mw[res_swz<NX>(g * SC + u + 1, c)];
@@ -2172,7 +2170,7 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
         Ct[c] = c_update<float>(Ct[c], kap, h0, COMP ? Lt + c : nullptr);
       }
       if (g == NSEG - 1) {
-        const int k34 = (kResRows + 2) * NX + c, k35 = k34 + NX;
+        const int k34 = (NR + 2) * NX + c, k35 = k34 + NX;
         Ct[k34] = c_update<float>(Ct[k34], kap, t_own.x, COMP ? Lt + k34 : nullptr);
         Ct[k35] = c_update<float>(Ct[k35], kap, t_own.y, COMP ? Lt + k35 : nullptr);
       }
@@ -2182,7 +2180,7 @@ __global__ void __launch_bounds__(kResThreads, kResMinBlocks) res_kernel(DevView
   cluster_sync();  // no CTA leaves while others may still read its end states
   if (keeper) *st = *lst;
   // own rows back to HBM
-  for (int k = tid; k < kResRows * NQ; k += kResThreads) {
+  for (int k = tid; k < NR * NQ; k += TH) {
     const int r = k / NQ, q = k - r * NQ;
     reinterpret_cast<float4*>(Cg + (int64_t)(j0 + r) * NX)[q] = reinterpret_cast<const float4*>(Ct + (r + 2) * NX)[q];
     if (COMP)
@@ -2496,12 +2494,12 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
 }
 
 // One launch of the resident kernel over the n tiles of one class (clusters of Q CTAs).
-template <int NX, bool COMP, bool OBS>
+template <int NX, int NR, bool COMP, bool OBS>
 cudaError_t res_launch(const DevView& v, int base, int n, int Q, int64_t nsteps, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n * Q), 1, 1);
-  cfg.blockDim = dim3(kResThreads, 1, 1);
-  cfg.dynamicSmemBytes = res_smem_bytes(NX, COMP);
+  cfg.blockDim = dim3(8 * NR, 1, 1);
+  cfg.dynamicSmemBytes = res_smem_bytes(NX, NR, COMP);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -2510,7 +2508,7 @@ cudaError_t res_launch(const DevView& v, int base, int n, int Q, int64_t nsteps,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, res_kernel<NX, COMP, OBS>, v, base, nsteps);
+  return cudaLaunchKernelEx(&cfg, res_kernel<NX, NR, COMP, OBS>, v, base, nsteps);
 }
 
 template <bool OBS>
@@ -2520,24 +2518,30 @@ cudaError_t res_all(const DevView& v, const LaunchShape& sh, int64_t nsteps, cud
     const int n = sh.res_n[ci];
     if (n <= 0) continue;
     const int Q = ci % 8 + 1;
-    const bool comp = (ci / 8) & 1, wide = ci >= 16;
+    const bool comp = (ci / 8) & 1;
+    const int form = ci / 16;  // 0: 128 columns, 32 rows; 1: 256 columns, 32 rows; 2: 256, 64
     cudaError_t e;
-    if (wide)
-      e = comp ? res_launch<256, true, OBS>(v, base, n, Q, nsteps, st) : res_launch<256, false, OBS>(v, base, n, Q, nsteps, st);
+    if (form == 2)
+      e = comp ? res_launch<256, 64, true, OBS>(v, base, n, Q, nsteps, st)
+               : res_launch<256, 64, false, OBS>(v, base, n, Q, nsteps, st);
+    else if (form == 1)
+      e = comp ? res_launch<256, 32, true, OBS>(v, base, n, Q, nsteps, st)
+               : res_launch<256, 32, false, OBS>(v, base, n, Q, nsteps, st);
     else
-      e = comp ? res_launch<128, true, OBS>(v, base, n, Q, nsteps, st) : res_launch<128, false, OBS>(v, base, n, Q, nsteps, st);
+      e = comp ? res_launch<128, 32, true, OBS>(v, base, n, Q, nsteps, st)
+               : res_launch<128, 32, false, OBS>(v, base, n, Q, nsteps, st);
     if (e != cudaSuccess) return e;
     base += n;
   }
   return cudaSuccess;
 }
 
-template <int NX, bool COMP>
+template <int NX, int NR, bool COMP>
 cudaError_t res_smem_limit() {
-  const int b = (int)res_smem_bytes(NX, COMP);
-  cudaError_t e = cudaFuncSetAttribute(res_kernel<NX, COMP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  const int b = (int)res_smem_bytes(NX, NR, COMP);
+  cudaError_t e = cudaFuncSetAttribute(res_kernel<NX, NR, COMP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(res_kernel<NX, COMP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return cudaFuncSetAttribute(res_kernel<NX, NR, COMP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
 template <typename T>
@@ -2612,22 +2616,45 @@ cudaError_t smem_limits_impl() {
 cudaError_t set_kernel_smem_limits(int precision) {
   if (precision == 0) return smem_limits_impl<double>();
   cudaError_t e;
-  if ((e = smem_limits_impl<float>()) != cudaSuccess || (e = res_smem_limit<128, false>()) != cudaSuccess ||
-      (e = res_smem_limit<128, true>()) != cudaSuccess || (e = res_smem_limit<256, false>()) != cudaSuccess)
+  if ((e = smem_limits_impl<float>()) != cudaSuccess || (e = res_smem_limit<128, 32, false>()) != cudaSuccess ||
+      (e = res_smem_limit<128, 32, true>()) != cudaSuccess || (e = res_smem_limit<256, 32, false>()) != cudaSuccess ||
+      (e = res_smem_limit<256, 32, true>()) != cudaSuccess || (e = res_smem_limit<256, 64, false>()) != cudaSuccess)
     return e;
-  return res_smem_limit<256, true>();
+  return res_smem_limit<256, 64, true>();
 }
 
-size_t resident_smem_bytes(int nx, int comp) { return res_smem_bytes(nx, comp != 0); }
+size_t resident_smem_bytes(int nx, int nr, int comp) { return res_smem_bytes(nx, nr, comp != 0); }
 
-cudaError_t launch_resident(const DevView& v, int precision, const LaunchShape& sh, int64_t nsteps, cudaStream_t st) {
+cudaError_t launch_resident(const DevView& v, int precision, const LaunchShape& sh, int64_t nsteps,
+                            const cudaStream_t* streams, int nstreams) {
   if (precision == 0 || nsteps <= 0) return cudaSuccess;
-  for (int64_t done = 0; done < nsteps; done += kResChunk) {
-    const int64_t n = nsteps - done < kResChunk ? nsteps - done : kResChunk;
-    cudaError_t e = res_all<false>(v, sh, n, st);
-    if (e != cudaSuccess) return e;
+  // the classes present, each on its own stream (round robin)
+  int base = 0, j = 0;
+  for (int ci = 0; ci < kResClasses; ++ci) {
+    const int n = sh.res_n[ci];
+    if (n <= 0) continue;
+    LaunchShape one{};
+    one.res_n[ci] = n;
+    const DevView vc = [&] {
+      DevView w = v;
+      w.res_tiles = v.res_tiles + base;
+      return w;
+    }();
+    const cudaStream_t st = streams[j++ % nstreams];
+    for (int64_t done = 0; done < nsteps; done += kResChunk) {
+      const int64_t k = nsteps - done < kResChunk ? nsteps - done : kResChunk;
+      cudaError_t e = res_all<false>(vc, one, k, st);
+      if (e != cudaSuccess) return e;
+    }
+    base += n;
   }
   return cudaSuccess;
+}
+
+int resident_classes(const LaunchShape& sh) {
+  int c = 0;
+  for (int ci = 0; ci < kResClasses; ++ci) c += sh.res_n[ci] > 0;
+  return c;
 }
 
 cudaError_t launch_init_members(const DevView& v, int precision, const int* list, int count, int64_t max_points,

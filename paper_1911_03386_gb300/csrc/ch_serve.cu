@@ -363,6 +363,12 @@ int ch_server_create(size_t hbm_budget_bytes, int precision, int max_members, ch
     cudaFree(h->dsegy);
     cudaFree(h->dobs);
     cudaFree(S->dlist);
+    cudaFree(h->drt);  // tile tables, if upload_tiles allocated them before failing
+    cudaFree(h->dst);
+    cudaFree(h->dct);
+    cudaFree(h->dcst);
+    cudaFree(h->dres);
+    cudaFree(h->dpart);
     if (h->own) cudaStreamDestroy(h->own);
     delete h;
     delete S;
@@ -502,9 +508,11 @@ void ch_server_destroy(ch_server s) {
   cudaFree(h->drt);
   cudaFree(h->dst);
   cudaFree(h->dct);
+  cudaFree(h->dres);
   cudaFree(h->dpart);
   cudaFree(h->dobs);
   cudaFree(s->dlist);
+  chh::free_aux(h);
   cudaStreamDestroy(h->own);
   delete h;
   delete s;

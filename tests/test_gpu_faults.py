@@ -110,3 +110,19 @@ def test_injected_stall_times_out_a_short_wait():
         assert e.value.code == ch.CH_ETIMEOUT
         res = s.wait(rid, 60.0)
         assert res["steps"] == 200 and math.isfinite(res["F"])
+
+
+@pytest.mark.parametrize("n", [9, 11, 14])
+def test_failed_allocation_in_server_tiles_leaks_nothing(n):
+    # the server's tile tables are allocated after its buffers: fail one of them
+    torch = pytest.importorskip("torch")
+    with ch.Server(16 << 20, ch.CH_FP32):
+        pass
+    free0 = free_bytes(torch)
+    ch.ch_set_fault("alloc:%d" % n)
+    try:
+        ch.Server(16 << 20, ch.CH_FP32).close()
+    except ch.ChError as e:
+        assert e.code == ch.CH_ENOMEM
+    ch.ch_set_fault(None)
+    assert free_bytes(torch) == free0

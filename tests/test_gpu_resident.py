@@ -75,11 +75,14 @@ def test_members_run_resident():
         assert e.tuning()["resident"] == -1  # FP32 only
 
 
-def test_resident_members_match_oracle(orc):
+@pytest.mark.parametrize("rows", [32, 64])
+def test_resident_members_match_oracle(orc, rows):
+    # rows = 64: the 256-column members with ny a multiple of 64 run in CTAs of 64 rows
     descs = descs_of(MEMBERS)
     nsteps, every = 120, 20
     with ch.Ensemble.batch(descs, ch.CH_FP32) as e:
-        e.set_tuning(resident=1)  # every member, compensated 256-wide ones included
+        e.set_tuning(resident=1, resident_rows=rows)  # every member, compensated 256-wide ones included
+        assert e.tuning()["resident_rows"] == rows
         e.set_sampling(every, 0.0, capacity=16)
         e.step(nsteps)
         F, D, B = e.observables()
@@ -110,15 +113,15 @@ def test_resident_agrees_with_tiled_kernels(orc):
     descs = descs_of(MEMBERS)
     nsteps = 60
     fields = {}
-    for res in (1, -1):
+    for res, rows in ((1, 32), (1, 64), (-1, 0)):
         with ch.Ensemble.batch(descs, ch.CH_FP32) as e:
-            e.set_tuning(resident=res)
+            e.set_tuning(resident=res, resident_rows=rows)
             assert e.tuning()["resident"] == res
             e.set_sampling(10, 0.0, capacity=8)
             e.step(nsteps)
-            fields[res] = [(e.field(k), e.series(k, 8)) for k in range(len(descs))]
+            fields[rows] = [(e.field(k), e.series(k, 8)) for k in range(len(descs))]
     for k, d in enumerate(descs):
-        (a, sa), (b, sb) = fields[1][k], fields[-1][k]
+        (a, sa), (a64, sa64), (b, sb) = fields[32][k], fields[64][k], fields[0][k]
         # two FP32 evaluations of the same steps, each within 2 u (1 + 16 s) of the step's
         # size per step (the solve's conditioning; the first step is the largest) plus the
         # rounding of the stored field: their difference is within twice that
@@ -127,7 +130,9 @@ def test_resident_agrees_with_tiled_kernels(orc):
         orc.step(one, d["L"], d["gamma"], d["dt"])
         bound = 2 * (nsteps * 2 * 2.0 ** -24 * (1 + 16 * s_max(d)) * np.max(np.abs(one - start)) + 2.0 ** -24)
         assert np.max(np.abs(a - b)) <= bound, (k, np.max(np.abs(a - b)), bound)
+        assert np.max(np.abs(a64 - b)) <= bound, (k, np.max(np.abs(a64 - b)), bound)
         np.testing.assert_allclose(sa[:, 1:], sb[:, 1:], rtol=1e-4)
+        np.testing.assert_allclose(sa64[:, 1:], sb[:, 1:], rtol=1e-4)
 
 
 def test_resident_launch_chunks_and_horizons(orc):
