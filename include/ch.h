@@ -243,6 +243,12 @@ int ch_launch_phase(ch_handle h, int phase);
  *               threads, two per SM) or 64 (256-column members with ny a multiple of 64:
  *               clusters of ny/64 CTAs of 512 threads, one per SM, half the CTAs per
  *               member); 0 = default.
+ *   preroll_head  FP64 streaming sweeps (stream): the leading points of every pre-roll
+ *               run in FP32 from the zero state and the rest in FP64 from that state; the
+ *               FP64 part is long enough that the FP32 part's rounding reaches the line
+ *               damped below the pre-roll's own 1e-17 tolerance (ch_preroll_head), so the
+ *               FP64 pipe does fewer operations for the same result to FP64 round-off.
+ *               0 = on (default); -1 = every pre-roll point in FP64.
  * Bands and panels shrink per member to fit 227 KB of shared memory.  Captured step
  * graphs are discarded.  Errors: CH_EINVAL (negative fields, products above the CTA
  * size, lines too long for shared memory, a row_seg that some member's nx does not fit).
@@ -261,6 +267,7 @@ typedef struct {
   int col_seg;
   int resident;
   int resident_rows;
+  int preroll_head;
 } ch_tuning;
 int ch_set_tuning(ch_handle h, const ch_tuning* t); /* NULL restores the defaults */
 int ch_get_tuning(ch_handle h, ch_tuning* t);       /* shape in effect (member 0's values) */
@@ -303,6 +310,21 @@ int ch_load(ch_handle h, const char* path);
  * Errors: CH_EINVAL (s not finite or <= 0, bad precision, no convergence).
  */
 int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, int* K);
+
+/*
+ * Host-side split of an FP64 pre-roll, no GPU work: for the recurrence of
+ * ch_penta_factor(s, CH_FP64) (companion matrix M = [[p1, p2], [1, 0]], pre-roll length K)
+ * returns in *head the number of leading pre-roll points that the FP64 streaming sweeps
+ * run in FP32 (ch_tuning.preroll_head).  The FP32 part starts from the zero state with its
+ * inputs truncated to FP32 and FP32 coefficients; its state error is at most
+ *   E = g2 2^-24 (3 + g (3 + |p1| + |p2|)) R,
+ * R the line's largest input, g = sum_k |(M^k)_00| (the impulse response's l1 norm) and
+ * g2 = sum_k ||M^k||_inf; the K - head FP64 points that follow multiply it by M^(K - head).
+ * head is the largest multiple of 16 with ||M^(K - head)||_inf E <= 1e-17 R, the
+ * tolerance K itself is chosen for, or 0.  Either output pointer may be NULL.
+ * Errors: CH_EINVAL (s as in ch_penta_factor).
+ */
+int ch_preroll_head(double s, int* K, int* head);
 
 /*
  * Host-side scan tables of the segment form of the row sweep (ch_tuning.row_seg), no GPU

@@ -18,7 +18,7 @@ __all__ = [
     "ch_step", "ch_synchronize", "ch_observables", "ch_beta_avg", "ch_series", "ch_get_field",
     "ch_set_field", "ch_set_fields", "ch_get_fields", "ch_launch_phase", "ch_set_tuning", "ch_get_tuning", "Tuning",
     "ch_get_step", "ch_reset", "ch_num_members", "ch_member_shape",
-    "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_seg_tables", "ch_step_field_noalloc", "ch_last_error", "ch_version",
+    "ch_debug_row_solve", "ch_save", "ch_load", "ch_penta_factor", "ch_preroll_head", "ch_seg_tables", "ch_step_field_noalloc", "ch_last_error", "ch_version",
     "CH_MOMENTS", "CH_MAX_BINS", "ch_stats_moments", "ch_stats_histogram", "ch_stats_trend", "ch_ensemble_moments",
     "ch_ensemble_histogram", "ch_ensemble_trend", "ch_refinement_error", "ch_ensemble_refinement_error",
     "ch_droplets_run",
@@ -83,7 +83,7 @@ class Tuning(ctypes.Structure):
                 ("sweep_band", ctypes.c_int), ("cols_panel", ctypes.c_int), ("cols_p", ctypes.c_int),
                 ("threads", ctypes.c_int), ("stream", ctypes.c_int), ("persist", ctypes.c_int),
                 ("row_seg", ctypes.c_int), ("col_seg", ctypes.c_int), ("resident", ctypes.c_int),
-                ("resident_rows", ctypes.c_int)]
+                ("resident_rows", ctypes.c_int), ("preroll_head", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -121,6 +121,7 @@ _SIGS = {
     "ch_save": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_load": (_c_int, [_vp, ctypes.c_char_p]),
     "ch_penta_factor": (_c_int, [_c_dbl, _c_int, _dp, _dp, _dp, _ip]),
+    "ch_preroll_head": (_c_int, [_c_dbl, _ip, _ip]),
     "ch_seg_tables": (_c_int, [_c_dbl, _c_int, _c_int, _dp]),
     "ch_step_field_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
     "ch_stats_moments": (_c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _vp, _vp]),
@@ -193,6 +194,14 @@ def ch_penta_factor(s, precision=CH_FP64):
     c, p1, p2, K = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     _check(lib().ch_penta_factor(s, precision, ctypes.byref(c), ctypes.byref(p1), ctypes.byref(p2), ctypes.byref(K)))
     return c.value, p1.value, p2.value, K.value
+
+
+def ch_preroll_head(s):
+    """(K, head) of the FP64 pre-roll of I + s D^4: its length and the leading points the
+    FP64 streaming sweeps run in FP32 (host computation, no GPU)."""
+    K, head = ctypes.c_int(), ctypes.c_int()
+    _check(lib().ch_preroll_head(s, ctypes.byref(K), ctypes.byref(head)))
+    return K.value, head.value
 
 
 def ch_seg_tables(s, seg, groups):
@@ -403,9 +412,9 @@ def ch_launch_phase(h, phase):
 
 
 def ch_set_tuning(h, split=-1, rows_band=0, rows_p=0, sweep_band=0, cols_panel=0, cols_p=0, threads=0, stream=-1,
-                  persist=-1, row_seg=0, col_seg=0, resident=0, resident_rows=0):
+                  persist=-1, row_seg=0, col_seg=0, resident=0, resident_rows=0, preroll_head=0):
     t = Tuning(split, rows_band, rows_p, sweep_band, cols_panel, cols_p, threads, stream, persist, row_seg, col_seg,
-               resident, resident_rows)
+               resident, resident_rows, preroll_head)
     _check(lib().ch_set_tuning(h, ctypes.byref(t)))
 
 

@@ -42,6 +42,7 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr size_t kSmemMax = 227 * 1024;  // dynamic shared memory per CTA on sm_103a
+constexpr double kPrerollTol64 = 1e-17;    // FP64 pre-roll: max |(M^K)_ij| (relative state error)
 // FP32 members with max(s_x, s_y) above this keep their field as the pair hi + lo
 // (compensated update): the delta-form factor damps the high diagonal modes by only
 // ~1/(4s) per step, so the rounding of an FP32 field would accumulate there; at s = 13.8
@@ -121,6 +122,35 @@ int preroll_length(double p1, double p2, double tol) {
     if (mx <= tol) return k;
   }
   return -1;
+}
+
+// Leading points of an FP64 pre-roll of K points that may run in FP32 (multiple of 16).
+// The FP32 part's local error per step is at most 2^-24 (3 + g (3 + |p1| + |p2|)) R: the
+// input truncated to FP32 (2^-23 R), the coefficients rounded to FP32 acting on a state of
+// at most g R, and two FMA roundings of values up to (1 + |p2| g) R and g R, where
+// g = sum_k |(M^k)_00| bounds |y| / R.  Summed through the recurrence the state error is at
+// most g2 = sum_k ||M^k||_inf times that, and the FP64 points after it multiply it by
+// M^(K - head).  Returns the largest head with ||M^(K - head)||_inf E <= tol R.
+int preroll_head_length(double p1, double p2, int K, double tol) {
+  double m00 = 1, m01 = 0, m10 = 0, m11 = 1, g = 0, g2 = 0;
+  std::vector<double> norms;  // ||M^k||_inf, k = 0 .. K
+  for (int k = 0; k <= 4000000; ++k) {
+    const double ninf = std::fmax(std::fabs(m00) + std::fabs(m01), std::fabs(m10) + std::fabs(m11));
+    if (k <= K) norms.push_back(ninf);
+    g += std::fabs(m00);
+    g2 += ninf;
+    if (ninf <= 1e-30 && k >= K) break;
+    const double n00 = p1 * m00 + p2 * m10, n01 = p1 * m01 + p2 * m11;
+    m10 = m00;
+    m11 = m01;
+    m00 = n00;
+    m01 = n01;
+  }
+  const double E = g2 * std::ldexp(1.0, -24) * (3.0 + g * (3.0 + std::fabs(p1) + std::fabs(p2)));
+  int tail = 0;  // smallest number of FP64 points that damps E below tol
+  while (tail <= K && norms[tail] * E > tol) ++tail;
+  if (tail > K) return 0;
+  return (K - tail) / 16 * 16;
 }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
@@ -292,7 +322,7 @@ int fill_params(const ch_member_desc& d, int precision, MemberParams* p) {
   const double sx = sigma / (hx2 * hx2), sy = sigma / (hy2 * hy2);
   if (!spectral_factor(sx, &p->cx, &p->p1x, &p->p2x) || !spectral_factor(sy, &p->cy, &p->p1y, &p->p2y))
     return fail(CH_EINVAL, "factorisation of I + s D^4 did not converge (s out of range)");
-  const double tol = precision == CH_FP64 ? 1e-17 : 1e-8;
+  const double tol = precision == CH_FP64 ? kPrerollTol64 : 1e-8;
   p->kx = preroll_length(p->p1x, p->p2x, tol);
   p->ky = preroll_length(p->p1y, p->p2y, tol);
   if (p->kx < 0 || p->ky < 0) return fail(CH_EINVAL, "decay of I + s D^4 too slow (s out of range)");
@@ -471,6 +501,7 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       const int nr = resident_rows(p), Q = p.ny / nr;
       rcl[chk::res_class(p.nx, nr, p.comp, Q)].push_back(Tile{k, 0, p.ny, 0, 0, 0});
       p.seg_g = p.row_t = p.col_s = 0;
+      p.kx32 = p.ky32 = 0;
       p.nbands = Q;
       p.partial_base = part;
       part += Q;
@@ -505,6 +536,10 @@ int build_tiles(ch_ensemble* h, const ch_tuning& t) {
       sh.seg_ccap[ri] = std::max(sh.seg_ccap[ri], (int)seg_ctile(br, p.nx));
       sh.seg_mcap[ri] = std::max(sh.seg_mcap[ri], (int)seg_mtile(br, p.nx, rc, h->elt));
     }
+    // FP32 heads of the FP64 streaming sweeps' pre-rolls
+    const bool head = f64 && stream && t.preroll_head >= 0;
+    p.kx32 = head ? preroll_head_length(p.p1x, p.p2x, p.kx, kPrerollTol64) : 0;
+    p.ky32 = head ? preroll_head_length(p.p1y, p.p2y, p.ky, kPrerollTol64) : 0;
     p.rows_p = t.rows_p > 0 ? t.rows_p : (f64 ? 1 : std::max(1, std::min(threads / br, p.nx / 64)));
     if (br * p.rows_p > threads) p.rows_p = std::max(1, threads / br);
     int bs = stream ? std::min(p.ny, 32) : std::min(p.ny, want_bs);
@@ -802,6 +837,17 @@ void free_aux(ch_ensemble* h) {
   h->aux_used = 0;
 }
 
+// The auxiliary streams and their events, created on first use.
+int ensure_aux(ch_ensemble* h) {
+  if (h->fork) return CH_OK;
+  for (int i = 0; i < ch_ensemble::kAux; ++i) {
+    CH_CUDA(cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking), "auxiliary stream");
+    CH_CUDA(cudaEventCreateWithFlags(&h->aux_done[i], cudaEventDisableTiming), "auxiliary event");
+  }
+  CH_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming), "fork event");
+  return CH_OK;
+}
+
 int fork_resident(ch_ensemble* h, int64_t n) {
   h->aux_used = 0;
   const int nc = chk::resident_classes(h->shape);
@@ -810,13 +856,7 @@ int fork_resident(ch_ensemble* h, int64_t n) {
     CH_CUDA(chk::launch_resident(h->view(), h->precision, h->shape, n, &h->stream, 1), "resident step launch");
     return CH_OK;
   }
-  if (!h->fork) {
-    for (int i = 0; i < ch_ensemble::kAux; ++i) {
-      CH_CUDA(cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking), "auxiliary stream");
-      CH_CUDA(cudaEventCreateWithFlags(&h->aux_done[i], cudaEventDisableTiming), "auxiliary event");
-    }
-    CH_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming), "fork event");
-  }
+  if (int rc = ensure_aux(h)) return rc;
   const int na = std::min(nc, (int)ch_ensemble::kAux);
   CH_CUDA(cudaEventRecord(h->fork, h->stream), "fork");
   for (int i = 0; i < na; ++i) CH_CUDA(cudaStreamWaitEvent(h->aux[i], h->fork, 0), "fork");
@@ -840,13 +880,13 @@ int launch_steps_direct(ch_ensemble* h, int64_t n) {
 
 int ensure_graph(ch_ensemble* h) {
   if (h->graph) return CH_OK;
+  const int n = kGraphSteps;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "begin graph capture");
   const chk::DevView v = h->view();
   cudaError_t le = cudaSuccess;
-  for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i)
-    le = chk::launch_step(v, h->precision, h->shape, h->stream);
+  for (int i = 0; i < n && le == cudaSuccess; ++i) le = chk::launch_step(v, h->precision, h->shape, h->stream);
   e = cudaStreamEndCapture(h->stream, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -859,7 +899,7 @@ int ensure_graph(ch_ensemble* h) {
     h->graph = nullptr;
     return cuda_fail(e, "graph instantiate");
   }
-  h->graph_steps = kGraphSteps;
+  h->graph_steps = n;
   return CH_OK;
 }
 
@@ -884,6 +924,7 @@ ch_tuning default_tuning() {
   t.col_seg = 0;
   t.resident = 0;
   t.resident_rows = 0;
+  t.preroll_head = 0;
   return t;
 }
 
@@ -1181,6 +1222,7 @@ int ch_set_tuning(ch_handle h, const ch_tuning* t) {
   if (req.resident < -1 || req.resident > 1) return fail(CH_EINVAL, "resident must be -1, 0 or 1");
   if (req.resident_rows != 0 && req.resident_rows != 32 && req.resident_rows != 64)
     return fail(CH_EINVAL, "resident_rows must be 0, 32 or 64");
+  if (req.preroll_head < -1 || req.preroll_head > 0) return fail(CH_EINVAL, "preroll_head must be -1 or 0");
   CH_CUDA(cudaStreamSynchronize(h->stream), "synchronise");
   const std::vector<MemberParams> saved = h->hp;
   const ch_tuning old = h->tuning;
@@ -1211,6 +1253,7 @@ int ch_get_tuning(ch_handle h, ch_tuning* t) {
   t->col_seg = h->hp[0].col_s ? h->hp[0].col_s : -1;
   t->resident = h->rest.empty() ? -1 : 1;
   t->resident_rows = 0;
+  t->preroll_head = h->tuning.preroll_head < 0 ? -1 : 0;
   for (const Tile& r : h->rest)
     if (r.member == 0) {  // member 0 runs in the resident form
       t->row_seg = t->col_seg = 0;
@@ -1341,12 +1384,23 @@ int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, 
   if (precision != CH_FP64 && precision != CH_FP32) return fail(CH_EINVAL, "bad precision");
   double cc, q1, q2;
   if (!spectral_factor(s, &cc, &q1, &q2)) return fail(CH_EINVAL, "factorisation did not converge");
-  const int k = preroll_length(q1, q2, precision == CH_FP64 ? 1e-17 : 1e-8);
+  const int k = preroll_length(q1, q2, precision == CH_FP64 ? kPrerollTol64 : 1e-8);
   if (k < 0) return fail(CH_EINVAL, "decay too slow");
   if (c) *c = cc;
   if (p1) *p1 = q1;
   if (p2) *p2 = q2;
   if (K) *K = k;
+  return CH_OK;
+}
+
+int ch_preroll_head(double s, int* K, int* head) {
+  if (!finite_pos(s)) return fail(CH_EINVAL, "s must be finite and > 0");
+  double cc, q1, q2;
+  if (!spectral_factor(s, &cc, &q1, &q2)) return fail(CH_EINVAL, "factorisation did not converge");
+  const int k = preroll_length(q1, q2, kPrerollTol64);
+  if (k < 0) return fail(CH_EINVAL, "decay too slow");
+  if (K) *K = k;
+  if (head) *head = preroll_head_length(q1, q2, k, kPrerollTol64);
   return CH_OK;
 }
 

@@ -1181,9 +1181,9 @@ __global__ void __launch_bounds__(256) rows_seg_kernel(DevView v, int base, int 
 // Split form, kernel 1: stencil + observables of a band, R' written to the W scratch.
 // -------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(512) stencil_kernel(DevView v) {
+__global__ void __launch_bounds__(512) stencil_kernel(DevView v, int tile_base) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const Tile tl = v.row_tiles[blockIdx.x];
+  const Tile tl = v.row_tiles[tile_base + blockIdx.x];
   const MemberParams& P = v.mp[tl.member];
   MemberState* st = v.ms + tl.member;
   bool sample = true;
@@ -2205,6 +2205,20 @@ constexpr size_t rowstream_smem_bytes(size_t elt) {
   return (size_t)kStreamWarps * 2 * 32 * ((elt == 8 ? 16 : 32) + 1) * elt;
 }
 
+// Binary64 -> binary32 with the significand truncated, from the two formats' fields (IEEE
+// 754: binary64 = sign, 11-bit exponent biased by 1023, 52-bit fraction; binary32 = sign,
+// 8-bit exponent biased by 127, 23-bit fraction): the exponent is rebiased by 896 and the
+// top 23 fraction bits kept, so the relative error is below 2^-23.  |x| < 2^-126 gives a
+// signed zero, |x| >= 2^128 (and NaN) a signed infinity.  Integer operations only: the
+// FP32 heads of the FP64 pre-rolls leave the FP64 pipe to the FP64 part.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned mag = hi & 0x7fffffffu, sign = hi & 0x80000000u;
+  const unsigned body = __funnelshift_l(lo, mag - (896u << 20), 3);  // (exp - 896) << 23 | fraction >> 29
+  const unsigned bits = mag < (897u << 20) ? sign : (mag >= (1151u << 20) ? (sign | 0x7f800000u) : (sign | body));
+  return __uint_as_float(bits);
+}
+
 // Sequence position q of a pass -> column/row index: positions 0..K-1 are the pre-roll,
 // K..K+n-1 the line itself.  Forward: pre-roll over indices -K..-1 (mod n), then 0..n-1.
 // Backward: pre-roll over n-1+K..n (mod n), then n-1..0.
@@ -2213,14 +2227,39 @@ __device__ __forceinline__ int bwd_index(int q, int K, int n) {
   return q < K ? wrap_index(n - 1 + K - q, n) : n - 1 - (q - K);
 }
 
+// FP32 head of an FP64 column pre-roll: positions 0 .. kh-1 of the forward (fwd) or
+// backward pass from the zero state, inputs truncated to FP32; the state is handed to the
+// FP64 part that continues at position kh.  kh is a multiple of 16 and at most K.
+__device__ __forceinline__ void head_pass_col(const double* Wc, int nx, int ny, int K, int kh, float p1, float p2,
+                                              bool fwd, double* s1, double* s2) {
+  constexpr int kU = 8;
+  float f1 = 0.f, f2 = 0.f;
+  for (int q0 = 0; q0 < kh; q0 += kU) {
+    float r[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = fwd ? fwd_index(q0 + u, K, ny) : bwd_index(q0 + u, K, ny);
+      r[u] = f32_trunc(Wc[(int64_t)j * nx]);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const float y = fmaf(p1, f1, fmaf(p2, f2, r[u]));
+      f2 = f1;
+      f1 = y;
+    }
+  }
+  *s1 = (double)f1;
+  *s2 = (double)f2;
+}
+
 // Column sweep + update, one thread per column, straight from global memory (a warp reads
 // 32 consecutive elements of a row per access).  Tiles: 32-column groups; kStreamWarps
 // groups per CTA.
 template <typename T>
-__global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v, int ntiles) {
+__global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v, int ntiles, int tile_base) {
   const int wt = blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
   if (wt >= ntiles) return;
-  const Tile tl = v.col_tiles[wt];
+  const Tile tl = v.col_tiles[tile_base + wt];
   MemberState* st = v.ms + tl.member;
   if (!st->active) return;
   const MemberParams& P = v.mp[tl.member];
@@ -2233,9 +2272,11 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
     T* const Lc = lo_ptr<T>(v, P, tl.start + lane);  // lo column of compensated members, else null
     constexpr int kUnroll = 8;  // loads issued ahead of the recurrence
     const int len = K + ny;
+    const int kh = P.ky32;      // FP32 head of each pre-roll (FP64 only; a multiple of 16)
     // forward: y_j = W'_j + p1 y_{j-1} + p2 y_{j-2}; y written over W'
     T y1 = T(0), y2 = T(0);
-    for (int q0 = 0; q0 < len; q0 += kUnroll) {
+    if constexpr (sizeof(T) == 8) head_pass_col(Wc, nx, ny, K, kh, P.fp1y, P.fp2y, true, &y1, &y2);
+    for (int q0 = sizeof(T) == 8 ? kh : 0; q0 < len; q0 += kUnroll) {
       T r[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u)
@@ -2252,7 +2293,8 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
     }
     // backward: x_j = y_j + p1 x_{j+1} + p2 x_{j+2};  C_j += kappa x_j
     T x1 = T(0), x2 = T(0);
-    for (int q0 = 0; q0 < len; q0 += kUnroll) {
+    if constexpr (sizeof(T) == 8) head_pass_col(Wc, nx, ny, K, kh, P.fp1y, P.fp2y, false, &x1, &x2);
+    for (int q0 = sizeof(T) == 8 ? kh : 0; q0 < len; q0 += kUnroll) {
       T r[kUnroll], c[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
@@ -2303,6 +2345,8 @@ __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v,
   const int nx = P.nx, K = P.kx, nr = tl.count;
   T* Wb = static_cast<T*>(v.W) + P.offset + (int64_t)tl.start * nx;
   const T p1 = (T)P.p1x, p2 = (T)P.p2x;
+  const float fp1 = P.fp1x, fp2 = P.fp2x;
+  const int kh = sizeof(T) == 8 ? P.kx32 : 0;  // FP32 head of each pre-roll: chunks 0 .. kh/CW - 1
   const int len = K + nx;
   const int nchunks = (len + CW - 1) / CW;
   // this warp's two 32 x (CW+1) buffers
@@ -2325,6 +2369,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v,
     };
     issue(0, 0);
     T s1 = T(0), s2 = T(0);
+    float f1 = 0.f, f2 = 0.f;
     for (int ch = 0; ch < nchunks; ++ch) {
       const int b = ch & 1;
       if (ch + 1 < nchunks) {
@@ -2338,7 +2383,23 @@ __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v,
       const int cnt = min(CW, len - qbase);
       if (lane < nr) {
         T* row = buf[b][lane];
-        if (cnt == CW) {
+        if (qbase + CW <= kh) {
+          if constexpr (sizeof(T) == 8) {  // FP32 head: nothing of it is stored
+            float vals[CW];
+#pragma unroll
+            for (int u = 0; u < CW; ++u) vals[u] = f32_trunc(row[u]);
+#pragma unroll
+            for (int u = 0; u < CW; ++u) {
+              const float val = fmaf(fp1, f1, fmaf(fp2, f2, vals[u]));
+              f2 = f1;
+              f1 = val;
+            }
+            if (qbase + CW == kh) {
+              s1 = (T)f1;
+              s2 = (T)f2;
+            }
+          }
+        } else if (cnt == CW) {
           T vals[CW];
 #pragma unroll
           for (int u = 0; u < CW; ++u) vals[u] = row[u];
@@ -2453,7 +2514,7 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
     case 0:
       if (sh.split) {
         const int whole = sh.n_row_tiles - sh.rt_blk;
-        if (whole > 0) stencil_kernel<T><<<whole, sh.rows_threads, sh.rows_smem, st>>>(v);
+        if (whole > 0) stencil_kernel<T><<<whole, sh.rows_threads, sh.rows_smem, st>>>(v, 0);
         if (sh.rt_blk > 0) {
           if (sizeof(T) != sizeof(double)) return cudaErrorInvalidValue;  // FP64 only
           stencil_block_kernel<T, false><<<sh.rt_blk, sh.rows_threads, sh.blk_smem, st>>>(v, whole);
@@ -2482,7 +2543,7 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
         break;
       else if (sh.stream)
         colstream_kernel<T><<<(sh.n_col_tiles + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps, 0, st>>>(
-            v, sh.n_col_tiles);
+            v, sh.n_col_tiles, 0);
       else if (sh.cols_persist)
         cols_kernel<T, true><<<min(sh.n_col_tiles, sh.cols_grid), sh.cols_threads, sh.cols_smem, st>>>(
             v, sh.n_col_tiles, sh.cols_panel_cap);
