@@ -225,7 +225,7 @@ def kernel_name(phase, t, elt, nx=256):
     """Kernel that runs a phase under tuning t (member 0's kernel classes)."""
     ty = "double" if elt == 8 else "float"
     if phase == "resident":
-        return "res_kernel<%d, false, false>" % nx
+        return "res_kernel<%d, %d, false, false>" % (nx, t.get("resident_rows") or 32)
     if phase == "stencil":
         return "stencil_kernel<%s>" % ty
     if phase == "rowsweep":
