@@ -243,8 +243,8 @@ int ch_launch_phase(ch_handle h, int phase);
  *               threads, two per SM) or 64 (256-column members with ny a multiple of 64:
  *               clusters of ny/64 CTAs of 512 threads, one per SM, half the CTAs per
  *               member); 0 = default.
- *   preroll_head  FP64 streaming sweeps (stream): the leading points of every pre-roll
- *               run in FP32 from the zero state and the rest in FP64 from that state; the
+ *   preroll_head  FP64 streaming row sweeps (stream): the leading points of every row
+ *               pre-roll run in FP32 from the zero state and the rest in FP64 from it; the
  *               FP64 part is long enough that the FP32 part's rounding reaches the line
  *               damped below the pre-roll's own 1e-17 tolerance (ch_preroll_head), so the
  *               FP64 pipe does fewer operations for the same result to FP64 round-off.
@@ -314,8 +314,8 @@ int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, 
 /*
  * Host-side split of an FP64 pre-roll, no GPU work: for the recurrence of
  * ch_penta_factor(s, CH_FP64) (companion matrix M = [[p1, p2], [1, 0]], pre-roll length K)
- * returns in *head the number of leading pre-roll points that the FP64 streaming sweeps
- * run in FP32 (ch_tuning.preroll_head).  The FP32 part starts from the zero state with its
+ * returns in *head the number of leading pre-roll points that the FP64 streaming row
+ * sweeps run in FP32 (ch_tuning.preroll_head).  The FP32 part starts from the zero state with its
  * inputs truncated to FP32 and FP32 coefficients; its state error is at most
  *   E = g2 2^-24 (3 + g (3 + |p1| + |p2|)) R,
  * R the line's largest input, g = sum_k |(M^k)_00| (the impulse response's l1 norm) and

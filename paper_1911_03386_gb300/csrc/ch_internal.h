@@ -25,7 +25,7 @@ struct MemberParams {
   int64_t offset;        // first element of the member's field in C and W
   int nx, ny;
   int kx, ky;            // pre-roll lengths of the x / y recurrences (see ch_kernels.cu)
-  int kx32, ky32;        // FP64 streaming sweeps: leading pre-roll points run in FP32 (0: none)
+  int kx32;              // FP64 streaming row sweeps: leading pre-roll points run in FP32 (0: none)
   int nbands;            // row tiles of this member = partial slots per sample
   int rows_p, cols_p;    // threads per line in the row / column sweep
   int seg_g;             // segment form of the row sweep: lanes per row (nx / S), 0 = chunked

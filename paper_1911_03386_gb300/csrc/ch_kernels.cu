@@ -2227,31 +2227,6 @@ __device__ __forceinline__ int bwd_index(int q, int K, int n) {
   return q < K ? wrap_index(n - 1 + K - q, n) : n - 1 - (q - K);
 }
 
-// FP32 head of an FP64 column pre-roll: positions 0 .. kh-1 of the forward (fwd) or
-// backward pass from the zero state, inputs truncated to FP32; the state is handed to the
-// FP64 part that continues at position kh.  kh is a multiple of 16 and at most K.
-__device__ __forceinline__ void head_pass_col(const double* Wc, int nx, int ny, int K, int kh, float p1, float p2,
-                                              bool fwd, double* s1, double* s2) {
-  constexpr int kU = 8;
-  float f1 = 0.f, f2 = 0.f;
-  for (int q0 = 0; q0 < kh; q0 += kU) {
-    float r[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int j = fwd ? fwd_index(q0 + u, K, ny) : bwd_index(q0 + u, K, ny);
-      r[u] = f32_trunc(Wc[(int64_t)j * nx]);
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const float y = fmaf(p1, f1, fmaf(p2, f2, r[u]));
-      f2 = f1;
-      f1 = y;
-    }
-  }
-  *s1 = (double)f1;
-  *s2 = (double)f2;
-}
-
 // Column sweep + update, one thread per column, straight from global memory (a warp reads
 // 32 consecutive elements of a row per access).  Tiles: 32-column groups; kStreamWarps
 // groups per CTA.
@@ -2272,11 +2247,9 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
     T* const Lc = lo_ptr<T>(v, P, tl.start + lane);  // lo column of compensated members, else null
     constexpr int kUnroll = 8;  // loads issued ahead of the recurrence
     const int len = K + ny;
-    const int kh = P.ky32;      // FP32 head of each pre-roll (FP64 only; a multiple of 16)
     // forward: y_j = W'_j + p1 y_{j-1} + p2 y_{j-2}; y written over W'
     T y1 = T(0), y2 = T(0);
-    if constexpr (sizeof(T) == 8) head_pass_col(Wc, nx, ny, K, kh, P.fp1y, P.fp2y, true, &y1, &y2);
-    for (int q0 = sizeof(T) == 8 ? kh : 0; q0 < len; q0 += kUnroll) {
+    for (int q0 = 0; q0 < len; q0 += kUnroll) {
       T r[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u)
@@ -2293,8 +2266,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v,
     }
     // backward: x_j = y_j + p1 x_{j+1} + p2 x_{j+2};  C_j += kappa x_j
     T x1 = T(0), x2 = T(0);
-    if constexpr (sizeof(T) == 8) head_pass_col(Wc, nx, ny, K, kh, P.fp1y, P.fp2y, false, &x1, &x2);
-    for (int q0 = sizeof(T) == 8 ? kh : 0; q0 < len; q0 += kUnroll) {
+    for (int q0 = 0; q0 < len; q0 += kUnroll) {
       T r[kUnroll], c[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {

@@ -35,7 +35,7 @@ def run(nx, ny, L, C0, nsteps, head, gamma=0.005, dt=1e-3):
 
 
 def test_ensemble_size_members_with_and_without_head():
-    # 256 x 256 over [0, 2 pi)^2: K = 110 with a 32-point FP32 head in both directions
+    # 256 x 256 over [0, 2 pi)^2: K = 110 with a 32-point FP32 head in the row sweeps
     K, head = ch.ch_preroll_head(0.005 * 1e-3 / (2 * math.pi / 256) ** 4)
     assert head == 32
     # Rounding differences grow with the spinodal instability, at most like exp(t / (4 gamma))
