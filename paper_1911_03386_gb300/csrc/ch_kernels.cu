@@ -2197,12 +2197,17 @@ __global__ void __launch_bounds__(8 * NR, NR == 32 ? 2 : 1) res_kernel(DevView v
 // elements: the forward pass pre-rolls over the line's end and writes front to back; the
 // backward pass pre-rolls over the line's start and writes back to front.
 // -------------------------------------------------------------------------------------
-constexpr int kStreamWarps = 4;  // warps per CTA of the streaming sweeps
+constexpr int kStreamWarps = 4;  // register budget of the streaming sweeps: launch bounds of 4 warps
+// Warps per CTA of the streaming sweeps (at most kStreamWarps).  One: the SMs then hold
+// whole-warp shares of the lines (256 x 256^2: 2048 warps over 152 SMs, 13 or 14 each),
+// where 4-warp CTAs left some SMs 16 warps and others 12; measured 0.192 / 0.242 ms per
+// row / column launch against 0.212 / 0.260 with 4-warp CTAs.
+constexpr int kStreamCta = 1;
 
 
 // shared memory of rowstream_kernel: per warp two 32 x (CW+1) tiles, CW = 32 floats / 16 doubles
 constexpr size_t rowstream_smem_bytes(size_t elt) {
-  return (size_t)kStreamWarps * 2 * 32 * ((elt == 8 ? 16 : 32) + 1) * elt;
+  return (size_t)kStreamCta * 2 * 32 * ((elt == 8 ? 16 : 32) + 1) * elt;
 }
 
 // Binary64 -> binary32 with the significand truncated, from the two formats' fields (IEEE
@@ -2228,11 +2233,11 @@ __device__ __forceinline__ int bwd_index(int q, int K, int n) {
 }
 
 // Column sweep + update, one thread per column, straight from global memory (a warp reads
-// 32 consecutive elements of a row per access).  Tiles: 32-column groups; kStreamWarps
+// 32 consecutive elements of a row per access).  Tiles: 32-column groups; kStreamCta
 // groups per CTA.
 template <typename T>
 __global__ void __launch_bounds__(32 * kStreamWarps) colstream_kernel(DevView v, int ntiles, int tile_base) {
-  const int wt = blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
+  const int wt = blockIdx.x * kStreamCta + (threadIdx.x >> 5);
   if (wt >= ntiles) return;
   const Tile tl = v.col_tiles[tile_base + wt];
   MemberState* st = v.ms + tl.member;
@@ -2309,7 +2314,7 @@ __global__ void __launch_bounds__(32 * kStreamWarps) rowstream_kernel(DevView v,
   constexpr int RPI = 32 / CW;  // rows covered by one warp-wide copy instruction
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wt = blockIdx.x * kStreamWarps + w;
+  const int wt = blockIdx.x * kStreamCta + w;
   if (wt >= ntiles) return;
   const Tile tl = v.sweep_tiles[tile_base + wt];
   if (!v.ms[tl.member].active) return;
@@ -2503,7 +2508,7 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
       const int base = sh.st_seg[0] + sh.st_seg[1], rest = sh.n_sweep_tiles - base;
       if (rest <= 0) break;
       if (sh.stream)
-        rowstream_kernel<T><<<(rest + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps,
+        rowstream_kernel<T><<<(rest + kStreamCta - 1) / kStreamCta, 32 * kStreamCta,
                               rowstream_smem_bytes(sizeof(T)), st>>>(v, rest, base);
       else
         rowsweep_kernel<T><<<rest, sh.sweep_threads, sh.sweep_smem, st>>>(v, base);
@@ -2514,7 +2519,7 @@ cudaError_t phase_impl(const DevView& v, int phase, const LaunchShape& sh, cudaS
       if (sh.n_col_tiles == 0)
         break;
       else if (sh.stream)
-        colstream_kernel<T><<<(sh.n_col_tiles + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps, 0, st>>>(
+        colstream_kernel<T><<<(sh.n_col_tiles + kStreamCta - 1) / kStreamCta, 32 * kStreamCta, 0, st>>>(
             v, sh.n_col_tiles, 0);
       else if (sh.cols_persist)
         cols_kernel<T, true><<<min(sh.n_col_tiles, sh.cols_grid), sh.cols_threads, sh.cols_smem, st>>>(
