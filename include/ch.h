@@ -315,8 +315,8 @@ int ch_penta_factor(double s, int precision, double* c, double* p1, double* p2, 
  * Host-side split of an FP64 pre-roll, no GPU work: for the recurrence of
  * ch_penta_factor(s, CH_FP64) (companion matrix M = [[p1, p2], [1, 0]], pre-roll length K)
  * returns in *head the number of leading pre-roll points that the FP64 streaming row
- * sweeps run in FP32 (ch_tuning.preroll_head).  The FP32 part starts from the zero state with its
- * inputs truncated to FP32 and FP32 coefficients; its state error is at most
+ * sweeps run in FP32 (ch_tuning.preroll_head).  The FP32 part starts from the zero state
+ * with its inputs truncated to FP32 and FP32 coefficients; its state error is at most
  *   E = g2 2^-24 (3 + g (3 + |p1| + |p2|)) R,
  * R the line's largest input, g = sum_k |(M^k)_00| (the impulse response's l1 norm) and
  * g2 = sum_k ||M^k||_inf; the K - head FP64 points that follow multiply it by M^(K - head).
