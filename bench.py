@@ -582,7 +582,9 @@ def value_estimate(res):
 #               stencil_kernel, rowstream_kernel, colstream_kernel per step
 #   segment32   FP32 with the resident form off, the whole ensemble (134 MB):
 #               rows_seg_kernel, colseg_kernel per step
-KERNEL_CASES = {"resident32": ("fp32", 0, 32), "stream64": ("fp64", -1, 256), "segment32": ("fp32", -1, 256)}
+# name: (precision, ch_tuning.resident, members, workload)
+KERNEL_CASES = {"resident32": ("fp32", 0, 32, "ensemble"), "stream64": ("fp64", -1, 256, "ensemble"),
+                "segment32": ("fp32", -1, 256, "ensemble"), "long16": ("fp32", -1, 16, "long")}
 
 
 def kernel_case(name):
@@ -591,8 +593,8 @@ def kernel_case(name):
     __graft_entry__.build()
     import paper_1911_03386_gb300 as ch
     from paper_1911_03386_gb300 import workloads as wl
-    prec, res, members = KERNEL_CASES[name]
-    p = wl.ENSEMBLE_256
+    prec, res, members, work = KERNEL_CASES[name]
+    p = wl.ENSEMBLE_256 if work == "ensemble" else wl.LONG_1024
     stride = len(p["C0"]) // members
     descs = [dict(nx=p["nx"], ny=p["ny"], L=p["L"], gamma=p["gamma"], dt=p["dt"], C0=p["C0"][stride * k],
                   seed=wl.BASE_SEED, counter_base=k * p["nx"] * p["ny"]) for k in range(members)]
@@ -600,7 +602,8 @@ def kernel_case(name):
         e.set_tuning(resident=res)
         stream = torch.cuda.Stream()
         e.set_stream(stream.cuda_stream)
-        e.set_sampling(p["every"], p["t1"], capacity=0)
+        # sampling every 100 steps; the 1024^2 workload averages over the last 80 % of its horizon
+        e.set_sampling(p.get("every", 100), p.get("t1", 0.2 * p["steps"] * p["dt"]), capacity=0)
         e.step(200)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
